@@ -1,0 +1,190 @@
+"""CPU oracle for FAS-FMG and segmental-refinement FAS-FMG (FP64, plain C).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may load this package; the product path never
+does.  The C source (``srfmg_oracle.c``) shares no code with the CUDA library.
+
+Arrays are numpy float64, shape (n, n, n), index order [z][y][x] (x fastest).
+Every function returns new arrays and leaves its inputs untouched.
+
+Paper: Adams, Brown, Knepley, Samtaney, "Segmental Refinement: A Multigrid
+Technique for Data Locality" -- Sec. 3 (FASMGV, FMG), Sec. 4 (FASFMGSR,
+FASMGVSR, Eq. eq:nb), Sec. 5.1 (components).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAXK = 12
+
+
+class OrConfig(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("seg", ctypes.c_int),
+        ("K", ctypes.c_int),
+        ("J", ctypes.c_int * MAXK),
+        ("alpha", ctypes.c_int),
+        ("nu1", ctypes.c_int),
+        ("nu2", ctypes.c_int),
+        ("cheb_lo", ctypes.c_double),
+        ("cheb_hi", ctypes.c_double),
+        ("reverse_segments", ctypes.c_int),
+        ("n_threads", ctypes.c_int),
+        ("n_coarse", ctypes.c_int),
+    ]
+
+
+_LIB = None
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        for name in ("or_solve", "or_vcycle"):
+            getattr(lib, name).argtypes = [ctypes.POINTER(OrConfig), _DP, _DP]
+            getattr(lib, name).restype = ctypes.c_int
+        lib.or_check_config.argtypes = [ctypes.POINTER(OrConfig)]
+        lib.or_apply.argtypes = [ctypes.c_int, _DP, _DP]
+        lib.or_smooth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP, _DP]
+        lib.or_residual.argtypes = [ctypes.c_int, _DP, _DP, _DP]
+        lib.or_restrict.argtypes = [ctypes.c_int, _DP, _DP]
+        lib.or_prolong.argtypes = [ctypes.c_int, _DP, _DP]
+        lib.or_coarse_solve.argtypes = [ctypes.c_int, _DP, _DP]
+        lib.or_buffer_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int)]
+        lib.or_buffer_schedule.restype = None
+        lib.or_max_threads.restype = ctypes.c_int
+        _LIB = lib
+    return _LIB
+
+
+def _p(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _grid(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.ndim != 3 or a.shape[0] != a.shape[1] or a.shape[1] != a.shape[2]:
+        raise ValueError("expected an (n, n, n) array")
+    if n is not None and a.shape[0] != n:
+        raise ValueError("grid size mismatch")
+    return a
+
+
+def _check(st, what):
+    if st != 0:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+
+
+def buffer_schedule(A, B, K):
+    """J_k = 2 floor((A + B (K - k)) / 2) for k = 1..K (Eq. eq:nb)."""
+    J = (ctypes.c_int * max(K, 1))()
+    _lib().or_buffer_schedule(A, B, K, J)
+    return [J[i] for i in range(K)]
+
+
+def make_config(n, seg=0, K=0, J=None, A=4, B=1, alpha=1, nu1=2, nu2=2,
+                cheb_lo=1.0 / 6.0, cheb_hi=1.0, reverse_segments=False, n_threads=0,
+                n_coarse=0):
+    c = OrConfig()
+    c.n, c.seg, c.K = n, seg, K
+    if K > 0:
+        Js = list(J) if J is not None else buffer_schedule(A, B, K)
+        if len(Js) != K:
+            raise ValueError("J must have K entries")
+        for i, v in enumerate(Js):
+            c.J[i] = int(v)
+    c.alpha, c.nu1, c.nu2 = alpha, nu1, nu2
+    c.cheb_lo, c.cheb_hi = cheb_lo, cheb_hi
+    c.reverse_segments = int(bool(reverse_segments))
+    c.n_threads = n_threads
+    c.n_coarse = n_coarse
+    return c
+
+
+def check_config(**kw):
+    """0 if the oracle accepts the configuration, a negative code otherwise."""
+    return _lib().or_check_config(ctypes.byref(make_config(**kw)))
+
+
+def solve(f, **kw):
+    """FMG (seg=0 or K=0) or SR-FMG (FASFMGSR) of A u = f; returns u."""
+    f = _grid(f)
+    c = make_config(f.shape[0], **kw)
+    u = np.zeros_like(f)
+    _check(_lib().or_solve(ctypes.byref(c), _p(f), _p(u)), "solve")
+    return u
+
+
+def vcycle(f, u, **kw):
+    """One FAS V-cycle FASMGV(L, u, f) on the global grid; returns the new u."""
+    f = _grid(f)
+    u = _grid(u, f.shape[0]).copy()
+    kw = {k: v for k, v in kw.items() if k not in ("seg", "K", "J", "A", "B")}
+    c = make_config(f.shape[0], **kw)
+    _check(_lib().or_vcycle(ctypes.byref(c), _p(f), _p(u)), "vcycle")
+    return u
+
+
+def apply(u):
+    """A u with A = -Delta_h (7-point, Dirichlet ghosts)."""
+    u = _grid(u)
+    out = np.empty_like(u)
+    _check(_lib().or_apply(u.shape[0], _p(u), _p(out)), "apply")
+    return out
+
+
+def residual(u, f):
+    u = _grid(u)
+    f = _grid(f, u.shape[0])
+    r = np.empty_like(u)
+    _check(_lib().or_residual(u.shape[0], _p(f), _p(u), _p(r)), "residual")
+    return r
+
+
+def smooth(u, f, nu, cheb_lo=1.0 / 6.0, cheb_hi=1.0):
+    """Chebyshev smoother S^nu(L, u, f) on the whole grid; returns the new u."""
+    u = _grid(u).copy()
+    f = _grid(f, u.shape[0])
+    _check(_lib().or_smooth(u.shape[0], nu, cheb_lo, cheb_hi, _p(f), _p(u)), "smooth")
+    return u
+
+
+def restrict(a):
+    """8-child average onto the (n/2)^3 grid."""
+    a = _grid(a)
+    n = a.shape[0]
+    out = np.empty((n // 2,) * 3)
+    _check(_lib().or_restrict(n, _p(a), _p(out)), "restrict")
+    return out
+
+
+def prolong(ac):
+    """Cell-centred trilinear interpolation onto the (2 nc)^3 grid."""
+    ac = _grid(ac)
+    nc = ac.shape[0]
+    out = np.empty((2 * nc,) * 3)
+    _check(_lib().or_prolong(nc, _p(ac), _p(out)), "prolong")
+    return out
+
+
+def coarse_solve(f):
+    """Exact solve of A u = f by a banded Cholesky factorisation (small grids)."""
+    f = _grid(f)
+    u = np.empty_like(f)
+    _check(_lib().or_coarse_solve(f.shape[0], _p(f), _p(u)), "coarse_solve")
+    return u
+
+
+def max_threads():
+    return _lib().or_max_threads()
+
+
+LIBRARY = _build.LIBRARY

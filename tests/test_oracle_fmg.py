@@ -1,0 +1,94 @@
+"""Pins for the oracle's FAS V-cycle (Sec. 3.1, Fig. "FAS multigrid V-cycle")
+and full multigrid (Sec. 3.2, Fig. "Full multigrid").
+
+- the V-cycle's fixed point is the exact discrete solution (DST solve), and
+  its measured contraction satisfies the paper's condition Gamma < 0.25;
+- FMG with the coarsest grid solved exactly at 4^3 or 8^3 is the direct dense
+  solve;
+- FMG's total error against the manufactured solution falls at second order
+  and, with a 16^3 coarsest grid, its algebraic error is below the
+  discretisation error; at the paper's depth (2^3 coarsest) the ratio r of
+  algebraic to discretisation error stays bounded.
+"""
+import numpy as np
+import pytest
+
+import exact
+from paper_1406_7808_gb300 import inputs
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_vcycle_converges_to_discrete_solution(oracle_mod, n):
+    f, _ = inputs.manufactured(n, 0)
+    uh = exact.dst_solve(f)
+    rng = np.random.default_rng(0)
+    u = rng.standard_normal(f.shape)
+    errs = []
+    for _ in range(22):
+        u = oracle_mod.vcycle(f, u)
+        errs.append(np.abs(u - uh).max())
+    assert errs[-1] < 1e-11 * np.abs(uh).max()
+    gamma = errs[8] / errs[7]
+    assert gamma < 0.25  # Sec. 3.2: FMG needs a solver with Gamma < 0.25
+
+
+@pytest.mark.parametrize("n,nc", [(4, 4), (8, 8), (8, 4), (4, 2)])
+def test_fmg_against_dense_direct_solve(oracle_mod, n, nc):
+    f, uex = inputs.manufactured(n, 0)
+    ud = np.linalg.solve(exact.dense_matrix(n), f.ravel()).reshape(n, n, n)
+    u = oracle_mod.solve(f, n_coarse=nc)
+    if n == nc:  # FMG on a single level is the coarsest-grid direct solve
+        assert np.allclose(u, ud, rtol=0, atol=1e-13 * np.abs(ud).max())
+    else:
+        e_alg = np.abs(u - ud).max()
+        e_disc = np.abs(ud - uex).max()
+        assert e_alg < 3.0 * e_disc
+
+
+def test_fmg_second_order_and_bounded_ratio(oracle_mod):
+    errs, ratios = [], []
+    for n in (16, 32, 64, 128):
+        f, uex = inputs.manufactured(n, 0)
+        uh = exact.dst_solve(f)
+        u = oracle_mod.solve(f)
+        errs.append(np.abs(u - uex).max())
+        ratios.append(np.abs(u - uh).max() / np.abs(uh - uex).max())
+    q = [a / b for a, b in zip(errs, errs[1:])]
+    assert all(x > 2.5 for x in q)
+    assert all(b > a for a, b in zip(q, q[1:]))  # the order climbs towards 2 (ratio 4)
+    assert q[-1] > 3.3
+    assert max(ratios) < 12.0
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_fmg_algebraic_below_discretisation_error(oracle_mod, n):
+    f, uex = inputs.manufactured(n, 0)
+    uh = exact.dst_solve(f)
+    u = oracle_mod.solve(f, n_coarse=16)
+    assert np.abs(u - uh).max() < np.abs(uh - uex).max()
+
+
+def test_fmg_linear_in_f(oracle_mod):
+    n = 16
+    f1, _ = inputs.manufactured(n, 3)
+    f2, _ = inputs.manufactured(n, 4)
+    a, b = 0.7, -1.9
+    lhs = oracle_mod.solve(a * f1 + b * f2)
+    rhs = a * oracle_mod.solve(f1) + b * oracle_mod.solve(f2)
+    assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(lhs).max()
+
+
+def test_fmg_work_cycle_parameters(oracle_mod):
+    """More smoothing per level can only help the FMG result here."""
+    n = 32
+    f, _ = inputs.manufactured(n, 0)
+    uh = exact.dst_solve(f)
+    e122 = np.abs(oracle_mod.solve(f) - uh).max()
+    e144 = np.abs(oracle_mod.solve(f, nu1=4, nu2=4) - uh).max()
+    assert e144 < e122
+
+
+def test_rejects_bad_sizes(oracle_mod):
+    assert oracle_mod.check_config(n=20) != 0  # 20 -> 10 -> 5 never reaches 2 or 3
+    assert oracle_mod.check_config(n=24) == 0
+    assert oracle_mod.check_config(n=32, n_coarse=3) != 0

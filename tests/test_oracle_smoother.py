@@ -1,0 +1,41 @@
+"""Pins for the Chebyshev smoother (Sec. 5.1: degree-2 pre/post smoothers,
+degree-1 before each FMG V-cycle): on an eigenmode of D^-1 A with f = 0 the
+smoother multiplies the mode by the Chebyshev factor p_nu(lambda), evaluated
+here in closed form (cos / cosh of nu times arccos / arccosh)."""
+import numpy as np
+import pytest
+
+import exact
+
+
+@pytest.mark.parametrize("nu", [1, 2, 3])
+@pytest.mark.parametrize("interval", [(1.0 / 6.0, 1.0), (0.1, 1.1), (0.05, 1.0)])
+def test_chebyshev_mode_factor(oracle_mod, nu, interval):
+    n = 8
+    rng = np.random.default_rng(nu)
+    for _ in range(4):
+        k = tuple(int(v) for v in rng.integers(1, n + 1, size=3))
+        m = exact.mode(n, k)
+        lam = exact.eigenvalue(n, k) / (6.0 * n * n)  # eigenvalue of D^-1 A
+        out = oracle_mod.smooth(m, np.zeros_like(m), nu, *interval)
+        fac = exact.chebyshev_factor(lam, nu, *interval)
+        assert np.allclose(out, fac * m, rtol=0, atol=1e-13)
+
+
+def test_degree_one_is_damped_jacobi(oracle_mod):
+    rng = np.random.default_rng(2)
+    n = 6
+    u, f = rng.standard_normal((2, n, n, n))
+    lo, hi = 1.0 / 6.0, 1.0
+    omega = 1.0 / (lo + hi)  # 1 / theta with theta = (2 lo + 2 hi) / 2
+    r = f - (exact.dense_matrix(n) @ u.ravel()).reshape(n, n, n)
+    ref = u + omega * r / (6.0 * n * n)
+    assert np.allclose(oracle_mod.smooth(u, f, 1, lo, hi), ref, rtol=0, atol=1e-13)
+
+
+def test_smoother_fixed_point(oracle_mod):
+    n = 8
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal((n, n, n))
+    uh = exact.dst_solve(f)
+    assert np.allclose(oracle_mod.smooth(uh, f, 2), uh, rtol=0, atol=1e-14 * np.abs(uh).max() * 10)

@@ -1,0 +1,112 @@
+"""Pins for the oracle's segmental refinement (Sec. 4: regions, Eq. eq:nb,
+Figs. "FMG segmental refinement" and "FAS V-cycle segmental refinement").
+
+- special cases that must reduce to plain FMG: one segment, and buffers that
+  cover the whole level (J_k >= N_k);
+- equality with an independent full-grid/mask implementation
+  (tests/sr_masked.py) on several geometries, including clipped boxes and a
+  grid that coarsens to 3^3;
+- invariants: segment order and thread count do not change a bit of the
+  result; the solve is linear in f;
+- accuracy: the SR error ratio e_r = e_SR / e_conv (Sec. 5.2) improves with
+  larger buffers.  The paper's absolute e_r values (Tables 1-3) come from a
+  27-point stencil on another domain and do not pin this problem.
+"""
+import numpy as np
+import pytest
+
+import sr_masked
+from paper_1406_7808_gb300 import inputs
+
+
+def test_buffer_schedule_eq_nb(oracle_mod):
+    assert oracle_mod.buffer_schedule(4, 1, 3) == [6, 4, 4]
+    assert oracle_mod.buffer_schedule(8, 0, 5) == [8] * 5
+    assert oracle_mod.buffer_schedule(2, 3, 4) == [10, 8, 4, 2]
+    assert oracle_mod.buffer_schedule(3, 0, 2) == [2, 2]
+
+
+@pytest.mark.parametrize("n,K", [(16, 1), (32, 2), (32, 3)])
+def test_one_segment_is_plain_fmg(oracle_mod, n, K):
+    f, _ = inputs.manufactured(n, 0)
+    plain = oracle_mod.solve(f)
+    sr = oracle_mod.solve(f, seg=n, K=K, A=4, B=1)
+    assert np.array_equal(sr, plain)
+
+
+@pytest.mark.parametrize("n,seg,K", [(16, 8, 1), (32, 8, 2), (32, 16, 3)])
+def test_whole_level_buffers_are_plain_fmg(oracle_mod, n, seg, K):
+    f, _ = inputs.manufactured(n, 1)
+    plain = oracle_mod.solve(f)
+    J = [n >> (K - k) for k in range(1, K + 1)]  # J_k = N_k: every box is the whole level
+    sr = oracle_mod.solve(f, seg=seg, K=K, J=J)
+    assert np.array_equal(sr, plain)
+
+
+GEOMETRIES = [
+    (16, 8, 1, [2]),
+    (32, 8, 2, [4, 4]),
+    (32, 16, 2, [2, 4]),
+    (32, 8, 3, [6, 4, 4]),
+    (24, 12, 2, [2, 2]),
+    (48, 16, 2, [4, 2]),
+    (32, 8, 2, [0, 0]),
+]
+
+
+@pytest.mark.parametrize("n,seg,K,J", GEOMETRIES)
+def test_matches_independent_masked_implementation(oracle_mod, n, seg, K, J):
+    f, _ = inputs.manufactured(n, 1)
+    a = oracle_mod.solve(f, seg=seg, K=K, J=J)
+    b = sr_masked.sr_fmg(f, seg, K, J, sr_masked.Params())
+    assert not np.isnan(b).any()
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_masked_plain_fmg_matches(oracle_mod):
+    for n in (8, 16, 24):
+        f, _ = inputs.manufactured(n, 0)
+        a = oracle_mod.solve(f)
+        b = sr_masked.inner(sr_masked.fmg(f, sr_masked.Params()))
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_segment_order_and_threads_do_not_matter(oracle_mod):
+    n = 64
+    f, _ = inputs.manufactured(n, 2)
+    kw = dict(seg=16, K=2, A=4, B=1)
+    a = oracle_mod.solve(f, n_threads=1, **kw)
+    b = oracle_mod.solve(f, n_threads=1, reverse_segments=True, **kw)
+    c = oracle_mod.solve(f, n_threads=4, **kw)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, c)
+
+
+def test_sr_linear_in_f(oracle_mod):
+    n = 32
+    f1, _ = inputs.manufactured(n, 5)
+    f2, _ = inputs.manufactured(n, 6)
+    kw = dict(seg=8, K=2, A=4, B=1)
+    lhs = oracle_mod.solve(2.0 * f1 - 0.5 * f2, **kw)
+    rhs = 2.0 * oracle_mod.solve(f1, **kw) - 0.5 * oracle_mod.solve(f2, **kw)
+    assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(lhs).max()
+
+
+def test_error_ratio_improves_with_buffers(oracle_mod):
+    n = 128
+    f, uex = inputs.manufactured(n, 0)
+    e_conv = np.abs(oracle_mod.solve(f) - uex).max()
+    er = {}
+    for A, B in [(2, 0), (4, 1), (8, 0), (8, 2)]:
+        u = oracle_mod.solve(f, seg=32, K=3, A=A, B=B)
+        er[(A, B)] = np.abs(u - uex).max() / e_conv
+    assert er[(2, 0)] > er[(4, 1)] > er[(8, 0)] > er[(8, 2)] >= 0.99
+    assert er[(8, 2)] < 1.1  # acceptable in the sense of Sec. 5.2 (within ~10%)
+
+
+def test_rejects_inconsistent_geometry(oracle_mod):
+    assert oracle_mod.check_config(n=32, seg=12, K=2, J=[2, 2]) != 0   # seg does not divide n
+    assert oracle_mod.check_config(n=32, seg=8, K=4, J=[2] * 4) != 0   # seg not divisible by 2^K
+    assert oracle_mod.check_config(n=32, seg=8, K=2, J=[3, 4]) != 0    # odd buffer
+    assert oracle_mod.check_config(n=32, seg=8, K=2, J=[2, 8]) != 0    # J_1 < J_2 / 2
+    assert oracle_mod.check_config(n=32, seg=8, K=2, J=[4, 8]) == 0
