@@ -1,0 +1,162 @@
+/*
+ * srfmg.h -- C ABI of the GB300 (sm_103a) segmental-refinement full multigrid
+ * solver for the cell-centred 7-point Poisson problem on the unit cube.
+ *
+ * Method: Adams, Brown, Knepley, Samtaney, "Segmental Refinement: A Multigrid
+ * Technique for Data Locality".
+ *   problem        Sec. 2, Eq. (eq:eq), Eq. (eq:deq): -Delta u = f in (0,1)^3,
+ *                  u = 0 on the boundary, N^3 cells, cell centres (i + 1/2)/N.
+ *                  The library solves A u = f with A = -Delta_h,
+ *                  (A u)_i = (6 u_i - sum of the 6 neighbours) N^2, ghost cells
+ *                  outside the domain holding minus their mirror cell (Sec. 3.3).
+ *   FMG            Sec. 3.2, Fig. "Full multigrid": F(alpha, nu1, nu2) cycles
+ *                  built on the FAS V-cycle of Sec. 3.1, Fig. "FAS multigrid
+ *                  V-cycle", Eq. (eq:cresid2).
+ *   SR-FMG         Sec. 4, Figs. "FMG segmental refinement" and "FAS V-cycle
+ *                  segmental refinement": the K finest levels are split into
+ *                  segments of seg^3 genuine cells (on the finest level) plus
+ *                  J_k buffer cells per side, Eq. (eq:nb); levels 0 and below
+ *                  are solved globally.
+ *   components     Sec. 5.1: Chebyshev smoothers (degree nu1/nu2 around the
+ *                  V-cycle, alpha before it), 8-child average restriction,
+ *                  cell-centred trilinear prolongation.
+ *
+ * Conventions for every entry point:
+ *   - grids are contiguous float64 arrays of n^3 values, index [z][y][x],
+ *     x fastest, owned by the caller;
+ *   - "device" pointers must be CUDA device memory of the device that was
+ *     current when the handle was created; "host" pointers are host memory;
+ *   - stream is a cudaStream_t (NULL = the legacy default stream);
+ *   - return value: SR_OK (0) or a negative SR_ERR_* code; no entry point
+ *     aborts the process or prints.
+ */
+#ifndef SRFMG_H
+#define SRFMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SR_FMG_MAXK 12
+
+/* status codes */
+#define SR_OK 0
+#define SR_ERR_INVALID (-1)          /* bad argument or inconsistent configuration */
+#define SR_ERR_UNSUPPORTED_SIZE (-2) /* grid size the solver does not handle */
+#define SR_ERR_OOM (-3)              /* device or host allocation failed */
+#define SR_ERR_CUDA (-4)             /* a CUDA call failed (launch, copy, sync) */
+#define SR_ERR_TIMEOUT (-5)          /* a bounded device-side wait gave up */
+#define SR_ERR_NONFINITE (-6)        /* the right-hand side holds a NaN or Inf */
+#define SR_ERR_NO_DEVICE (-7)        /* no usable CUDA device */
+
+/* precision modes */
+#define SR_FP64 0   /* every step in float64 */
+#define SR_MIXED 1  /* float32 smoothing and transfers inside a float64 defect
+                       correction loop (not in this version: SR_ERR_INVALID) */
+
+typedef struct sr_fmg_s* sr_fmg_t;
+
+/*
+ * Solver configuration.  sr_fmg_default_config fills it for a given n.
+ *   n         fine cells per dimension; n must halve down to the coarsest grid.
+ *   n_coarse  edge of the coarsest grid, solved exactly (Sec. 3.1, the "else"
+ *             branch of FASMGV); 0 = keep halving until 2 or 3 cells remain.
+ *             At most 8.
+ *   seg       genuine segment edge on the finest level; 0 = plain FMG (no
+ *             segmental refinement).  n % seg == 0 and seg % 2^K == 0.
+ *   K         number of SR levels (the K finest levels); 0 = plain FMG.
+ *   A, B      buffer schedule J_k = 2 floor((A + B (K - k)) / 2), Eq. (eq:nb),
+ *             used when use_J == 0.
+ *   use_J, J  when use_J != 0, J[k-1] is the buffer width J_k, k = 1..K;
+ *             every J_k must be even and J_{k-1} >= J_k / 2.
+ *   alpha, nu1, nu2   Chebyshev degrees of the F(alpha, nu1, nu2) cycle (1, 2, 2).
+ *   cheb_lo, cheb_hi  Chebyshev interval as fractions of lambda_max(D^-1 A) = 2
+ *             (D = 6 N^2 the diagonal); defaults 1/6 and 1.
+ *   precision SR_FP64.
+ *   n_outer   reserved for SR_MIXED (defect-correction passes).
+ */
+typedef struct {
+  int n;
+  int n_coarse;
+  int seg;
+  int K;
+  int A, B;
+  int use_J;
+  int J[SR_FMG_MAXK];
+  int alpha, nu1, nu2;
+  double cheb_lo, cheb_hi;
+  int precision;
+  int n_outer;
+} sr_fmg_config;
+
+/* Fill cfg with the defaults for an n^3 grid: plain FMG, F(1,2,2), Chebyshev
+ * interval [1/6, 1] * lambda_max, coarsest grid 2^3 or 3^3, SR_FP64. */
+void sr_fmg_default_config(sr_fmg_config* cfg, int n);
+
+/* Validate cfg, build the level and segment plan and allocate the device
+ * workspace on the current device.  *out receives the handle (NULL on error).
+ * Errors: SR_ERR_INVALID, SR_ERR_UNSUPPORTED_SIZE, SR_ERR_OOM, SR_ERR_CUDA,
+ * SR_ERR_NO_DEVICE. */
+int sr_fmg_create(sr_fmg_t* out, const sr_fmg_config* cfg);
+
+/* Release the workspace and the handle (NULL is accepted). */
+int sr_fmg_destroy(sr_fmg_t h);
+
+/* Bytes of device memory the handle holds. */
+int sr_fmg_workspace_bytes(sr_fmg_t h, size_t* bytes);
+
+/* Solve A u = f by FMG or SR-FMG.  f_dev, u_dev: device arrays of n^3
+ * doubles; u_dev receives the solution (its prior content is ignored).  The
+ * work is queued on stream; the call then waits for the stream and returns
+ * the solve's status (SR_ERR_NONFINITE if f holds a NaN or Inf, in which case
+ * u_dev is undefined).  f_dev and u_dev must not overlap. */
+int sr_fmg_solve(sr_fmg_t h, const double* f_dev, double* u_dev, void* stream);
+
+/* As sr_fmg_solve, but only queues the work and returns launch errors; the
+ * solve's own status is read later by sr_fmg_check.  Calls on one handle must
+ * not run concurrently (they share the workspace). */
+int sr_fmg_solve_async(sr_fmg_t h, const double* f_dev, double* u_dev, void* stream);
+
+/* Wait for stream and return the status of the solves queued on h since the
+ * previous check (SR_OK, SR_ERR_NONFINITE, SR_ERR_TIMEOUT). */
+int sr_fmg_check(sr_fmg_t h, void* stream);
+
+/* End-to-end solve from host memory: copies f_host (n^3 doubles) to the
+ * device, solves, copies the solution to u_host, waits for stream.  Page-
+ * locked host buffers give the fastest copies; pageable memory also works. */
+int sr_fmg_solve_host(sr_fmg_t h, const double* f_host, double* u_host, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* sr_fmg_status_string(int status);
+
+/*
+ * Single components on a whole n^3 grid, device arrays, for testing each
+ * step against a reference.  Each call allocates and frees its own
+ * temporaries and waits for stream before returning.
+ *   sr_op_apply        out = A u                                  (Eq. eq:deq)
+ *   sr_op_residual     r = f - A u                                (Fig. "FAS multigrid V-cycle")
+ *   sr_op_smooth       u <- S^nu(A, u, f), Chebyshev on D^-1 A over
+ *                      [cheb_lo, cheb_hi] * 2                     (Sec. 5.1)
+ *   sr_op_restrict     ac = 8-child average of a, (n/2)^3 result  (Sec. 5.1)
+ *   sr_op_prolong      af = trilinear interpolation of the nc^3 grid ac onto
+ *                      (2 nc)^3                                  (Sec. 5.1)
+ *   sr_op_coarse_solve u = A^-1 f exactly, n <= 8                 (Sec. 3.1)
+ *   sr_op_vcycle       one FAS V-cycle on u with right-hand side f, using
+ *                      cfg's cycle parameters (seg and K ignored)  (Sec. 3.1)
+ */
+int sr_op_apply(int n, const double* u, double* out, void* stream);
+int sr_op_residual(int n, const double* f, const double* u, double* r, void* stream);
+int sr_op_smooth(int n, int nu, double cheb_lo, double cheb_hi, const double* f, double* u,
+                 void* stream);
+int sr_op_restrict(int n, const double* a, double* ac, void* stream);
+int sr_op_prolong(int nc, const double* ac, double* af, void* stream);
+int sr_op_coarse_solve(int n, const double* f, double* u, void* stream);
+int sr_op_vcycle(const sr_fmg_config* cfg, const double* f, double* u, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRFMG_H */

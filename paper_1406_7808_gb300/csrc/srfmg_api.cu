@@ -1,0 +1,753 @@
+// Host side of the solver: configuration checks, the level / segment plan,
+// device workspace, the launch sequence of FMG and SR-FMG, and the C ABI
+// declared in include/srfmg.h.
+//
+// Launch sequence (Sec. 3 and Sec. 4 of the paper):
+//   f hierarchy      f_{k-1} = 8-child average of f_k, every level
+//   FMG              coarsest exact solve, then per global level: prolongation,
+//                    S^alpha, one FAS V-cycle (Fig. "Full multigrid")
+//   SR stages k=1..K per stage, on all segments at once: prolongation onto
+//                    Omega^C u Omega^GSR, S^alpha, the down-leg of FASMGVSR
+//                    (S^nu1, residual + restriction onto Omega^F, modified tau
+//                    right-hand side), the transition-level right-hand side,
+//                    the global V-cycle, then the up-leg (corrections onto
+//                    Omega^C u Omega^GSR and S^nu2) (Figs. "FMG segmental
+//                    refinement", "FAS V-cycle segmental refinement")
+//   output           genuine cells of the finest level into u
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "srfmg.h"
+#include "srfmg_internal.cuh"
+
+using namespace srfmg;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// plan
+
+struct Level {
+  int n = 0;
+  int nbox = 0;
+  bool global = true;
+  long long slot = 0;            // elements per box (SR levels)
+  std::vector<BoxDesc> hboxes;
+  BoxDesc* dboxes = nullptr;     // device copy of hboxes
+  BoxDesc* dglobal = nullptr;    // device descriptor of the whole level, unpadded
+  LevelView view{};
+  double *u = nullptr, *t = nullptr, *rhs = nullptr, *r = nullptr, *rho = nullptr,
+         *d = nullptr, *f = nullptr;
+};
+
+struct Cheb {
+  int nu = 0;
+  double a = 0, b = 0;            // degree-2 polynomial form
+  std::vector<double> alpha, beta;  // recurrence steps
+};
+
+}  // namespace
+
+struct sr_fmg_s {
+  sr_fmg_config cfg{};
+  int device = 0;
+  int K = 0;                       // SR levels
+  int G = 0;                       // global levels, glev[G-1] is level 0
+  std::vector<Level> glev;
+  std::vector<Level> slev;         // slev[k], k = 1..K
+  double* minv = nullptr;          // inverse of the coarsest operator
+  unsigned int* status = nullptr;  // device status bits
+  Cheb pre, post, fmg;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  double* hbuf_f = nullptr;        // device staging for sr_fmg_solve_host
+  double* hbuf_u = nullptr;
+};
+
+namespace {
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return SR_ERR_CUDA;    \
+  } while (0)
+
+int halvings_to_coarsest(int n, int nc) {
+  int m = 0;
+  while (nc ? n > nc : n > 3) {
+    if (n % 2) return -1;
+    n /= 2;
+    ++m;
+  }
+  if (nc) return n == nc ? m : -1;
+  return n >= 2 ? m : -1;
+}
+
+void schedule(const sr_fmg_config& c, int* J) {
+  for (int k = 1; k <= c.K; ++k) {
+    if (c.use_J) {
+      J[k - 1] = c.J[k - 1];
+    } else {
+      const int v = c.A + c.B * (c.K - k);  // Eq. (eq:nb)
+      J[k - 1] = 2 * (v / 2);
+    }
+  }
+}
+
+int check_config(const sr_fmg_config* c) {
+  if (!c) return SR_ERR_INVALID;
+  if (c->precision != SR_FP64) return SR_ERR_INVALID;
+  if (c->alpha < 0 || c->nu1 < 0 || c->nu2 < 0 || c->alpha > 16 || c->nu1 > 16 || c->nu2 > 16)
+    return SR_ERR_INVALID;
+  if (!(c->cheb_lo > 0.0 && c->cheb_hi > c->cheb_lo && c->cheb_hi < 4.0)) return SR_ERR_INVALID;
+  if (c->n_coarse < 0 || c->n_coarse > 8 || c->n_coarse == 1) return SR_ERR_UNSUPPORTED_SIZE;
+  if (c->n < 2 || c->n > 2048) return SR_ERR_UNSUPPORTED_SIZE;
+  if (halvings_to_coarsest(c->n, c->n_coarse) < 0) return SR_ERR_UNSUPPORTED_SIZE;
+  if (c->seg < 0 || c->K < 0 || c->K > SR_FMG_MAXK) return SR_ERR_INVALID;
+  if (c->seg == 0 || c->K == 0) return SR_OK;
+  if (c->n % c->seg) return SR_ERR_INVALID;
+  if (c->seg % (1 << c->K)) return SR_ERR_INVALID;
+  if (halvings_to_coarsest(c->n >> c->K, c->n_coarse) < 0) return SR_ERR_UNSUPPORTED_SIZE;
+  const long long nseg1 = c->n / c->seg;
+  if (nseg1 * nseg1 * nseg1 > 65535) return SR_ERR_UNSUPPORTED_SIZE;
+  int J[SR_FMG_MAXK];
+  schedule(*c, J);
+  for (int k = 1; k <= c->K; ++k) {
+    if (J[k - 1] < 0 || J[k - 1] % 2) return SR_ERR_INVALID;
+    if (k >= 2 && 2 * J[k - 2] < J[k - 1]) return SR_ERR_INVALID;
+  }
+  return SR_OK;
+}
+
+Cheb chebyshev(int nu, double lo_frac, double hi_frac) {
+  Cheb c;
+  c.nu = nu;
+  const double lo = 2.0 * lo_frac, hi = 2.0 * hi_frac;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  // three-term recurrence: d_0 = r_0/theta, d_m = rho_m rho_{m-1} d_{m-1} + (2 rho_m/delta) r_m
+  double rho_old = delta / theta;
+  for (int m = 0; m < nu; ++m) {
+    if (m == 0) {
+      c.alpha.push_back(0.0);
+      c.beta.push_back(1.0 / theta);
+    } else {
+      const double rho = 1.0 / (2.0 * theta / delta - rho_old);
+      c.alpha.push_back(rho * rho_old);
+      c.beta.push_back(2.0 * rho / delta);
+      rho_old = rho;
+    }
+  }
+  if (nu == 2) {
+    // x2 = x0 + c1 r0 + c2 B r0 with B r0 = r0 - (sum of neighbours of r0)/6
+    const double r0 = delta / theta;
+    const double r1 = 1.0 / (2.0 * theta / delta - r0);
+    const double c1 = (1.0 + r1 * r0) / theta + 2.0 * r1 / delta;
+    const double c2 = -2.0 * r1 / (delta * theta);
+    c.a = c1 + c2;
+    c.b = -c2 / 6.0;
+  }
+  return c;
+}
+
+template <typename T>
+int dalloc(sr_fmg_s* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return SR_OK;
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return SR_ERR_OOM;
+  }
+  h->allocs.push_back(q);
+  h->bytes += count * sizeof(T);
+  if (cudaMemset(q, 0, count * sizeof(T)) != cudaSuccess) return SR_ERR_CUDA;
+  *p = static_cast<T*>(q);
+  return SR_OK;
+}
+
+BoxDesc whole_box(int n) {
+  BoxDesc b;
+  std::memset(&b, 0, sizeof(b));
+  for (int d = 0; d < 3; ++d) {
+    b.lo[d] = 0; b.hi[d] = n;
+    b.plo[d] = 0; b.phi[d] = n;
+    b.rlo[d] = 0; b.rhi[d] = n / 2;
+    b.glo[d] = 0; b.ghi[d] = n;
+  }
+  b.ox = b.oy = b.oz = 0;
+  b.sy = n;
+  b.sz = (long long)n * n;
+  b.base = 0;
+  return b;
+}
+
+long long prod(const int lo[3], const int hi[3]) {
+  return (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+}
+
+int finish_level(sr_fmg_s* h, Level& L) {
+  L.nbox = (int)L.hboxes.size();
+  int rc = dalloc(h, &L.dboxes, L.hboxes.size());
+  if (rc) return rc;
+  CK(cudaMemcpy(L.dboxes, L.hboxes.data(), sizeof(BoxDesc) * L.hboxes.size(),
+                cudaMemcpyHostToDevice));
+  BoxDesc g = whole_box(L.n);
+  rc = dalloc(h, &L.dglobal, 1);
+  if (rc) return rc;
+  CK(cudaMemcpy(L.dglobal, &g, sizeof(BoxDesc), cudaMemcpyHostToDevice));
+  LevelView v{};
+  v.boxes = L.dboxes;
+  v.nbox = L.nbox;
+  v.n = L.n;
+  for (const BoxDesc& b : L.hboxes) {
+    const int slo[3] = {b.ox, b.oy, b.oz};
+    int shi[3];
+    const bool shell = b.ox < b.lo[0];
+    for (int d = 0; d < 3; ++d) shi[d] = shell ? b.hi[d] + 1 : b.hi[d];
+    auto mx = [](int& m, long long x) { if (x > m) m = (int)x; };
+    mx(v.max_cells, prod(b.lo, b.hi));
+    mx(v.max_stored, prod(slo, shi));
+    mx(v.max_prolong, prod(b.plo, b.phi));
+    mx(v.max_restrict, prod(b.rlo, b.rhi));
+    mx(v.max_genuine, prod(b.glo, b.ghi));
+  }
+  L.view = v;
+  return SR_OK;
+}
+
+// dense inverse of the coarsest operator from its eigen-decomposition: the
+// 1D factors sin(k pi (i + 1/2) / n), k = 1..n, are orthogonal with squared
+// norms n/2 (k < n) and n (k = n), eigenvalues 4 n^2 sin^2(k pi / 2n).
+std::vector<double> coarsest_inverse(int n) {
+  const int m = n * n * n;
+  std::vector<double> phi((size_t)n * n), lam(n);
+  const double pi = 3.14159265358979323846;
+  for (int k = 1; k <= n; ++k) {
+    const double norm = std::sqrt((k < n) ? 2.0 / n : 1.0 / n);
+    for (int i = 0; i < n; ++i) phi[(size_t)(k - 1) * n + i] = norm * std::sin(pi * k * (i + 0.5) / n);
+    const double s = std::sin(pi * k / (2.0 * n));
+    lam[k - 1] = 4.0 * n * n * s * s;
+  }
+  std::vector<double> minv((size_t)m * m, 0.0);
+  for (int k3 = 0; k3 < n; ++k3)
+    for (int k2 = 0; k2 < n; ++k2)
+      for (int k1 = 0; k1 < n; ++k1) {
+        const double il = 1.0 / (lam[k1] + lam[k2] + lam[k3]);
+        std::vector<double> v(m);
+        for (int z = 0; z < n; ++z)
+          for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x)
+              v[(z * n + y) * n + x] = phi[(size_t)k1 * n + x] * phi[(size_t)k2 * n + y] *
+                                       phi[(size_t)k3 * n + z];
+        for (int p = 0; p < m; ++p) {
+          const double w = il * v[p];
+          double* row = &minv[(size_t)p * m];
+          for (int q = 0; q < m; ++q) row[q] += w * v[q];
+        }
+      }
+  return minv;
+}
+
+int build_global_levels(sr_fmg_s* h, int ntop, bool finest_is_user) {
+  const int m = halvings_to_coarsest(ntop, h->cfg.n_coarse);
+  h->G = m + 1;
+  h->glev.resize(h->G);
+  const bool need_d = h->cfg.alpha > 2 || h->cfg.nu1 > 2 || h->cfg.nu2 > 2;
+  for (int g = 0; g < h->G; ++g) {
+    Level& L = h->glev[g];
+    L.n = ntop >> (h->G - 1 - g);
+    L.global = true;
+    L.hboxes.assign(1, whole_box(L.n));
+    if (g == 0) for (int d = 0; d < 3; ++d) { L.hboxes[0].rlo[d] = 0; L.hboxes[0].rhi[d] = 0; }
+    int rc = finish_level(h, L);
+    if (rc) return rc;
+    const size_t cells = (size_t)L.n * L.n * L.n;
+    const bool top = (g == h->G - 1);
+    if ((rc = dalloc(h, &L.r, cells))) return rc;
+    if (need_d && (rc = dalloc(h, &L.d, cells))) return rc;
+    if (top && finest_is_user) continue;  // u and f are the caller's arrays
+    if ((rc = dalloc(h, &L.u, cells))) return rc;
+    if ((rc = dalloc(h, &L.t, cells))) return rc;
+    if ((rc = dalloc(h, &L.rhs, cells))) return rc;
+    if ((rc = dalloc(h, &L.rho, cells))) return rc;
+    if ((rc = dalloc(h, &L.f, cells))) return rc;
+  }
+  const int nc = h->glev[0].n;
+  std::vector<double> minv = coarsest_inverse(nc);
+  int rc = dalloc(h, &h->minv, minv.size());
+  if (rc) return rc;
+  CK(cudaMemcpy(h->minv, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return SR_OK;
+}
+
+int build_sr_levels(sr_fmg_s* h) {
+  const sr_fmg_config& c = h->cfg;
+  const int K = h->K;
+  int J[SR_FMG_MAXK];
+  schedule(c, J);
+  const int nseg1 = c.n / c.seg;
+  const bool need_d = c.alpha > 2 || c.nu1 > 2 || c.nu2 > 2;
+  h->slev.resize(K + 1);
+  for (int k = 1; k <= K; ++k) {
+    Level& L = h->slev[k];
+    L.n = c.n >> (K - k);
+    L.global = false;
+    const int sk = c.seg >> (K - k);
+    const int s0 = c.seg >> K;
+    std::vector<BoxDesc> boxes;
+    long long slot = 0;
+    for (int pz = 0; pz < nseg1; ++pz)
+      for (int py = 0; py < nseg1; ++py)
+        for (int px = 0; px < nseg1; ++px) {
+          const int q[3] = {px, py, pz};
+          BoxDesc b;
+          std::memset(&b, 0, sizeof(b));
+          for (int d = 0; d < 3; ++d) {
+            b.glo[d] = q[d] * sk;
+            b.ghi[d] = (q[d] + 1) * sk;
+            b.lo[d] = b.glo[d] - J[k - 1] < 0 ? 0 : b.glo[d] - J[k - 1];
+            b.hi[d] = b.ghi[d] + J[k - 1] > L.n ? L.n : b.ghi[d] + J[k - 1];
+            b.plo[d] = b.lo[d] > 0 ? b.lo[d] - 1 : 0;
+            b.phi[d] = b.hi[d] < L.n ? b.hi[d] + 1 : L.n;
+            if (k > 1) {  // Omega^F on level k-1: the cells under the compute region
+              b.rlo[d] = b.lo[d] / 2;
+              b.rhi[d] = b.hi[d] / 2;
+            } else {      // transition: this segment's genuine level-0 cells
+              b.rlo[d] = q[d] * s0;
+              b.rhi[d] = (q[d] + 1) * s0;
+            }
+          }
+          b.ox = b.lo[0] - 1;
+          b.oy = b.lo[1] - 1;
+          b.oz = b.lo[2] - 1;
+          const int e0 = b.hi[0] - b.lo[0] + 2, e1 = b.hi[1] - b.lo[1] + 2,
+                    e2 = b.hi[2] - b.lo[2] + 2;
+          b.sy = e0;
+          b.sz = (long long)e0 * e1;
+          const long long size = (long long)e0 * e1 * e2;
+          if (size > slot) slot = size;
+          boxes.push_back(b);
+        }
+    for (size_t i = 0; i < boxes.size(); ++i) boxes[i].base = (long long)i * slot;
+    L.slot = slot;
+    L.hboxes = boxes;
+    int rc = finish_level(h, L);
+    if (rc) return rc;
+    const size_t elems = (size_t)slot * boxes.size();
+    if ((rc = dalloc(h, &L.u, elems))) return rc;
+    if ((rc = dalloc(h, &L.r, elems))) return rc;
+    if (need_d && (rc = dalloc(h, &L.d, elems))) return rc;
+    if (k < K) {
+      if ((rc = dalloc(h, &L.t, elems))) return rc;
+      if ((rc = dalloc(h, &L.rhs, elems))) return rc;
+      if ((rc = dalloc(h, &L.rho, elems))) return rc;
+      if ((rc = dalloc(h, &L.f, (size_t)L.n * L.n * L.n))) return rc;
+    }
+  }
+  return SR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch sequence
+
+FieldView view_global(const Level& L, const double* p) { return FieldView{p, L.dglobal, 1}; }
+FieldView view_boxes(const Level& L, const double* p) { return FieldView{p, L.dboxes, 0}; }
+
+int smooth(const Level& L, const Cheb& c, double* u, FieldView f, cudaStream_t s) {
+  if (c.nu == 0) return SR_OK;
+  if (c.nu == 2) {
+    CK(launch_cheb_residual(L.view, u, L.r, f, s));
+    CK(launch_cheb2_update(L.view, u, L.r, c.a, c.b, s));
+    return SR_OK;
+  }
+  for (int m = 0; m < c.nu; ++m) {
+    CK(launch_cheb_residual(L.view, u, L.r, f, s));
+    const int write_d = (c.nu > 1 && m < c.nu - 1) ? 1 : 0;
+    CK(launch_cheb_step(L.view, u, L.d, L.r, c.alpha[m], c.beta[m], write_d, s));
+  }
+  return SR_OK;
+}
+
+// FASMGV on global level g (Fig. "FAS multigrid V-cycle"); u is L.u (or the
+// caller's u on the finest plain level).
+int vcycle_global(sr_fmg_s* h, int g, double* u, FieldView rhs, cudaStream_t s) {
+  Level& L = h->glev[g];
+  if (g == 0) {
+    CK(launch_coarse_solve(L.view, h->minv, rhs, u, s));
+    return SR_OK;
+  }
+  Level& C = h->glev[g - 1];
+  int rc = smooth(L, h->pre, u, rhs, s);
+  if (rc) return rc;
+  CK(launch_resid_restrict(L.view, u, rhs, C.view, C.u, C.rho, s));
+  CK(launch_coarse_rhs(C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
+  rc = vcycle_global(h, g - 1, C.u, view_global(C, C.rhs), s);
+  if (rc) return rc;
+  CK(launch_prolong(C.view, C.u, C.t, L.view, u, 1, s));
+  return smooth(L, h->post, u, rhs, s);
+}
+
+// the f hierarchy, FMG over the global levels (Fig. "Full multigrid")
+int run_fmg_global(sr_fmg_s* h, const double* ftop, double* utop, cudaStream_t s) {
+  const int top = h->G - 1;
+  auto fg = [&](int g) -> const double* { return (g == top && !h->K) ? ftop : h->glev[g].f; };
+  auto ug = [&](int g) -> double* { return (g == top && !h->K) ? utop : h->glev[g].u; };
+  CK(launch_coarse_solve(h->glev[0].view, h->minv, view_global(h->glev[0], fg(0)), ug(0), s));
+  for (int g = 1; g <= top; ++g) {
+    Level& L = h->glev[g];
+    CK(launch_prolong(h->glev[g - 1].view, ug(g - 1), nullptr, L.view, ug(g), 0, s));
+    FieldView f = view_global(L, fg(g));
+    int rc = smooth(L, h->fmg, ug(g), f, s);
+    if (rc) return rc;
+    rc = vcycle_global(h, g, ug(g), f, s);
+    if (rc) return rc;
+  }
+  return SR_OK;
+}
+
+int f_hierarchy(sr_fmg_s* h, const double* f, cudaStream_t s) {
+  const double* src = f;
+  int nsrc = h->cfg.n;
+  int check = 1;
+  for (int k = h->K - 1; k >= 1; --k) {
+    CK(launch_restrict_global(nsrc, src, h->slev[k].f, check, h->status, s));
+    check = 0;
+    src = h->slev[k].f;
+    nsrc = h->slev[k].n;
+  }
+  for (int g = h->G - (h->K ? 1 : 2); g >= 0; --g) {
+    CK(launch_restrict_global(nsrc, src, h->glev[g].f, check, h->status, s));
+    check = 0;
+    src = h->glev[g].f;
+    nsrc = h->glev[g].n;
+  }
+  return SR_OK;
+}
+
+int run_sr(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
+  const int K = h->K;
+  Level& L0 = h->glev[h->G - 1];
+  auto fview = [&](int k) -> FieldView {
+    return view_global(h->slev[k], k == K ? f : h->slev[k].f);
+  };
+  for (int k = 1; k <= K; ++k) {
+    Level& Lk = h->slev[k];
+    // u_k <- Pi u_{k-1} on Omega^C_k u Omega^GSR_k, then S^alpha on Omega^C_k
+    {
+      const Level& C = (k == 1) ? L0 : h->slev[k - 1];
+      CK(launch_prolong(C.view, C.u, nullptr, Lk.view, Lk.u, 0, s));
+      int rc = smooth(Lk, h->fmg, Lk.u, fview(k), s);
+      if (rc) return rc;
+    }
+    // FASMGVSR(k): down-leg
+    for (int j = k; j >= 1; --j) {
+      Level& Lj = h->slev[j];
+      const FieldView rhs = (j == k) ? fview(k) : view_boxes(Lj, Lj.rhs);
+      int rc = smooth(Lj, h->pre, Lj.u, rhs, s);
+      if (rc) return rc;
+      if (j > 1) {
+        Level& C = h->slev[j - 1];
+        CK(launch_resid_restrict(Lj.view, Lj.u, rhs, C.view, C.u, C.rho, s));
+        CK(launch_coarse_rhs(C.view, Lj.view, C.u, C.rho, C.rhs, C.t, s));
+      } else {
+        CK(launch_resid_restrict(Lj.view, Lj.u, rhs, L0.view, L0.t, L0.rho, s));
+      }
+    }
+    // transition level: u_0 <- \hat I u_1, t_0 = u_0, r_0 = rho_0 + L_0 u_0, FASMGV
+    CK(launch_transition_rhs(L0.view, L0.t, L0.rho, L0.u, L0.rhs, s));
+    int rc = vcycle_global(h, h->G - 1, L0.u, view_global(L0, L0.rhs), s);
+    if (rc) return rc;
+    // up-leg
+    for (int j = 1; j <= k; ++j) {
+      Level& Lj = h->slev[j];
+      const Level& C = (j == 1) ? L0 : h->slev[j - 1];
+      CK(launch_prolong(C.view, C.u, C.t, Lj.view, Lj.u, 1, s));
+      const FieldView rhs = (j == k) ? fview(k) : view_boxes(Lj, Lj.rhs);
+      rc = smooth(Lj, h->post, Lj.u, rhs, s);
+      if (rc) return rc;
+    }
+  }
+  CK(launch_gather_genuine(h->slev[K].view, h->slev[K].u, u, s));
+  return SR_OK;
+}
+
+int enqueue_solve(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
+  CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned int), s));
+  int rc = f_hierarchy(h, f, s);
+  if (rc) return rc;
+  rc = run_fmg_global(h, f, u, s);
+  if (rc) return rc;
+  if (h->K) rc = run_sr(h, f, u, s);
+  return rc;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void free_all(sr_fmg_s* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+void sr_fmg_default_config(sr_fmg_config* cfg, int n) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->n = n;
+  cfg->n_coarse = 0;
+  cfg->seg = 0;
+  cfg->K = 0;
+  cfg->A = 8;
+  cfg->B = 0;
+  cfg->use_J = 0;
+  cfg->alpha = 1;
+  cfg->nu1 = 2;
+  cfg->nu2 = 2;
+  cfg->cheb_lo = 1.0 / 6.0;
+  cfg->cheb_hi = 1.0;
+  cfg->precision = SR_FP64;
+  cfg->n_outer = 0;
+}
+
+int sr_fmg_create(sr_fmg_t* out, const sr_fmg_config* cfg) {
+  if (!out) return SR_ERR_INVALID;
+  *out = nullptr;
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return SR_ERR_NO_DEVICE;
+  }
+  sr_fmg_s* h = new (std::nothrow) sr_fmg_s();
+  if (!h) return SR_ERR_OOM;
+  h->cfg = *cfg;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return SR_ERR_CUDA;
+  }
+  h->K = (cfg->seg > 0) ? cfg->K : 0;
+  h->pre = chebyshev(cfg->nu1, cfg->cheb_lo, cfg->cheb_hi);
+  h->post = chebyshev(cfg->nu2, cfg->cheb_lo, cfg->cheb_hi);
+  h->fmg = chebyshev(cfg->alpha, cfg->cheb_lo, cfg->cheb_hi);
+  rc = dalloc(h, &h->status, 1);
+  if (!rc) rc = build_global_levels(h, cfg->n >> h->K, h->K == 0);
+  if (!rc && h->K) rc = build_sr_levels(h);
+  if (rc) {
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return SR_OK;
+}
+
+int sr_fmg_destroy(sr_fmg_t h) {
+  if (!h) return SR_OK;
+  DeviceGuard g(h->device);
+  free_all(h);
+  delete h;
+  return SR_OK;
+}
+
+int sr_fmg_workspace_bytes(sr_fmg_t h, size_t* bytes) {
+  if (!h || !bytes) return SR_ERR_INVALID;
+  *bytes = h->bytes;
+  return SR_OK;
+}
+
+int sr_fmg_solve_async(sr_fmg_t h, const double* f_dev, double* u_dev, void* stream) {
+  if (!h || !f_dev || !u_dev) return SR_ERR_INVALID;
+  const size_t n = (size_t)h->cfg.n;
+  const char* fa = (const char*)f_dev;
+  const char* ua = (const char*)u_dev;
+  const size_t bytes = n * n * n * sizeof(double);
+  if (fa < ua + bytes && ua < fa + bytes) return SR_ERR_INVALID;
+  if (!is_device_ptr(f_dev) || !is_device_ptr(u_dev)) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  return enqueue_solve(h, f_dev, u_dev, (cudaStream_t)stream);
+}
+
+int sr_fmg_check(sr_fmg_t h, void* stream) {
+  if (!h) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned int st = 0;
+  CK(cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st & 1u) return SR_ERR_NONFINITE;
+  if (st & 2u) return SR_ERR_TIMEOUT;
+  return SR_OK;
+}
+
+int sr_fmg_solve(sr_fmg_t h, const double* f_dev, double* u_dev, void* stream) {
+  int rc = sr_fmg_solve_async(h, f_dev, u_dev, stream);
+  if (rc) return rc;
+  return sr_fmg_check(h, stream);
+}
+
+int sr_fmg_solve_host(sr_fmg_t h, const double* f_host, double* u_host, void* stream) {
+  if (!h || !f_host || !u_host) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  const size_t n = (size_t)h->cfg.n;
+  const size_t bytes = n * n * n * sizeof(double);
+  if (!h->hbuf_f) {
+    int rc = dalloc(h, &h->hbuf_f, n * n * n);
+    if (!rc) rc = dalloc(h, &h->hbuf_u, n * n * n);
+    if (rc) return rc;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->hbuf_f, f_host, bytes, cudaMemcpyHostToDevice, s));
+  int rc = enqueue_solve(h, h->hbuf_f, h->hbuf_u, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(u_host, h->hbuf_u, bytes, cudaMemcpyDeviceToHost, s));
+  return sr_fmg_check(h, stream);
+}
+
+const char* sr_fmg_status_string(int status) {
+  switch (status) {
+    case SR_OK: return "ok";
+    case SR_ERR_INVALID: return "invalid argument or configuration";
+    case SR_ERR_UNSUPPORTED_SIZE: return "unsupported grid size";
+    case SR_ERR_OOM: return "out of memory";
+    case SR_ERR_CUDA: return "CUDA error";
+    case SR_ERR_TIMEOUT: return "device wait timed out";
+    case SR_ERR_NONFINITE: return "right-hand side is not finite";
+    case SR_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown status";
+  }
+}
+
+// ---------------------------------------------------------------------------
+// single components on whole grids
+
+namespace {
+
+struct TmpLevel {
+  sr_fmg_s h;
+  Level L;
+  ~TmpLevel() { free_all(&h); }
+};
+
+int tmp_level(TmpLevel& T, int n) {
+  T.L.n = n;
+  T.L.hboxes.assign(1, whole_box(n));
+  return finish_level(&T.h, T.L);
+}
+
+bool dev_ok(const void* p) { return p && is_device_ptr(p); }
+
+}  // namespace
+
+int sr_op_apply(int n, const double* u, double* out, void* stream) {
+  if (n < 1 || !dev_ok(u) || !dev_ok(out)) return SR_ERR_INVALID;
+  TmpLevel T;
+  int rc = tmp_level(T, n);
+  if (rc) return rc;
+  CK(launch_apply(T.L.view, u, out, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return SR_OK;
+}
+
+int sr_op_residual(int n, const double* f, const double* u, double* r, void* stream) {
+  if (n < 1 || !dev_ok(f) || !dev_ok(u) || !dev_ok(r)) return SR_ERR_INVALID;
+  TmpLevel T;
+  int rc = tmp_level(T, n);
+  if (rc) return rc;
+  CK(launch_residual(T.L.view, u, view_global(T.L, f), r, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return SR_OK;
+}
+
+int sr_op_smooth(int n, int nu, double cheb_lo, double cheb_hi, const double* f, double* u,
+                 void* stream) {
+  if (n < 1 || nu < 0 || nu > 16 || !dev_ok(f) || !dev_ok(u)) return SR_ERR_INVALID;
+  if (!(cheb_lo > 0.0 && cheb_hi > cheb_lo)) return SR_ERR_INVALID;
+  TmpLevel T;
+  int rc = tmp_level(T, n);
+  const size_t cells = (size_t)n * n * n;
+  if (!rc) rc = dalloc(&T.h, &T.L.r, cells);
+  if (!rc) rc = dalloc(&T.h, &T.L.d, cells);
+  if (rc) return rc;
+  Cheb c = chebyshev(nu, cheb_lo, cheb_hi);
+  rc = smooth(T.L, c, u, view_global(T.L, f), (cudaStream_t)stream);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return SR_OK;
+}
+
+int sr_op_restrict(int n, const double* a, double* ac, void* stream) {
+  if (n < 2 || n % 2 || !dev_ok(a) || !dev_ok(ac)) return SR_ERR_INVALID;
+  TmpLevel T;
+  int rc = dalloc(&T.h, &T.h.status, 1);
+  if (rc) return rc;
+  CK(launch_restrict_global(n, a, ac, 0, T.h.status, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return SR_OK;
+}
+
+int sr_op_prolong(int nc, const double* ac, double* af, void* stream) {
+  if (nc < 1 || !dev_ok(ac) || !dev_ok(af)) return SR_ERR_INVALID;
+  TmpLevel C, F;
+  int rc = tmp_level(C, nc);
+  if (!rc) rc = tmp_level(F, 2 * nc);
+  if (rc) return rc;
+  CK(launch_prolong(C.L.view, ac, nullptr, F.L.view, af, 0, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return SR_OK;
+}
+
+int sr_op_coarse_solve(int n, const double* f, double* u, void* stream) {
+  if (n < 1 || n > 8 || !dev_ok(f) || !dev_ok(u)) return SR_ERR_INVALID;
+  TmpLevel T;
+  int rc = tmp_level(T, n);
+  if (rc) return rc;
+  std::vector<double> minv = coarsest_inverse(n);
+  double* dm = nullptr;
+  rc = dalloc(&T.h, &dm, minv.size());
+  if (rc) return rc;
+  CK(cudaMemcpy(dm, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(launch_coarse_solve(T.L.view, dm, view_global(T.L, f), u, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return SR_OK;
+}
+
+int sr_op_vcycle(const sr_fmg_config* cfg, const double* f, double* u, void* stream) {
+  if (!cfg || !dev_ok(f) || !dev_ok(u)) return SR_ERR_INVALID;
+  sr_fmg_config c = *cfg;
+  c.seg = 0;
+  c.K = 0;
+  sr_fmg_t h = nullptr;
+  int rc = sr_fmg_create(&h, &c);
+  if (rc) return rc;
+  const int top = h->G - 1;
+  rc = vcycle_global(h, top, u, view_global(h->glev[top], f), (cudaStream_t)stream);
+  if (!rc && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = SR_ERR_CUDA;
+  sr_fmg_destroy(h);
+  return rc;
+}
+
+}  // extern "C"

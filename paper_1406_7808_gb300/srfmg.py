@@ -1,0 +1,303 @@
+"""Thin Python binding of the C ABI in include/srfmg.h (ctypes; argument
+marshalling only -- every step of the solve runs in the CUDA library).
+
+Device arrays are torch float64 CUDA tensors of shape (n, n, n), contiguous,
+index order [z][y][x]; work is queued on torch's current CUDA stream.  The
+library is loaded on first use; a missing or unloadable library raises
+RuntimeError (there is no fallback path).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAXK = 12
+
+SR_OK = 0
+SR_ERR_INVALID = -1
+SR_ERR_UNSUPPORTED_SIZE = -2
+SR_ERR_OOM = -3
+SR_ERR_CUDA = -4
+SR_ERR_TIMEOUT = -5
+SR_ERR_NONFINITE = -6
+SR_ERR_NO_DEVICE = -7
+
+SR_FP64 = 0
+SR_MIXED = 1
+
+
+class SRFMGError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class Config(ctypes.Structure):
+    """Mirror of sr_fmg_config."""
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("n_coarse", ctypes.c_int),
+        ("seg", ctypes.c_int),
+        ("K", ctypes.c_int),
+        ("A", ctypes.c_int),
+        ("B", ctypes.c_int),
+        ("use_J", ctypes.c_int),
+        ("J", ctypes.c_int * MAXK),
+        ("alpha", ctypes.c_int),
+        ("nu1", ctypes.c_int),
+        ("nu2", ctypes.c_int),
+        ("cheb_lo", ctypes.c_double),
+        ("cheb_hi", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("n_outer", ctypes.c_int),
+    ]
+
+
+_LIB = None
+_VP = ctypes.c_void_p
+
+
+def library_path():
+    return _build.LIBRARY
+
+
+def load():
+    """Load the CUDA library (raises RuntimeError if it is not built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    lib.sr_fmg_default_config.argtypes = [ctypes.POINTER(Config), ctypes.c_int]
+    lib.sr_fmg_default_config.restype = None
+    lib.sr_fmg_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(Config)]
+    lib.sr_fmg_destroy.argtypes = [_VP]
+    lib.sr_fmg_workspace_bytes.argtypes = [_VP, ctypes.POINTER(ctypes.c_size_t)]
+    for name in ("sr_fmg_solve", "sr_fmg_solve_async", "sr_fmg_solve_host"):
+        getattr(lib, name).argtypes = [_VP, _VP, _VP, _VP]
+    lib.sr_fmg_check.argtypes = [_VP, _VP]
+    lib.sr_fmg_status_string.argtypes = [ctypes.c_int]
+    lib.sr_fmg_status_string.restype = ctypes.c_char_p
+    lib.sr_op_apply.argtypes = [ctypes.c_int, _VP, _VP, _VP]
+    lib.sr_op_residual.argtypes = [ctypes.c_int, _VP, _VP, _VP, _VP]
+    lib.sr_op_smooth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                 _VP, _VP, _VP]
+    lib.sr_op_restrict.argtypes = [ctypes.c_int, _VP, _VP, _VP]
+    lib.sr_op_prolong.argtypes = [ctypes.c_int, _VP, _VP, _VP]
+    lib.sr_op_coarse_solve.argtypes = [ctypes.c_int, _VP, _VP, _VP]
+    lib.sr_op_vcycle.argtypes = [ctypes.POINTER(Config), _VP, _VP, _VP]
+    _LIB = lib
+    return lib
+
+
+def status_string(status):
+    try:
+        return load().sr_fmg_status_string(int(status)).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def _check(status, what):
+    if status != SR_OK:
+        raise SRFMGError(status, what)
+
+
+def buffer_schedule(A, B, K):
+    """J_k = 2 floor((A + B (K - k)) / 2), k = 1..K (Eq. eq:nb)."""
+    return [2 * ((A + B * (K - k)) // 2) for k in range(1, K + 1)]
+
+
+def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, nu2=2,
+                cheb_lo=1.0 / 6.0, cheb_hi=1.0, precision=SR_FP64, n_outer=0):
+    c = Config()
+    load().sr_fmg_default_config(ctypes.byref(c), int(n))
+    c.n_coarse, c.seg, c.K, c.A, c.B = n_coarse, seg, K, A, B
+    if J is not None:
+        if len(J) != K:
+            raise ValueError("J must have K entries")
+        c.use_J = 1
+        for i, v in enumerate(J):
+            c.J[i] = int(v)
+    c.alpha, c.nu1, c.nu2 = alpha, nu1, nu2
+    c.cheb_lo, c.cheb_hi = cheb_lo, cheb_hi
+    c.precision, c.n_outer = precision, n_outer
+    return c
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, n=None, name="array"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dim() != 3 or len(set(t.shape)) != 1 or (n is not None and t.shape[0] != n):
+        raise ValueError(f"{name} must have shape (n, n, n)")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One sr_fmg_t handle: plan and device workspace for one configuration."""
+
+    def __init__(self, n, **kw):
+        self.config = make_config(n, **kw)
+        self.n = int(n)
+        h = _VP()
+        _check(load().sr_fmg_create(ctypes.byref(h), ctypes.byref(self.config)), "sr_fmg_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sr_fmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def workspace_bytes(self):
+        b = ctypes.c_size_t()
+        _check(load().sr_fmg_workspace_bytes(self._h, ctypes.byref(b)), "workspace_bytes")
+        return b.value
+
+    def solve(self, f, out=None):
+        """u = solver(f) for a float64 CUDA tensor f; waits and checks status."""
+        import torch
+        if out is None:
+            out = torch.empty_like(f)
+        _check(load().sr_fmg_solve(self._h, _dev(f, self.n, "f"), _dev(out, self.n, "u"),
+                                   _stream()), "sr_fmg_solve")
+        return out
+
+    def solve_async(self, f, out):
+        _check(load().sr_fmg_solve_async(self._h, _dev(f, self.n, "f"), _dev(out, self.n, "u"),
+                                         _stream()), "sr_fmg_solve_async")
+        return out
+
+    def check(self):
+        _check(load().sr_fmg_check(self._h, _stream()), "sr_fmg_check")
+
+    def solve_host(self, f, out=None):
+        """End-to-end solve of a host array (numpy float64 (n, n, n) or a CPU
+        tensor); the copies to and from the device run inside the library."""
+        if hasattr(f, "numpy"):
+            f = f.numpy()
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (self.n,) * 3:
+            raise ValueError("f must have shape (n, n, n)")
+        if out is None:
+            out = np.empty_like(f)
+        fp = ctypes.c_void_p(f.ctypes.data)
+        up = ctypes.c_void_p(out.ctypes.data) if isinstance(out, np.ndarray) else \
+            ctypes.c_void_p(out.data_ptr())
+        _check(load().sr_fmg_solve_host(self._h, fp, up, _stream()), "sr_fmg_solve_host")
+        return out
+
+
+# ---- single components on whole grids (for parity tests) ----
+
+def op_apply(u):
+    import torch
+    out = torch.empty_like(u)
+    _check(load().sr_op_apply(u.shape[0], _dev(u), _dev(out), _stream()), "sr_op_apply")
+    return out
+
+
+def op_residual(u, f):
+    import torch
+    r = torch.empty_like(u)
+    _check(load().sr_op_residual(u.shape[0], _dev(f), _dev(u), _dev(r), _stream()),
+           "sr_op_residual")
+    return r
+
+
+def op_smooth(u, f, nu, cheb_lo=1.0 / 6.0, cheb_hi=1.0):
+    """Chebyshev smoother; returns a new tensor (u is not modified)."""
+    u = u.clone()
+    _check(load().sr_op_smooth(u.shape[0], nu, cheb_lo, cheb_hi, _dev(f), _dev(u), _stream()),
+           "sr_op_smooth")
+    return u
+
+
+def op_restrict(a):
+    import torch
+    n = a.shape[0]
+    out = torch.empty((n // 2,) * 3, dtype=a.dtype, device=a.device)
+    _check(load().sr_op_restrict(n, _dev(a), _dev(out), _stream()), "sr_op_restrict")
+    return out
+
+
+def op_prolong(ac):
+    import torch
+    nc = ac.shape[0]
+    out = torch.empty((2 * nc,) * 3, dtype=ac.dtype, device=ac.device)
+    _check(load().sr_op_prolong(nc, _dev(ac), _dev(out), _stream()), "sr_op_prolong")
+    return out
+
+
+def op_coarse_solve(f):
+    import torch
+    u = torch.empty_like(f)
+    _check(load().sr_op_coarse_solve(f.shape[0], _dev(f), _dev(u), _stream()),
+           "sr_op_coarse_solve")
+    return u
+
+
+def op_vcycle(f, u, **kw):
+    """One FAS V-cycle; returns a new tensor."""
+    u = u.clone()
+    c = make_config(f.shape[0], **kw)
+    _check(load().sr_op_vcycle(ctypes.byref(c), _dev(f), _dev(u), _stream()), "sr_op_vcycle")
+    return u
+
+
+def _autograd_function():
+    import torch
+
+    class SRFMGFunction(torch.autograd.Function):
+        """u = S(f) with S the (SR-)FMG solve; backward returns S(dL/du).
+
+        A is symmetric, so the derivative of the exact discrete solution
+        A^-1 f is A^-1 g; the backward pass approximates it with a second
+        solve on g.  S itself is linear but not symmetric (the cycle is not),
+        so S(g) differs from the exact derivative of the algorithm, S^T g, by
+        the order of the algebraic error."""
+
+        @staticmethod
+        def forward(ctx, f, solver):
+            ctx.solver = solver
+            return solver.solve(f.contiguous())
+
+        @staticmethod
+        def backward(ctx, g):
+            return ctx.solver.solve(g.contiguous()), None
+
+    return SRFMGFunction
+
+
+_FN = None
+
+
+def solve_autograd(f, solver):
+    """Differentiable solve: u = S(f), with dL/df = S(dL/du)."""
+    global _FN
+    if _FN is None:
+        _FN = _autograd_function()
+    return _FN.apply(f, solver)

@@ -20,3 +20,15 @@ def oracle_mod():
     import oracle
     oracle._lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The CUDA library and torch on cuda:0; fails (does not skip) without a GPU."""
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1406_7808_gb300 import build, srfmg
+    build.build()
+    srfmg.load()
+    torch.cuda.set_device(0)
+    return srfmg

@@ -1,0 +1,133 @@
+"""Parity of the full CUDA FMG / SR-FMG solve with the oracle through the C
+ABI (FP64, 1e-11 relative max-norm), on small geometries that span several
+blocks and clipped segment boxes, and on the full 256^3 SR configuration the
+benchmark times; plus the error behaviour of the boundary."""
+import numpy as np
+import pytest
+
+from paper_1406_7808_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def T(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_solve(gpu, f, **kw):
+    with gpu.Solver(f.shape[0], **kw) as s:
+        return s.solve(T(f)).cpu().numpy()
+
+
+@pytest.mark.parametrize("n,kw", [
+    (2, {}), (3, {}), (4, {}), (8, {}), (16, {}), (24, {}), (32, {}), (48, {}), (64, {}),
+    (96, {}), (128, {}),
+    (32, dict(n_coarse=4)), (64, dict(n_coarse=8)), (32, dict(alpha=2, nu1=3, nu2=1)),
+    (32, dict(cheb_lo=0.1, cheb_hi=1.1)),
+])
+def test_plain_fmg_parity(gpu, oracle_mod, n, kw):
+    f, _ = inputs.manufactured(n, 0)
+    assert rel(gpu_solve(gpu, f, **kw), oracle_mod.solve(f, **kw)) < TOL
+
+
+SR_CASES = [
+    (16, dict(seg=8, K=1, J=[2])),
+    (32, dict(seg=8, K=2, J=[4, 4])),
+    (32, dict(seg=16, K=2, J=[2, 4])),
+    (32, dict(seg=8, K=3, J=[6, 4, 4])),
+    (24, dict(seg=12, K=2, J=[2, 2])),
+    (48, dict(seg=16, K=2, J=[4, 2])),
+    (32, dict(seg=8, K=2, J=[0, 0])),
+    (32, dict(seg=32, K=2, A=4, B=1)),
+    (64, dict(seg=16, K=2, A=4, B=1)),
+    (64, dict(seg=32, K=3, A=8, B=0)),
+    (64, dict(seg=16, K=2, A=8, B=0, n_coarse=4)),
+    (128, dict(seg=32, K=3, A=8, B=0)),
+    (96, dict(seg=24, K=3, A=6, B=0)),
+]
+
+
+def _oracle_kw(kw):
+    kw = dict(kw)
+    if "J" not in kw:
+        kw.setdefault("A", 8)
+        kw.setdefault("B", 0)
+    return kw
+
+
+@pytest.mark.parametrize("n,kw", SR_CASES)
+def test_sr_fmg_parity(gpu, oracle_mod, n, kw):
+    f, _ = inputs.manufactured(n, 1)
+    ref = oracle_mod.solve(f, **_oracle_kw(kw))
+    assert rel(gpu_solve(gpu, f, **kw), ref) < TOL
+
+
+def test_sr_fmg_parity_full_size(gpu, oracle_mod):
+    """The benchmark's workload: 256^3, 32^3-cell segments (512), K = 3,
+    buffers A = 8, B = 0; every cell compared with the oracle."""
+    n = 256
+    kw = dict(seg=32, K=3, A=8, B=0)
+    f, uex = inputs.manufactured(n, 0)
+    ref = oracle_mod.solve(f, **kw)
+    u = gpu_solve(gpu, f, **kw)
+    assert rel(u, ref) < TOL
+    plain = oracle_mod.solve(f)
+    e_r = np.abs(u - uex).max() / np.abs(plain - uex).max()
+    assert 0.99 < e_r < 1.2
+
+
+def test_repeated_solves_identical(gpu):
+    n = 64
+    f, _ = inputs.manufactured(n, 3)
+    with gpu.Solver(n, seg=16, K=2) as s:
+        a = s.solve(T(f)).cpu().numpy()
+        b = s.solve(T(f)).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_solve_host_matches_device(gpu):
+    n = 64
+    f, _ = inputs.manufactured(n, 4)
+    with gpu.Solver(n, seg=16, K=2) as s:
+        a = s.solve(T(f)).cpu().numpy()
+        b = s.solve_host(f)
+    assert np.array_equal(a, b)
+
+
+def test_nonfinite_rhs_reported(gpu):
+    import torch
+    n = 32
+    f, _ = inputs.manufactured(n, 0)
+    f[3, 4, 5] = np.nan
+    with gpu.Solver(n, seg=8, K=2) as s:
+        with pytest.raises(gpu.SRFMGError) as e:
+            s.solve(T(f))
+        assert e.value.status == gpu.SR_ERR_NONFINITE
+        f[3, 4, 5] = 0.0
+        s.solve(T(f))  # the handle stays usable
+        g = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+        g[0, 0, 0] = float("inf")
+        with pytest.raises(gpu.SRFMGError):
+            s.solve(g)
+
+
+def test_host_pointer_rejected(gpu):
+    import ctypes
+    n = 16
+    f = np.zeros((n, n, n))
+    u = np.zeros((n, n, n))
+    with gpu.Solver(n) as s:
+        st = gpu.load().sr_fmg_solve(s._h, ctypes.c_void_p(f.ctypes.data),
+                                     ctypes.c_void_p(u.ctypes.data), None)
+    assert st == gpu.SR_ERR_INVALID
+
+
+def test_workspace_reported(gpu):
+    with gpu.Solver(64, seg=16, K=2) as s:
+        assert s.workspace_bytes > 64 ** 3 * 8
