@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark: segmental-refinement FMG (FP64) on a 256^3 Poisson problem.
+
+One step = one full SR-FMG solve (every step of the method: f hierarchy,
+global FMG to the transition level, K = 3 SR stages over 512 segments of 32^3
+genuine cells with J = 8 buffer cells per side, output) of A u = f with the
+seeded manufactured right-hand side.  Metric: fine-grid DOF/s = n^3 / time
+per solve (whole job: all ranks' DOF over the slowest rank's time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Rank 0 prints one JSON line.  --impl reference times the CPU oracle (the
+plain C implementation the tests compare with) on this host's cores instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "3D Poisson FMG fine-grid DOF/s, SR vs plain, at discretization error; %HBM peak"
+N = 256
+SR = dict(seg=32, K=3, A=8, B=0)
+SEED = 0
+# float64 lanes per clock per SM (two FMA-capable lanes) x SMs x max SM clock
+FP64_LANES_PER_CLK_SM = 2
+GB300_SMS = 152
+GB300_MAX_MHZ = 2070.0
+FP64_PEAK_TOPS = FP64_LANES_PER_CLK_SM * GB300_SMS * GB300_MAX_MHZ * 1e6 / 1e12
+
+
+def workload_name(n=N, sr=SR):
+    J = [2 * ((sr["A"] + sr["B"] * (sr["K"] - k)) // 2) for k in range(1, sr["K"] + 1)]
+    nseg = (n // sr["seg"]) ** 3
+    return (f"SR-FMG FP64 {n}^3 cells, {nseg} segments of {sr['seg']}^3, K={sr['K']} SR levels, "
+            f"buffers Eq.(eq:nb) A={sr['A']} B={sr['B']} (J={J}), F(1,2,2) Chebyshev, "
+            f"global levels {n >> sr['K']}^3..2^3"), J
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, min_mhz_under_load=300):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower().startswith("active")})
+        loaded = [r[0] for r in rows if r[0] >= min_mhz_under_load] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+
+def ncu_traffic(kernel):
+    """DRAM traffic per launch of `kernel` from the committed ncu summary, if
+    the kernel source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}.md")
+    src = os.path.join(ROOT, "paper_1406_7808_gb300", "csrc", "kernels_fp64.cu")
+    if not os.path.exists(path) or not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernels_fp64.cu sha256[:16]") != sha:
+        return None
+    try:
+        return float(vals["dram bytes per launch (scaled to the bench workload)"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(f, min_seconds=10.0, max_solves=6):
+    """The oracle, as it stands, timed on this host's cores (full solves of
+    the same workload until about min_seconds of work)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    times, u = [], None
+    t_start = time.perf_counter()
+    while len(times) < max_solves:
+        t0 = time.perf_counter()
+        u = oracle.solve(f, n_threads=threads, **SR)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start >= min_seconds:
+            break
+    mean = sum(times) / len(times)
+    return u, {"value": N ** 3 / mean, "unit": "DOF/s", "cores": threads, "kind": "oracle",
+               "sample": f"{len(times)} full {N}^3 SR-FMG oracle solves (same f and geometry), "
+                         f"OpenMP over segments, mean {mean:.2f} s per solve"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_1406_7808_gb300 import inputs
+    from oracle import build as oracle_build
+    oracle_build.build()
+    threads = os.cpu_count() or 1
+    f, _ = inputs.manufactured(N, SEED)
+    name, J = workload_name()
+    # a step is one full solve unless the whole run would take too long, then
+    # the same segment geometry on a 128^3 grid (1/8 of the work)
+    t0 = time.perf_counter()
+    oracle.solve(f, n_threads=threads, **SR)
+    t_full = time.perf_counter() - t0
+    n_step, fs = N, f
+    if (args.steps + args.warmup) * t_full > 180.0:
+        n_step = N // 2
+        fs, _ = inputs.manufactured(n_step, SEED)
+    for _ in range(max(args.warmup - 1, 0)):
+        oracle.solve(fs, n_threads=threads, **SR)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve(fs, n_threads=threads, **SR)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = n_step ** 3 / dt
+    sample = (f"one full {n_step}^3 SR-FMG oracle solve per step "
+              f"({'the workload itself' if n_step == N else 'same segment geometry at 1/8 size'})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "n": N, **SR, "J": J},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1406_7808_gb300 import build, inputs, srfmg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # replicas: every rank solves its own instance (seeded by rank); no data
+    # is exchanged between ranks
+    f, u_exact = inputs.manufactured(N, SEED + rank)
+    ft = torch.from_numpy(f).cuda()
+    ut = torch.empty_like(ft)
+    name, J = workload_name()
+    stream = torch.cuda.current_stream()
+
+    def timed(solver, steps, sampler=None):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ctx = sampler if sampler is not None else _Null()
+        with ctx:
+            e0.record(stream)
+            for _ in range(steps):
+                solver.solve_async(ft, ut)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        solver.check()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1))
+
+    sr = srfmg.Solver(N, **SR)
+    for _ in range(args.warmup):
+        sr.solve_async(ft, ut)
+    sr.check()
+    u_sr = ut.cpu().numpy()
+    sampler = ClockSampler(local)
+    total_ms = timed(sr, args.steps, sampler)
+    clocks = sampler.summary()
+    ms = total_ms / args.steps
+    value = world * N ** 3 / (ms / 1e3)
+    launches = sr.launches_per_solve
+
+    # per-kernel device times (a profiled repeat of the timed loop)
+    sr.profile(True)
+    for _ in range(args.steps):
+        sr.solve_async(ft, ut)
+    sr.check()
+    prof = sr.profile_read()
+    sr.profile(False)
+    dominant = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dominant]
+    achieved = d["fp64_ops"] / (d["ms"] / 1e3) / 1e12
+    hbm_peak = None
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, ValueError, KeyError):
+        pass
+    roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved,
+                "peak": FP64_PEAK_TOPS, "unit": "TFP64op/s", "frac": achieved / FP64_PEAK_TOPS,
+                "traffic": ncu_traffic(dominant),
+                "peak_note": "float64 pipe: 2 lanes/clk/SM x 152 SMs x 2070 MHz (derived)",
+                "launches": d["launches"] // args.steps,
+                "fp64_ops_per_launch": d["fp64_ops"] / d["launches"],
+                "ms_per_launch": d["ms"] / d["launches"],
+                "hbm_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9,
+                "hbm_frac_of_measured": (d["bytes"] / (d["ms"] / 1e3) / 1e9 / hbm_peak)
+                if hbm_peak else None}
+    kernels = {k: {"ms_per_solve": v["ms"] / args.steps,
+                   "share": v["ms"] / sum(x["ms"] for x in prof.values()),
+                   "tfp64ops": v["fp64_ops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] else None}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # the same solve without segmental refinement (plain FMG), same f
+    plain = srfmg.Solver(N)
+    for _ in range(args.warmup):
+        plain.solve_async(ft, ut)
+    plain.check()
+    u_plain = ut.cpu().numpy()
+    plain_ms = timed(plain, args.steps) / args.steps
+    plain.close()
+
+    # end to end through the C ABI from pinned host memory
+    fh = torch.from_numpy(f).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    sr.solve_host(fh.numpy(), uh.numpy())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sr.solve_host(fh.numpy(), uh.numpy())
+    e2e_s = max_over_ranks(time.perf_counter() - t0) / args.steps
+    sr.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # accuracy at discretisation level
+    acc = {}
+    try:
+        from scipy.fft import dstn, idstn
+        k = np.arange(1, N + 1)
+        l1 = 4.0 * N * N * np.sin(k * np.pi / (2.0 * N)) ** 2
+        lam = l1[:, None, None] + l1[None, :, None] + l1[None, None, :]
+        u_h = idstn(dstn(f, type=2, workers=os.cpu_count()) / lam, type=2,
+                    workers=os.cpu_count())
+        acc["e_disc"] = float(np.abs(u_h - u_exact).max())
+        acc["e_alg_sr"] = float(np.abs(u_sr - u_h).max())
+        acc["e_alg_plain"] = float(np.abs(u_plain - u_h).max())
+    except ImportError:
+        pass
+    acc["e_sr"] = float(np.abs(u_sr - u_exact).max())
+    acc["e_plain"] = float(np.abs(u_plain - u_exact).max())
+    acc["e_r"] = acc["e_sr"] / acc["e_plain"]
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        u_or, cpu = cpu_baseline(f)
+        acc["max_rel_diff_vs_oracle"] = float(np.abs(u_sr - u_or).max() / np.abs(u_or).max())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "n": N, **SR, "J": J,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2: f is 134 MB and each solve sweeps 2.2 GB of "
+                         "workspace",
+                   "plain_fmg_dof_s": world * N ** 3 / (plain_ms / 1e3),
+                   "plain_fmg_ms_per_step": plain_ms},
+        "e2e": {"value": world * N ** 3 / e2e_s, "unit": "DOF/s",
+                "h2d_bytes_per_step": N ** 3 * 8, "d2h_bytes_per_step": N ** 3 * 8},
+        "gpu_launches": launches * args.steps,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "accuracy": acc,
+        "kernels": kernels,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -128,6 +128,25 @@ int sr_fmg_check(sr_fmg_t h, void* stream);
  * locked host buffers give the fastest copies; pageable memory also works. */
 int sr_fmg_solve_host(sr_fmg_t h, const double* f_host, double* u_host, void* stream);
 
+/* Number of kernel launches the handle's last queued solve made. */
+int sr_fmg_launches_per_solve(sr_fmg_t h, int* launches);
+
+/*
+ * Per-kernel profile.  sr_fmg_profile(h, 1) clears the counters and starts
+ * bracketing every kernel launch of later solves on h with CUDA events (a few
+ * microseconds of overhead per launch); sr_fmg_profile(h, 0) stops.  Both
+ * wait for the device.  sr_fmg_profile_read waits for the recorded launches
+ * and returns, for one kernel kind (0 <= kind < sr_fmg_profile_kinds()), its
+ * name (static string), launch count, summed device time in milliseconds, and
+ * the summed algorithmic float64 operations (each add, multiply or fused
+ * multiply-add counts one) and bytes (each array element read or written once)
+ * of those launches.
+ */
+int sr_fmg_profile(sr_fmg_t h, int enable);
+int sr_fmg_profile_kinds(void);
+int sr_fmg_profile_read(sr_fmg_t h, int kind, const char** name, long long* launches,
+                        double* ms, double* fp64_ops, double* bytes);
+
 /* Human-readable name of a status code (static string). */
 const char* sr_fmg_status_string(int status);
 

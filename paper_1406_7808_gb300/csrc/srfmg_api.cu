@@ -40,6 +40,8 @@ struct Level {
   BoxDesc* dboxes = nullptr;     // device copy of hboxes
   BoxDesc* dglobal = nullptr;    // device descriptor of the whole level, unpadded
   LevelView view{};
+  // totals over the boxes, for the algorithmic work counts of the profiler
+  double tot_cells = 0, tot_prolong = 0, tot_restrict = 0, tot_genuine = 0;
   double *u = nullptr, *t = nullptr, *rhs = nullptr, *r = nullptr, *rho = nullptr,
          *d = nullptr, *f = nullptr;
 };
@@ -48,6 +50,30 @@ struct Cheb {
   int nu = 0;
   double a = 0, b = 0;            // degree-2 polynomial form
   std::vector<double> alpha, beta;  // recurrence steps
+};
+
+// kernel kinds for the per-kernel profile
+enum Kind {
+  kChebResidual, kCheb2Update, kChebStep, kResidRestrict, kCoarseRhs, kTransitionRhs,
+  kProlongSet, kProlongAdd, kCoarseSolve, kRestrictF, kGather, kApply, kKinds
+};
+const char* const kKindName[kKinds] = {
+  "cheb_residual", "cheb2_update", "cheb_step", "resid_restrict", "coarse_rhs",
+  "transition_rhs", "prolong", "prolong_correct", "coarse_solve", "restrict_f",
+  "gather_genuine", "apply"};
+
+struct ProfRec {
+  int kind;
+  double ops, bytes;
+  cudaEvent_t e0, e1;
+};
+
+struct Profile {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;  // free events
+  std::vector<ProfRec> recs;      // recorded, not yet read
+  long long launches[kKinds] = {};
+  double ms[kKinds] = {}, ops[kKinds] = {}, bytes[kKinds] = {};
 };
 
 }  // namespace
@@ -66,6 +92,8 @@ struct sr_fmg_s {
   std::vector<void*> allocs;
   double* hbuf_f = nullptr;        // device staging for sr_fmg_solve_host
   double* hbuf_u = nullptr;
+  int launches = 0;                // kernel launches queued by the last solve
+  Profile prof;
 };
 
 namespace {
@@ -74,6 +102,44 @@ namespace {
   do {                                            \
     cudaError_t e_ = (call);                      \
     if (e_ != cudaSuccess) return SR_ERR_CUDA;    \
+  } while (0)
+
+cudaEvent_t take_event(Profile& p) {
+  if (!p.pool.empty()) {
+    cudaEvent_t e = p.pool.back();
+    p.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Every kernel launch of a solve goes through here: it counts the launch and,
+// when profiling, brackets it with events and records the algorithmic float64
+// operations and bytes of the launch (units x per-unit counts).
+template <class F>
+int launch(sr_fmg_s* h, int kind, double units, double ops_per_unit, double bytes_per_unit,
+           cudaStream_t s, F&& fn) {
+  ++h->launches;
+  ProfRec rec{kind, units * ops_per_unit, units * bytes_per_unit, nullptr, nullptr};
+  if (h->prof.on) {
+    rec.e0 = take_event(h->prof);
+    rec.e1 = take_event(h->prof);
+    if (rec.e0) cudaEventRecord(rec.e0, s);
+  }
+  const cudaError_t e = fn();
+  if (h->prof.on) {
+    if (rec.e1) cudaEventRecord(rec.e1, s);
+    if (rec.e0 && rec.e1) h->prof.recs.push_back(rec);
+  }
+  return e == cudaSuccess ? SR_OK : SR_ERR_CUDA;
+}
+
+#define LAUNCH(h, kind, units, ops, bytes, s, call)                                  \
+  do {                                                                             \
+    int rc_ = launch((h), (kind), (units), (ops), (bytes), (s), [&] { return (call); }); \
+    if (rc_) return rc_;                                                           \
   } while (0)
 
 int halvings_to_coarsest(int n, int nc) {
@@ -214,6 +280,10 @@ int finish_level(sr_fmg_s* h, Level& L) {
     mx(v.max_prolong, prod(b.plo, b.phi));
     mx(v.max_restrict, prod(b.rlo, b.rhi));
     mx(v.max_genuine, prod(b.glo, b.ghi));
+    L.tot_cells += (double)prod(b.lo, b.hi);
+    L.tot_prolong += (double)prod(b.plo, b.phi);
+    L.tot_restrict += (double)prod(b.rlo, b.rhi);
+    L.tot_genuine += (double)prod(b.glo, b.ghi);
   }
   L.view = v;
   return SR_OK;
@@ -357,17 +427,22 @@ int build_sr_levels(sr_fmg_s* h) {
 FieldView view_global(const Level& L, const double* p) { return FieldView{p, L.dglobal, 1}; }
 FieldView view_boxes(const Level& L, const double* p) { return FieldView{p, L.dboxes, 0}; }
 
-int smooth(const Level& L, const Cheb& c, double* u, FieldView f, cudaStream_t s) {
+// algorithmic per-cell counts (float64 operations; bytes with each array
+// element read or written once) of each kernel
+int smooth(sr_fmg_s* h, const Level& L, const Cheb& c, double* u, FieldView f, cudaStream_t s) {
   if (c.nu == 0) return SR_OK;
+  const double cells = L.tot_cells;
   if (c.nu == 2) {
-    CK(launch_cheb_residual(L.view, u, L.r, f, s));
-    CK(launch_cheb2_update(L.view, u, L.r, c.a, c.b, s));
+    LAUNCH(h, kChebResidual, cells, 7, 24, s, launch_cheb_residual(L.view, u, L.r, f, s));
+    LAUNCH(h, kCheb2Update, cells, 7, 24, s, launch_cheb2_update(L.view, u, L.r, c.a, c.b, s));
     return SR_OK;
   }
   for (int m = 0; m < c.nu; ++m) {
-    CK(launch_cheb_residual(L.view, u, L.r, f, s));
+    LAUNCH(h, kChebResidual, cells, 7, 24, s, launch_cheb_residual(L.view, u, L.r, f, s));
     const int write_d = (c.nu > 1 && m < c.nu - 1) ? 1 : 0;
-    CK(launch_cheb_step(L.view, u, L.d, L.r, c.alpha[m], c.beta[m], write_d, s));
+    const bool with_d = write_d || c.alpha[m] != 0.0;
+    LAUNCH(h, kChebStep, cells, with_d ? 3 : 2, with_d ? 40 : 24, s,
+           launch_cheb_step(L.view, u, L.d, L.r, c.alpha[m], c.beta[m], write_d, s));
   }
   return SR_OK;
 }
@@ -377,18 +452,22 @@ int smooth(const Level& L, const Cheb& c, double* u, FieldView f, cudaStream_t s
 int vcycle_global(sr_fmg_s* h, int g, double* u, FieldView rhs, cudaStream_t s) {
   Level& L = h->glev[g];
   if (g == 0) {
-    CK(launch_coarse_solve(L.view, h->minv, rhs, u, s));
+    const double m = L.tot_cells;
+    LAUNCH(h, kCoarseSolve, m * m, 1, 8, s, launch_coarse_solve(L.view, h->minv, rhs, u, s));
     return SR_OK;
   }
   Level& C = h->glev[g - 1];
-  int rc = smooth(L, h->pre, u, rhs, s);
+  int rc = smooth(h, L, h->pre, u, rhs, s);
   if (rc) return rc;
-  CK(launch_resid_restrict(L.view, u, rhs, C.view, C.u, C.rho, s));
-  CK(launch_coarse_rhs(C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
+  LAUNCH(h, kResidRestrict, L.tot_restrict, 41, 144, s,
+         launch_resid_restrict(L.view, u, rhs, C.view, C.u, C.rho, s));
+  LAUNCH(h, kCoarseRhs, C.tot_cells, 7, 32, s,
+         launch_coarse_rhs(C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
   rc = vcycle_global(h, g - 1, C.u, view_global(C, C.rhs), s);
   if (rc) return rc;
-  CK(launch_prolong(C.view, C.u, C.t, L.view, u, 1, s));
-  return smooth(L, h->post, u, rhs, s);
+  LAUNCH(h, kProlongAdd, L.tot_prolong, 16, 18, s,
+         launch_prolong(C.view, C.u, C.t, L.view, u, 1, s));
+  return smooth(h, L, h->post, u, rhs, s);
 }
 
 // the f hierarchy, FMG over the global levels (Fig. "Full multigrid")
@@ -396,12 +475,17 @@ int run_fmg_global(sr_fmg_s* h, const double* ftop, double* utop, cudaStream_t s
   const int top = h->G - 1;
   auto fg = [&](int g) -> const double* { return (g == top && !h->K) ? ftop : h->glev[g].f; };
   auto ug = [&](int g) -> double* { return (g == top && !h->K) ? utop : h->glev[g].u; };
-  CK(launch_coarse_solve(h->glev[0].view, h->minv, view_global(h->glev[0], fg(0)), ug(0), s));
+  {
+    const double m = h->glev[0].tot_cells;
+    LAUNCH(h, kCoarseSolve, m * m, 1, 8, s,
+           launch_coarse_solve(h->glev[0].view, h->minv, view_global(h->glev[0], fg(0)), ug(0), s));
+  }
   for (int g = 1; g <= top; ++g) {
     Level& L = h->glev[g];
-    CK(launch_prolong(h->glev[g - 1].view, ug(g - 1), nullptr, L.view, ug(g), 0, s));
+    LAUNCH(h, kProlongSet, L.tot_prolong, 8, 9, s,
+           launch_prolong(h->glev[g - 1].view, ug(g - 1), nullptr, L.view, ug(g), 0, s));
     FieldView f = view_global(L, fg(g));
-    int rc = smooth(L, h->fmg, ug(g), f, s);
+    int rc = smooth(h, L, h->fmg, ug(g), f, s);
     if (rc) return rc;
     rc = vcycle_global(h, g, ug(g), f, s);
     if (rc) return rc;
@@ -414,13 +498,17 @@ int f_hierarchy(sr_fmg_s* h, const double* f, cudaStream_t s) {
   int nsrc = h->cfg.n;
   int check = 1;
   for (int k = h->K - 1; k >= 1; --k) {
-    CK(launch_restrict_global(nsrc, src, h->slev[k].f, check, h->status, s));
+    const double nc = h->slev[k].n;
+    LAUNCH(h, kRestrictF, nc * nc * nc, 8, 72, s,
+           launch_restrict_global(nsrc, src, h->slev[k].f, check, h->status, s));
     check = 0;
     src = h->slev[k].f;
     nsrc = h->slev[k].n;
   }
   for (int g = h->G - (h->K ? 1 : 2); g >= 0; --g) {
-    CK(launch_restrict_global(nsrc, src, h->glev[g].f, check, h->status, s));
+    const double nc = h->glev[g].n;
+    LAUNCH(h, kRestrictF, nc * nc * nc, 8, 72, s,
+           launch_restrict_global(nsrc, src, h->glev[g].f, check, h->status, s));
     check = 0;
     src = h->glev[g].f;
     nsrc = h->glev[g].n;
@@ -439,43 +527,51 @@ int run_sr(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
     // u_k <- Pi u_{k-1} on Omega^C_k u Omega^GSR_k, then S^alpha on Omega^C_k
     {
       const Level& C = (k == 1) ? L0 : h->slev[k - 1];
-      CK(launch_prolong(C.view, C.u, nullptr, Lk.view, Lk.u, 0, s));
-      int rc = smooth(Lk, h->fmg, Lk.u, fview(k), s);
+      LAUNCH(h, kProlongSet, Lk.tot_prolong, 8, 9, s,
+             launch_prolong(C.view, C.u, nullptr, Lk.view, Lk.u, 0, s));
+      int rc = smooth(h, Lk, h->fmg, Lk.u, fview(k), s);
       if (rc) return rc;
     }
     // FASMGVSR(k): down-leg
     for (int j = k; j >= 1; --j) {
       Level& Lj = h->slev[j];
       const FieldView rhs = (j == k) ? fview(k) : view_boxes(Lj, Lj.rhs);
-      int rc = smooth(Lj, h->pre, Lj.u, rhs, s);
+      int rc = smooth(h, Lj, h->pre, Lj.u, rhs, s);
       if (rc) return rc;
       if (j > 1) {
         Level& C = h->slev[j - 1];
-        CK(launch_resid_restrict(Lj.view, Lj.u, rhs, C.view, C.u, C.rho, s));
-        CK(launch_coarse_rhs(C.view, Lj.view, C.u, C.rho, C.rhs, C.t, s));
+        LAUNCH(h, kResidRestrict, Lj.tot_restrict, 41, 144, s,
+               launch_resid_restrict(Lj.view, Lj.u, rhs, C.view, C.u, C.rho, s));
+        LAUNCH(h, kCoarseRhs, C.tot_cells, 7, 32, s,
+               launch_coarse_rhs(C.view, Lj.view, C.u, C.rho, C.rhs, C.t, s));
       } else {
-        CK(launch_resid_restrict(Lj.view, Lj.u, rhs, L0.view, L0.t, L0.rho, s));
+        LAUNCH(h, kResidRestrict, Lj.tot_restrict, 41, 144, s,
+               launch_resid_restrict(Lj.view, Lj.u, rhs, L0.view, L0.t, L0.rho, s));
       }
     }
     // transition level: u_0 <- \hat I u_1, t_0 = u_0, r_0 = rho_0 + L_0 u_0, FASMGV
-    CK(launch_transition_rhs(L0.view, L0.t, L0.rho, L0.u, L0.rhs, s));
+    LAUNCH(h, kTransitionRhs, L0.tot_cells, 7, 32, s,
+           launch_transition_rhs(L0.view, L0.t, L0.rho, L0.u, L0.rhs, s));
     int rc = vcycle_global(h, h->G - 1, L0.u, view_global(L0, L0.rhs), s);
     if (rc) return rc;
     // up-leg
     for (int j = 1; j <= k; ++j) {
       Level& Lj = h->slev[j];
       const Level& C = (j == 1) ? L0 : h->slev[j - 1];
-      CK(launch_prolong(C.view, C.u, C.t, Lj.view, Lj.u, 1, s));
+      LAUNCH(h, kProlongAdd, Lj.tot_prolong, 16, 18, s,
+             launch_prolong(C.view, C.u, C.t, Lj.view, Lj.u, 1, s));
       const FieldView rhs = (j == k) ? fview(k) : view_boxes(Lj, Lj.rhs);
-      rc = smooth(Lj, h->post, Lj.u, rhs, s);
+      rc = smooth(h, Lj, h->post, Lj.u, rhs, s);
       if (rc) return rc;
     }
   }
-  CK(launch_gather_genuine(h->slev[K].view, h->slev[K].u, u, s));
+  LAUNCH(h, kGather, h->slev[K].tot_genuine, 0, 16, s,
+         launch_gather_genuine(h->slev[K].view, h->slev[K].u, u, s));
   return SR_OK;
 }
 
 int enqueue_solve(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
+  h->launches = 0;
   CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned int), s));
   int rc = f_hierarchy(h, f, s);
   if (rc) return rc;
@@ -508,6 +604,30 @@ struct DeviceGuard {
 void free_all(sr_fmg_s* h) {
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
+  for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+  for (ProfRec& r : h->prof.recs) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  h->prof.pool.clear();
+  h->prof.recs.clear();
+}
+
+// fold recorded launches into the per-kind totals (after the stream is idle)
+int collect_profile(sr_fmg_s* h) {
+  for (ProfRec& r : h->prof.recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.e1) != cudaSuccess) return SR_ERR_CUDA;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) return SR_ERR_CUDA;
+    h->prof.launches[r.kind] += 1;
+    h->prof.ms[r.kind] += ms;
+    h->prof.ops[r.kind] += r.ops;
+    h->prof.bytes[r.kind] += r.bytes;
+    h->prof.pool.push_back(r.e0);
+    h->prof.pool.push_back(r.e1);
+  }
+  h->prof.recs.clear();
+  return SR_OK;
 }
 
 }  // namespace
@@ -627,6 +747,44 @@ int sr_fmg_solve_host(sr_fmg_t h, const double* f_host, double* u_host, void* st
   return sr_fmg_check(h, stream);
 }
 
+int sr_fmg_launches_per_solve(sr_fmg_t h, int* launches) {
+  if (!h || !launches) return SR_ERR_INVALID;
+  *launches = h->launches;
+  return SR_OK;
+}
+
+int sr_fmg_profile(sr_fmg_t h, int enable) {
+  if (!h) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return SR_ERR_CUDA;
+  int rc = collect_profile(h);
+  if (rc) return rc;
+  if (enable) {
+    for (int k = 0; k < kKinds; ++k) {
+      h->prof.launches[k] = 0;
+      h->prof.ms[k] = h->prof.ops[k] = h->prof.bytes[k] = 0.0;
+    }
+  }
+  h->prof.on = enable != 0;
+  return SR_OK;
+}
+
+int sr_fmg_profile_kinds(void) { return kKinds; }
+
+int sr_fmg_profile_read(sr_fmg_t h, int kind, const char** name, long long* launches,
+                        double* ms, double* fp64_ops, double* bytes) {
+  if (!h || kind < 0 || kind >= kKinds) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  int rc = collect_profile(h);
+  if (rc) return rc;
+  if (name) *name = kKindName[kind];
+  if (launches) *launches = h->prof.launches[kind];
+  if (ms) *ms = h->prof.ms[kind];
+  if (fp64_ops) *fp64_ops = h->prof.ops[kind];
+  if (bytes) *bytes = h->prof.bytes[kind];
+  return SR_OK;
+}
+
 const char* sr_fmg_status_string(int status) {
   switch (status) {
     case SR_OK: return "ok";
@@ -693,7 +851,7 @@ int sr_op_smooth(int n, int nu, double cheb_lo, double cheb_hi, const double* f,
   if (!rc) rc = dalloc(&T.h, &T.L.d, cells);
   if (rc) return rc;
   Cheb c = chebyshev(nu, cheb_lo, cheb_hi);
-  rc = smooth(T.L, c, u, view_global(T.L, f), (cudaStream_t)stream);
+  rc = smooth(&T.h, T.L, c, u, view_global(T.L, f), (cudaStream_t)stream);
   if (rc) return rc;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;

@@ -1,0 +1,50 @@
+"""Small, self-contained launches of the solver's kernels for profiler
+captures (ncu): each case runs a fixed, seeded workload once and exits.
+
+  python -m paper_1406_7808_gb300.profile_case smooth --n 256
+      one Chebyshev degree-2 smoothing of a whole n^3 grid (two kernels:
+      cheb_residual, cheb2_update)
+  python -m paper_1406_7808_gb300.profile_case solve --n 256 [--plain] [--warmup 1]
+      warm-up solves then one solve of the benchmark configuration
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    import torch
+
+    from paper_1406_7808_gb300 import build, inputs, srfmg
+
+    p = argparse.ArgumentParser()
+    p.add_argument("case", choices=["smooth", "solve"])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--plain", action="store_true")
+    p.add_argument("--warmup", type=int, default=1)
+    a = p.parse_args()
+    build.build()
+    torch.cuda.set_device(0)
+    f, _ = inputs.manufactured(a.n, 0)
+    ft = torch.from_numpy(f).cuda()
+    if a.case == "smooth":
+        u = torch.zeros_like(ft)
+        srfmg.op_smooth(u, ft, 2)
+    else:
+        kw = {} if a.plain else dict(seg=32, K=3, A=8, B=0)
+        with srfmg.Solver(a.n, **kw) as s:
+            ut = torch.empty_like(ft)
+            for _ in range(a.warmup):
+                s.solve_async(ft, ut)
+            s.check()
+            s.solve(ft, ut)
+            print(f"launches per solve: {s.launches_per_solve}")
+    torch.cuda.synchronize()
+
+
+if __name__ == "__main__":
+    main()

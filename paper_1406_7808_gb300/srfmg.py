@@ -82,6 +82,14 @@ def load():
     lib.sr_fmg_check.argtypes = [_VP, _VP]
     lib.sr_fmg_status_string.argtypes = [ctypes.c_int]
     lib.sr_fmg_status_string.restype = ctypes.c_char_p
+    lib.sr_fmg_launches_per_solve.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
+    lib.sr_fmg_profile.argtypes = [_VP, ctypes.c_int]
+    lib.sr_fmg_profile_kinds.argtypes = []
+    lib.sr_fmg_profile_read.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                        ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]
     lib.sr_op_apply.argtypes = [ctypes.c_int, _VP, _VP, _VP]
     lib.sr_op_residual.argtypes = [ctypes.c_int, _VP, _VP, _VP, _VP]
     lib.sr_op_smooth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -176,6 +184,32 @@ class Solver:
         b = ctypes.c_size_t()
         _check(load().sr_fmg_workspace_bytes(self._h, ctypes.byref(b)), "workspace_bytes")
         return b.value
+
+    @property
+    def launches_per_solve(self):
+        v = ctypes.c_int()
+        _check(load().sr_fmg_launches_per_solve(self._h, ctypes.byref(v)), "launches_per_solve")
+        return v.value
+
+    def profile(self, enable):
+        """Start (True, clears counters) or stop per-kernel event timing."""
+        _check(load().sr_fmg_profile(self._h, int(bool(enable))), "sr_fmg_profile")
+
+    def profile_read(self):
+        """{kernel: dict(launches, ms, fp64_ops, bytes)} for kernels that ran."""
+        lib = load()
+        out = {}
+        for k in range(lib.sr_fmg_profile_kinds()):
+            name = ctypes.c_char_p()
+            launches = ctypes.c_longlong()
+            ms, ops, nbytes = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            _check(lib.sr_fmg_profile_read(self._h, k, ctypes.byref(name), ctypes.byref(launches),
+                                           ctypes.byref(ms), ctypes.byref(ops),
+                                           ctypes.byref(nbytes)), "sr_fmg_profile_read")
+            if launches.value:
+                out[name.value.decode()] = dict(launches=launches.value, ms=ms.value,
+                                                fp64_ops=ops.value, bytes=nbytes.value)
+        return out
 
     def solve(self, f, out=None):
         """u = solver(f) for a float64 CUDA tensor f; waits and checks status."""
