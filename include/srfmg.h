@@ -174,6 +174,31 @@ int sr_op_prolong(int nc, const double* ac, double* af, void* stream);
 int sr_op_coarse_solve(int n, const double* f, double* u, void* stream);
 int sr_op_vcycle(const sr_fmg_config* cfg, const double* f, double* u, void* stream);
 
+/*
+ * Chebyshev smoother that allocates nothing (the paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory where they
+ * smooth, e.g. when all device memory is handed out by another allocator or
+ * when cudaMalloc's implicit synchronisation is not acceptable).
+ * Same operation and arguments as sr_op_smooth on device arrays f and u of
+ * n^3 doubles, but the scratch (two n^3 arrays and a grid descriptor) lives in
+ * one fixed device array of this library, sized for n <= SR_NOALLOC_MAX_N
+ * (4 MiB + 256 bytes; every GPU that loads the library holds it until the
+ * process exits).  No cudaMalloc, cudaFree or allocating library call is made.
+ *   - n > SR_NOALLOC_MAX_N returns SR_ERR_UNSUPPORTED_SIZE; bad arguments
+ *     return SR_ERR_INVALID.
+ *   - The work is queued on stream and the call returns without waiting.
+ *   - The first call on a device looks up the device address of the scratch
+ *     array (once per device, with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the one scratch array, which keeps the last call's
+ *     contents: calls that overlap on the GPU (other streams or threads, or
+ *     another solver using this entry point at the same time) race and give
+ *     wrong results.  Nothing in the scratch needs to start at zero.
+ */
+#define SR_NOALLOC_MAX_N 64
+int sr_op_smooth_noalloc(int n, int nu, double cheb_lo, double cheb_hi, const double* f,
+                         double* u, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

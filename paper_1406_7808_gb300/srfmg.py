@@ -94,6 +94,8 @@ def load():
     lib.sr_op_residual.argtypes = [ctypes.c_int, _VP, _VP, _VP, _VP]
     lib.sr_op_smooth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                  _VP, _VP, _VP]
+    lib.sr_op_smooth_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, _VP, _VP, _VP]
     lib.sr_op_restrict.argtypes = [ctypes.c_int, _VP, _VP, _VP]
     lib.sr_op_prolong.argtypes = [ctypes.c_int, _VP, _VP, _VP]
     lib.sr_op_coarse_solve.argtypes = [ctypes.c_int, _VP, _VP, _VP]
@@ -267,6 +269,20 @@ def op_smooth(u, f, nu, cheb_lo=1.0 / 6.0, cheb_hi=1.0):
     u = u.clone()
     _check(load().sr_op_smooth(u.shape[0], nu, cheb_lo, cheb_hi, _dev(f), _dev(u), _stream()),
            "sr_op_smooth")
+    return u
+
+
+NOALLOC_MAX_N = 64
+
+
+def op_smooth_noalloc(u, f, nu, cheb_lo=1.0 / 6.0, cheb_hi=1.0):
+    """Chebyshev smoother whose scratch lives in a fixed device array of the
+    library (no device allocation; n <= NOALLOC_MAX_N).  For callers that
+    cannot allocate device memory where they smooth.  Calls that overlap on
+    the GPU share that scratch and race.  Returns a new tensor."""
+    u = u.clone()
+    _check(load().sr_op_smooth_noalloc(u.shape[0], nu, cheb_lo, cheb_hi, _dev(f), _dev(u),
+                                       _stream()), "sr_op_smooth_noalloc")
     return u
 
 
