@@ -5,16 +5,23 @@
 // threads of blockIdx.x stride over the cells of the kernel's region in x-
 // fastest order.  On GB300 the float64 pipe (two lanes per clock per SM) is
 // the binding resource for these stencils, far below what HBM can feed, so
-// the kernels are written to spend as few float64 instructions per cell as
+// the kernels are written to spend as little float64 pipe time per cell as
 // the arithmetic allows:
 //   - ghost cells outside the domain are never stored: a neighbour outside
 //     the domain is replaced by minus the mirror cell on the fly (Sec. 3.3),
 //     with the sign flip done on the integer pipe;
+//   - every float64 operation is a fused multiply-add whose constant operands
+//     are kernel parameters (adds as fma(a, one, b), scalings as
+//     fma(a, c, zero)): on sm_103a that form issues faster than DADD, DMUL or
+//     an FMA with an immediate operand (0.63 against 0.53 T lane-op/s);
 //   - the degree-2 Chebyshev smoother is evaluated as x2 = x0 + a r0 + b S(r0)
-//     (two stencil passes, 14 float64 operations per cell) instead of the
-//     three-term recurrence (19);
+//     (two stencil passes, 14 operations per cell) instead of the three-term
+//     recurrence (19);
 //   - the residual of the 8 children of a coarse cell is summed through the
-//     24 faces of the 2x2x2 block (41 operations per coarse cell instead of 72).
+//     24 faces of the 2x2x2 block (41 operations per coarse cell instead of 72);
+//   - trilinear interpolation runs per coarse cell over its 2x2x2 children as
+//     three separable passes of 3a + b (about 9 operations per fine cell for
+//     the correction instead of 16).
 #include "srfmg_internal.cuh"
 
 namespace srfmg {
@@ -22,18 +29,33 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Constants handed to the kernels as parameters so that the compiler cannot
+// fold them into immediates (see above).  Values: one = 1, zero = 0.
+struct Fk {
+  double one, zero;
+};
+
+__host__ __device__ inline Fk fk() { return Fk{1.0, 0.0}; }
+
 __device__ __forceinline__ long long at(const BoxDesc& b, int x, int y, int z) {
   return b.base + (long long)(z - b.oz) * b.sz + (long long)(y - b.oy) * b.sy + (x - b.ox);
 }
 
-// -v, by flipping the sign bit on the integer pipe
+// -v, by flipping the sign bit of the high word on the integer pipe.  The
+// xor is inline PTX so that the compiler cannot turn it back into a float64
+// negation (which would cost a float64 instruction).
 __device__ __forceinline__ double negd(double v) {
-  return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL);
+  int hi = __double2hiint(v);
+  asm("xor.b32 %0, %0, 0x80000000;" : "+r"(hi));
+  return __hiloint2double(hi, __double2loint(v));
 }
 
 // v or -v, selected on the integer pipe
 __device__ __forceinline__ double neg_if(double v, bool flip) {
-  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)flip << 63));
+  int hi = __double2hiint(v);
+  const unsigned m = (unsigned)flip << 31;
+  asm("xor.b32 %0, %0, %1;" : "+r"(hi) : "r"(m));
+  return __hiloint2double(hi, __double2loint(v));
 }
 
 __device__ __forceinline__ void region_of(const BoxDesc& b, int which, int lo[3], int hi[3]) {
@@ -46,19 +68,25 @@ __device__ __forceinline__ void region_of(const BoxDesc& b, int which, int lo[3]
   for (int d = 0; d < 3; ++d) { lo[d] = l[d]; hi[d] = h[d]; }
 }
 
-// Sum of the six neighbours of stored cell c at (x, y, z); a neighbour outside
+// The six neighbours of stored cell c at (x, y, z); a neighbour outside
 // [0, n) is minus the centre value (mirror through u = 0 on the face).
-__device__ __forceinline__ double neighbour_sum(const double* __restrict__ a, long long c,
-                                                const BoxDesc& b, int n, int x, int y, int z,
-                                                double centre) {
+__device__ __forceinline__ void neighbours(const double* __restrict__ a, long long c,
+                                           const BoxDesc& b, int n, int x, int y, int z,
+                                           double centre, double v[6]) {
   const double m = negd(centre);
-  const double xm = (x > 0) ? a[c - 1] : m;
-  const double xp = (x < n - 1) ? a[c + 1] : m;
-  const double ym = (y > 0) ? a[c - b.sy] : m;
-  const double yp = (y < n - 1) ? a[c + b.sy] : m;
-  const double zm = (z > 0) ? a[c - b.sz] : m;
-  const double zp = (z < n - 1) ? a[c + b.sz] : m;
-  return ((xm + xp) + (ym + yp)) + (zm + zp);
+  v[0] = (x > 0) ? a[c - 1] : m;
+  v[1] = (x < n - 1) ? a[c + 1] : m;
+  v[2] = (y > 0) ? a[c - b.sy] : m;
+  v[3] = (y < n - 1) ? a[c + b.sy] : m;
+  v[4] = (z > 0) ? a[c - b.sz] : m;
+  v[5] = (z < n - 1) ? a[c + b.sz] : m;
+}
+
+// acc + w * (v0 + ... + v5) as six fused multiply-adds
+__device__ __forceinline__ double fma6(double w, const double v[6], double acc) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) acc = fma(w, v[i], acc);
+  return acc;
 }
 
 struct Cell {
@@ -76,10 +104,11 @@ __device__ __forceinline__ Cell cell_of(int i, const int lo[3], int ex, int ey) 
 
 // ---------------------------------------------------------------------------
 
+// r = D^-1 (f - A u) = f h^2/6 - u + (sum of neighbours)/6
 __global__ void __launch_bounds__(kThreads) k_cheb_residual(LevelView L,
                                                             const double* __restrict__ u,
                                                             double* __restrict__ r, FieldView f,
-                                                            double cf) {
+                                                            double cf, double sixth) {
   __shared__ BoxDesc B, FB;
   if (threadIdx.x == 0) {
     B = L.boxes[blockIdx.y];
@@ -89,18 +118,18 @@ __global__ void __launch_bounds__(kThreads) k_cheb_residual(LevelView L,
   const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
   const int ncell = ex * ey * ez;
   const int n = L.n;
-  constexpr double sixth = 1.0 / 6.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
     const double uc = u[c];
-    const double s = neighbour_sum(u, c, B, n, q.x, q.y, q.z, uc);
+    double v[6];
+    neighbours(u, c, B, n, q.x, q.y, q.z, uc, v);
     const double fv = f.p[at(FB, q.x, q.y, q.z)];
-    // D^-1 (f - A u) = f h^2/6 - u + s/6
-    r[c] = fma(s, sixth, fma(fv, cf, negd(uc)));
+    r[c] = fma6(sixth, v, fma(fv, cf, negd(uc)));
   }
 }
 
+// u += a r + b (sum of the neighbours of r)
 __global__ void __launch_bounds__(kThreads) k_cheb2_update(LevelView L, double* __restrict__ u,
                                                            const double* __restrict__ r,
                                                            double a, double b) {
@@ -114,32 +143,38 @@ __global__ void __launch_bounds__(kThreads) k_cheb2_update(LevelView L, double* 
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
     const double rc = r[c];
-    const double s = neighbour_sum(r, c, B, n, q.x, q.y, q.z, rc);
-    u[c] = fma(b, s, fma(a, rc, u[c]));
+    double v[6];
+    neighbours(r, c, B, n, q.x, q.y, q.z, rc, v);
+    u[c] = fma6(b, v, fma(a, rc, u[c]));
   }
 }
 
+// d = alpha d + beta r (alpha == 0: d = beta r); u += d
 __global__ void __launch_bounds__(kThreads) k_cheb_step(LevelView L, double* __restrict__ u,
                                                         double* __restrict__ d,
                                                         const double* __restrict__ r,
-                                                        double alpha, double beta, int write_d) {
+                                                        double alpha, double beta, int write_d,
+                                                        Fk k) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
   const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
   const int ncell = ex * ey * ez;
+  const bool use_d = alpha != 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
-    const double dn = (alpha != 0.0) ? fma(alpha, d[c], beta * r[c]) : beta * r[c];
+    double dn = fma(beta, r[c], k.zero);
+    if (use_d) dn = fma(alpha, d[c], dn);
     if (write_d) d[c] = dn;
-    u[c] += dn;
+    u[c] = fma(dn, k.one, u[c]);
   }
 }
 
+// residual == 0: out = A u = n^2 (6 u - sum);  residual == 1: out = f - A u
 __global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const double* __restrict__ u,
                                                     double* __restrict__ out, FieldView f,
-                                                    int residual) {
+                                                    int residual, double c6, double cn, Fk k) {
   __shared__ BoxDesc B, FB;
   if (threadIdx.x == 0) {
     B = L.boxes[blockIdx.y];
@@ -149,26 +184,30 @@ __global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const double* _
   const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
   const int ncell = ex * ey * ez;
   const int n = L.n;
-  const double ih2 = (double)n * (double)n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
     const double uc = u[c];
-    const double s = neighbour_sum(u, c, B, n, q.x, q.y, q.z, uc);
-    const double au = fma(6.0, uc, negd(s));
-    out[c] = residual ? fma(-ih2, au, f.p[at(FB, q.x, q.y, q.z)]) : ih2 * au;
+    double v[6];
+    neighbours(u, c, B, n, q.x, q.y, q.z, uc, v);
+    // apply: c6 = 6 n^2, cn = -n^2; residual: c6 = -6 n^2, cn = n^2
+    const double base = residual ? f.p[at(FB, q.x, q.y, q.z)] : k.zero;
+    out[c] = fma6(cn, v, fma(c6, uc, base));
   }
 }
 
 // Residual of the 8 children of each coarse cell, restricted, and the
 // restricted solution.  With S the sum of the children, the children's
 // operator values add up to n^2 (3 S - O), O the sum of the 24 neighbours
-// across the outer faces of the 2x2x2 block (each inner face cancels).
+// across the outer faces of the 2x2x2 block (each inner face cancels), so
+//   rho = (sum of f)/8 - (3 n^2/8) S + (n^2/8) O,   uhat = S/8.
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F,
                                                              const double* __restrict__ u,
                                                              FieldView f, LevelView C,
                                                              double* __restrict__ uhat_dst,
-                                                             double* __restrict__ rho_dst) {
+                                                             double* __restrict__ rho_dst,
+                                                             double cS, double cO, double eighth,
+                                                             Fk k) {
   __shared__ BoxDesc B, FB, CB;
   if (threadIdx.x == 0) {
     B = F.boxes[blockIdx.y];
@@ -181,7 +220,6 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F,
   const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
   const int ncell = ex * ey * ez;
   const int n = F.n;
-  const double ih2 = (double)n * (double)n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, lo, ex, ey);
     const int x0 = 2 * q.x, y0 = 2 * q.y, z0 = 2 * q.z;
@@ -194,58 +232,67 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F,
       for (int cy = 0; cy < 2; ++cy)
 #pragma unroll
         for (int cx = 0; cx < 2; ++cx) v[cz][cy][cx] = u[c0 + cz * sz + cy * sy + cx];
-    double fs = 0.0;
+    double fs;
     {
       const long long f0 = at(FB, x0, y0, z0);
       const long long fy = FB.sy, fz = FB.sz;
-      fs = ((f.p[f0] + f.p[f0 + 1]) + (f.p[f0 + fy] + f.p[f0 + fy + 1])) +
-           ((f.p[f0 + fz] + f.p[f0 + fz + 1]) + (f.p[f0 + fz + fy] + f.p[f0 + fz + fy + 1]));
+      fs = fma(f.p[f0], k.one, f.p[f0 + 1]);
+      fs = fma(f.p[f0 + fy], k.one, fs);
+      fs = fma(f.p[f0 + fy + 1], k.one, fs);
+      fs = fma(f.p[f0 + fz], k.one, fs);
+      fs = fma(f.p[f0 + fz + 1], k.one, fs);
+      fs = fma(f.p[f0 + fz + fy], k.one, fs);
+      fs = fma(f.p[f0 + fz + fy + 1], k.one, fs);
     }
-    const double S = ((v[0][0][0] + v[0][0][1]) + (v[0][1][0] + v[0][1][1])) +
-                     ((v[1][0][0] + v[1][0][1]) + (v[1][1][0] + v[1][1][1]));
+    double S = fma(v[0][0][0], k.one, v[0][0][1]);
+    S = fma(v[0][1][0], k.one, S);
+    S = fma(v[0][1][1], k.one, S);
+    S = fma(v[1][0][0], k.one, S);
+    S = fma(v[1][0][1], k.one, S);
+    S = fma(v[1][1][0], k.one, S);
+    S = fma(v[1][1][1], k.one, S);
     // the 24 outer neighbours, mirrored with a sign flip outside the domain
     const bool xl = x0 > 0, xr = x0 + 2 < n, yl = y0 > 0, yr = y0 + 2 < n, zl = z0 > 0,
                zr = z0 + 2 < n;
-    double O = 0.0;
+    double O = k.zero;
 #pragma unroll
     for (int cz = 0; cz < 2; ++cz)
 #pragma unroll
       for (int cy = 0; cy < 2; ++cy) {
         const long long row = c0 + cz * sz + cy * sy;
-        const double a = xl ? u[row - 1] : negd(v[cz][cy][0]);
-        const double b = xr ? u[row + 2] : negd(v[cz][cy][1]);
-        O += a + b;
+        O = fma(xl ? u[row - 1] : negd(v[cz][cy][0]), k.one, O);
+        O = fma(xr ? u[row + 2] : negd(v[cz][cy][1]), k.one, O);
       }
 #pragma unroll
     for (int cz = 0; cz < 2; ++cz)
 #pragma unroll
       for (int cx = 0; cx < 2; ++cx) {
         const long long col = c0 + cz * sz + cx;
-        const double a = yl ? u[col - sy] : negd(v[cz][0][cx]);
-        const double b = yr ? u[col + 2 * sy] : negd(v[cz][1][cx]);
-        O += a + b;
+        O = fma(yl ? u[col - sy] : negd(v[cz][0][cx]), k.one, O);
+        O = fma(yr ? u[col + 2 * sy] : negd(v[cz][1][cx]), k.one, O);
       }
 #pragma unroll
     for (int cy = 0; cy < 2; ++cy)
 #pragma unroll
       for (int cx = 0; cx < 2; ++cx) {
         const long long pil = c0 + cy * sy + cx;
-        const double a = zl ? u[pil - sz] : negd(v[0][cy][cx]);
-        const double b = zr ? u[pil + 2 * sz] : negd(v[1][cy][cx]);
-        O += a + b;
+        O = fma(zl ? u[pil - sz] : negd(v[0][cy][cx]), k.one, O);
+        O = fma(zr ? u[pil + 2 * sz] : negd(v[1][cy][cx]), k.one, O);
       }
     const long long cc = at(CB, q.x, q.y, q.z);
-    const double au = fma(3.0, S, negd(O));  // h^2 * sum of the children's A u
-    rho_dst[cc] = 0.125 * fma(-ih2, au, fs);
-    uhat_dst[cc] = 0.125 * S;
+    rho_dst[cc] = fma(cS, S, fma(cO, O, fma(fs, eighth, k.zero)));
+    uhat_dst[cc] = fma(S, eighth, k.zero);
   }
 }
 
+// rhs = rho + A u inside the restriction region of the matching fine box,
+// A u elsewhere in the compute region; t = u on the whole stored box
 __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView F,
                                                          const double* __restrict__ u,
                                                          const double* __restrict__ rho,
                                                          double* __restrict__ rhs,
-                                                         double* __restrict__ t) {
+                                                         double* __restrict__ t, double c6,
+                                                         double cn, Fk k) {
   __shared__ BoxDesc B, FBx;
   if (threadIdx.x == 0) {
     B = C.boxes[blockIdx.y];
@@ -253,7 +300,6 @@ __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView 
   }
   __syncthreads();
   const int n = C.n;
-  const double ih2 = (double)n * (double)n;
   const bool shell = B.ox < B.lo[0];
   int lo[3], hi[3];
 #pragma unroll
@@ -275,111 +321,144 @@ __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView 
     if (!compute) continue;
     const bool inF = q.x >= FBx.rlo[0] && q.x < FBx.rhi[0] && q.y >= FBx.rlo[1] &&
                      q.y < FBx.rhi[1] && q.z >= FBx.rlo[2] && q.z < FBx.rhi[2];
-    const double s = neighbour_sum(u, c, B, n, q.x, q.y, q.z, uc);
-    const double au = fma(6.0, uc, negd(s));
-    rhs[c] = inF ? fma(ih2, au, rho[c]) : ih2 * au;
+    double v[6];
+    neighbours(u, c, B, n, q.x, q.y, q.z, uc, v);
+    rhs[c] = fma6(cn, v, fma(c6, uc, inF ? rho[c] : k.zero));
   }
 }
 
+// u = t, rhs = rho + A t on the whole (global) transition level
 __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
                                                              const double* __restrict__ t,
                                                              const double* __restrict__ rho,
                                                              double* __restrict__ u,
-                                                             double* __restrict__ rhs) {
+                                                             double* __restrict__ rhs, double c6,
+                                                             double cn) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[0];
   __syncthreads();
   const int n = C.n;
-  const double ih2 = (double)n * (double)n;
   const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
   const int ncell = ex * ey * ez;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
     const double tc = t[c];
-    const double s = neighbour_sum(t, c, B, n, q.x, q.y, q.z, tc);
+    double v[6];
+    neighbours(t, c, B, n, q.x, q.y, q.z, tc, v);
     u[c] = tc;
-    rhs[c] = fma(ih2, fma(6.0, tc, negd(s)), rho[c]);
+    rhs[c] = fma6(cn, v, fma(c6, tc, rho[c]));
   }
 }
 
-// coarse value for trilinear interpolation: mirrored with a sign flip outside
-// the domain; with tc != nullptr the value is uc - tc.
-__device__ __forceinline__ double coarse_value(const double* __restrict__ uc,
-                                               const double* __restrict__ tc,
-                                               const BoxDesc& C, int nc, int x, int y, int z) {
-  bool flip = false;
-  if (x < 0) { x = 0; flip = !flip; } else if (x >= nc) { x = nc - 1; flip = !flip; }
-  if (y < 0) { y = 0; flip = !flip; } else if (y >= nc) { y = nc - 1; flip = !flip; }
-  if (z < 0) { z = 0; flip = !flip; } else if (z >= nc) { z = nc - 1; flip = !flip; }
-  const long long i = at(C, x, y, z);
-  const double v = tc ? uc[i] - tc[i] : uc[i];
-  return neg_if(v, flip);
-}
-
-// Trilinear prolongation in factored form: with 1D weights 3/4 (own coarse
-// cell) and 1/4 (neighbour), the fine value is (1/64) * the x, y, z passes of
-// 3 a + b.
+// Trilinear prolongation, one coarse cell and its 2x2x2 children per thread.
+// With 1D weights 3/4 (own coarse cell) and 1/4 (neighbour on the child's
+// side), each child is (1/64) x the z, y, x passes of 3 a + b over the 3x3x3
+// coarse neighbourhood.  add == 0: uf = P uc;  add == 1: uf += P (uc - tc).
+// Coarse cells outside the domain are mirrored with a sign flip; a neighbour
+// is read only if a child inside the fine region needs it.
 __global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const double* __restrict__ uc,
                                                       const double* __restrict__ tc, LevelView F,
-                                                      double* __restrict__ uf, int add) {
+                                                      double* __restrict__ uf, int add,
+                                                      double three, double w64, double mone,
+                                                      Fk k) {
   __shared__ BoxDesc B, CB;
   if (threadIdx.x == 0) {
     B = F.boxes[blockIdx.y];
     CB = (C.nbox == 1) ? C.boxes[0] : C.boxes[blockIdx.y];
   }
   __syncthreads();
-  int lo[3], hi[3];
-  region_of(B, kProlong, lo, hi);
-  const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
-  const int ncell = ex * ey * ez;
+  int plo[3], phi[3], clo[3], cex[3];
+  region_of(B, kProlong, plo, phi);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    clo[d] = plo[d] >> 1;
+    cex[d] = ((phi[d] - 1) >> 1) + 1 - clo[d];
+  }
+  const int ncell = cex[0] * cex[1] * cex[2];
   const int nc = C.n;
-  const double* tcp = add ? tc : nullptr;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
-    const Cell q = cell_of(i, lo, ex, ey);
-    const int cx = q.x >> 1, cy = q.y >> 1, cz = q.z >> 1;
-    const int nx = (q.x & 1) ? cx + 1 : cx - 1;
-    const int ny = (q.y & 1) ? cy + 1 : cy - 1;
-    const int nz = (q.z & 1) ? cz + 1 : cz - 1;
-    const int xs[2] = {cx, nx}, ys[2] = {cy, ny}, zs[2] = {cz, nz};
-    double pz[2];
+    const Cell q = cell_of(i, clo, cex[0], cex[1]);
+    const int X[3] = {q.x, q.y, q.z};
+    bool lo_ok[3], hi_ok[3];  // even child (needs X-1) / odd child (needs X+1) inside the region
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      double py[2];
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const double v0 = coarse_value(uc, tcp, CB, nc, xs[0], ys[b], zs[a]);
-        const double v1 = coarse_value(uc, tcp, CB, nc, xs[1], ys[b], zs[a]);
-        py[b] = fma(3.0, v0, v1);
-      }
-      pz[a] = fma(3.0, py[0], py[1]);
+    for (int d = 0; d < 3; ++d) {
+      lo_ok[d] = 2 * X[d] >= plo[d];
+      hi_ok[d] = 2 * X[d] + 1 < phi[d];
     }
-    const double e = fma(3.0, pz[0], pz[1]);
-    const long long c = at(B, q.x, q.y, q.z);
-    constexpr double w = 1.0 / 64.0;
-    if (add)
-      uf[c] = fma(w, e, uf[c]);
-    else
-      uf[c] = w * e;
+    // x pass over the 3x3 (z, y) lines of the coarse neighbourhood
+    double px[3][3][2];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        const bool need = (dz != 0 || lo_ok[2]) && (dz != 2 || hi_ok[2]) && (dy != 0 || lo_ok[1]) &&
+                          (dy != 2 || hi_ok[1]);
+        double v[3];
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const bool needx = need && (dx != 0 || lo_ok[0]) && (dx != 2 || hi_ok[0]);
+          double val = k.zero;
+          if (needx) {
+            int x = X[0] + dx - 1, y = X[1] + dy - 1, z = X[2] + dz - 1;
+            bool flip = false;
+            if (x < 0) { x = 0; flip = !flip; } else if (x >= nc) { x = nc - 1; flip = !flip; }
+            if (y < 0) { y = 0; flip = !flip; } else if (y >= nc) { y = nc - 1; flip = !flip; }
+            if (z < 0) { z = 0; flip = !flip; } else if (z >= nc) { z = nc - 1; flip = !flip; }
+            const long long ci = at(CB, x, y, z);
+            val = add ? fma(tc[ci], mone, uc[ci]) : uc[ci];
+            val = neg_if(val, flip);
+          }
+          v[dx] = val;
+        }
+        px[dz][dy][0] = fma(three, v[1], v[0]);
+        px[dz][dy][1] = fma(three, v[1], v[2]);
+      }
+    double py[3][2][2];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        py[dz][0][cx] = fma(three, px[dz][1][cx], px[dz][0][cx]);
+        py[dz][1][cx] = fma(three, px[dz][1][cx], px[dz][2][cx]);
+      }
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz) {
+      const int fz = 2 * X[2] + cz;
+      if (fz < plo[2] || fz >= phi[2]) continue;
+#pragma unroll
+      for (int cy = 0; cy < 2; ++cy) {
+        const int fy = 2 * X[1] + cy;
+        if (fy < plo[1] || fy >= phi[1]) continue;
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx) {
+          const int fx = 2 * X[0] + cx;
+          if (fx < plo[0] || fx >= phi[0]) continue;
+          const double e = fma(three, py[1][cy][cx], py[cz == 0 ? 0 : 2][cy][cx]);
+          const long long c = at(B, fx, fy, fz);
+          uf[c] = fma(w64, e, add ? uf[c] : k.zero);
+        }
+      }
+    }
   }
 }
 
 // One warp per row of the dense inverse.
 __global__ void k_coarse_solve(LevelView L, const double* __restrict__ minv, FieldView f,
-                               double* __restrict__ u) {
+                               double* __restrict__ u, Fk k) {
   const BoxDesc B = L.boxes[0];
   const BoxDesc FB = f.boxes[0];
   const int n = L.n, m = n * n * n;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= m) return;
-  double s = 0.0;
+  double s = k.zero;
   for (int j = lane; j < m; j += 32) {
     const int x = j % n, y = (j / n) % n, z = j / (n * n);
     s = fma(minv[(long long)warp * m + j], f.p[at(FB, x, y, z)], s);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  for (int o = 16; o > 0; o >>= 1) s = fma(__shfl_xor_sync(0xffffffffu, s, o), k.one, s);
   if (lane == 0) {
     const int x = warp % n, y = (warp / n) % n, z = warp / (n * n);
     u[at(B, x, y, z)] = s;
@@ -392,7 +471,8 @@ __device__ __forceinline__ bool not_finite(double v) {
 
 __global__ void __launch_bounds__(kThreads) k_restrict_global(int nf, const double* __restrict__ ff,
                                                               double* __restrict__ fc, int check,
-                                                              unsigned int* status) {
+                                                              unsigned int* status, double eighth,
+                                                              Fk k) {
   const int nc = nf / 2;
   const long long ncell = (long long)nc * nc * nc;
   bool bad = false;
@@ -403,13 +483,15 @@ __global__ void __launch_bounds__(kThreads) k_restrict_global(int nf, const doub
     const int y = (int)(t % nc), z = (int)(t / nc);
     const long long f0 = ((long long)(2 * z) * nf + 2 * y) * nf + 2 * x;
     const long long py = nf, pz = (long long)nf * nf;
-    const double a0 = ff[f0], a1 = ff[f0 + 1], a2 = ff[f0 + py], a3 = ff[f0 + py + 1];
-    const double a4 = ff[f0 + pz], a5 = ff[f0 + pz + 1], a6 = ff[f0 + pz + py],
-                 a7 = ff[f0 + pz + py + 1];
-    if (check)
-      bad |= not_finite(a0) | not_finite(a1) | not_finite(a2) | not_finite(a3) | not_finite(a4) |
-             not_finite(a5) | not_finite(a6) | not_finite(a7);
-    fc[i] = 0.125 * (((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7)));
+    const double a[8] = {ff[f0], ff[f0 + 1], ff[f0 + py], ff[f0 + py + 1],
+                         ff[f0 + pz], ff[f0 + pz + 1], ff[f0 + pz + py], ff[f0 + pz + py + 1]};
+    double s = k.zero;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (check) bad |= not_finite(a[j]);
+      s = fma(a[j], eighth, s);
+    }
+    fc[i] = s;
   }
   if (check && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
 }
@@ -437,12 +519,14 @@ dim3 grid_for(const LevelView& L, int cells) {
   return dim3((unsigned)bx, (unsigned)L.nbox, 1);
 }
 
+double sq(int n) { return (double)n * (double)n; }
+
 }  // namespace
 
 cudaError_t launch_cheb_residual(const LevelView& L, const double* u, double* r, FieldView f,
                                  cudaStream_t s) {
-  const double cf = 1.0 / (6.0 * (double)L.n * (double)L.n);
-  k_cheb_residual<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, cf);
+  const double cf = 1.0 / (6.0 * sq(L.n));
+  k_cheb_residual<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, cf, 1.0 / 6.0);
   return cudaGetLastError();
 }
 
@@ -454,45 +538,57 @@ cudaError_t launch_cheb2_update(const LevelView& L, double* u, const double* r, 
 
 cudaError_t launch_cheb_step(const LevelView& L, double* u, double* d, const double* r,
                              double alpha, double beta, int write_d, cudaStream_t s) {
-  k_cheb_step<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, d, r, alpha, beta, write_d);
+  k_cheb_step<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, d, r, alpha, beta, write_d,
+                                                            fk());
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const LevelView& L, const double* u, double* out, cudaStream_t s) {
   FieldView none{nullptr, L.boxes, 0};
-  k_apply<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, out, none, 0);
+  k_apply<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, out, none, 0, 6.0 * sq(L.n),
+                                                        -sq(L.n), fk());
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const LevelView& L, const double* u, FieldView f, double* r,
                             cudaStream_t s) {
-  k_apply<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, 1);
+  k_apply<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, 1, -6.0 * sq(L.n), sq(L.n),
+                                                        fk());
   return cudaGetLastError();
 }
 
 cudaError_t launch_resid_restrict(const LevelView& F, const double* u, FieldView f,
                                   const LevelView& C, double* uhat_dst, double* rho_dst,
                                   cudaStream_t s) {
-  k_resid_restrict<<<grid_for(F, F.max_restrict), kThreads, 0, s>>>(F, u, f, C, uhat_dst,
-                                                                    rho_dst);
+  const double n2 = sq(F.n);
+  k_resid_restrict<<<grid_for(F, F.max_restrict), kThreads, 0, s>>>(
+      F, u, f, C, uhat_dst, rho_dst, -3.0 * n2 / 8.0, n2 / 8.0, 0.125, fk());
   return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_rhs(const LevelView& C, const LevelView& F, const double* u,
                               const double* rho, double* rhs, double* t, cudaStream_t s) {
-  k_coarse_rhs<<<grid_for(C, C.max_stored), kThreads, 0, s>>>(C, F, u, rho, rhs, t);
+  k_coarse_rhs<<<grid_for(C, C.max_stored), kThreads, 0, s>>>(C, F, u, rho, rhs, t,
+                                                              6.0 * sq(C.n), -sq(C.n), fk());
   return cudaGetLastError();
 }
 
 cudaError_t launch_transition_rhs(const LevelView& C, const double* t, const double* rho,
                                   double* u, double* rhs, cudaStream_t s) {
-  k_transition_rhs<<<grid_for(C, C.max_cells), kThreads, 0, s>>>(C, t, rho, u, rhs);
+  k_transition_rhs<<<grid_for(C, C.max_cells), kThreads, 0, s>>>(C, t, rho, u, rhs,
+                                                                  6.0 * sq(C.n), -sq(C.n));
   return cudaGetLastError();
 }
 
 cudaError_t launch_prolong(const LevelView& C, const double* uc, const double* tc,
                            const LevelView& F, double* uf, int add, cudaStream_t s) {
-  k_prolong<<<grid_for(F, F.max_prolong), kThreads, 0, s>>>(C, uc, tc, F, uf, add);
+  // one thread per coarse cell over the children in the prolongation range:
+  // at most about max_prolong / 8 plus the partial blocks on the faces
+  int edge = 1;
+  while ((long long)edge * edge * edge < F.max_prolong) ++edge;
+  const int half = edge / 2 + 2;
+  k_prolong<<<grid_for(F, half * half * half), kThreads, 0, s>>>(C, uc, tc, F, uf, add, 3.0,
+                                                                 1.0 / 64.0, -1.0, fk());
   return cudaGetLastError();
 }
 
@@ -501,7 +597,7 @@ cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldVie
   const int m = L.n * L.n * L.n;
   const int warps_per_block = 8;
   const int blocks = (m + warps_per_block - 1) / warps_per_block;
-  k_coarse_solve<<<blocks, warps_per_block * 32, 0, s>>>(L, minv, f, u);
+  k_coarse_solve<<<blocks, warps_per_block * 32, 0, s>>>(L, minv, f, u, fk());
   return cudaGetLastError();
 }
 
@@ -512,7 +608,8 @@ cudaError_t launch_restrict_global(int nf, const double* ff, double* fc, int che
   long long blocks = (cells + kThreads - 1) / kThreads;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
-  k_restrict_global<<<(unsigned)blocks, kThreads, 0, s>>>(nf, ff, fc, check, status);
+  k_restrict_global<<<(unsigned)blocks, kThreads, 0, s>>>(nf, ff, fc, check, status, 0.125,
+                                                          fk());
   return cudaGetLastError();
 }
 

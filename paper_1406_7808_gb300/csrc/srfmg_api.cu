@@ -465,7 +465,7 @@ int vcycle_global(sr_fmg_s* h, int g, double* u, FieldView rhs, cudaStream_t s) 
          launch_coarse_rhs(C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
   rc = vcycle_global(h, g - 1, C.u, view_global(C, C.rhs), s);
   if (rc) return rc;
-  LAUNCH(h, kProlongAdd, L.tot_prolong, 16, 18, s,
+  LAUNCH(h, kProlongAdd, L.tot_prolong, 73.0 / 8.0, 18, s,
          launch_prolong(C.view, C.u, C.t, L.view, u, 1, s));
   return smooth(h, L, h->post, u, rhs, s);
 }
@@ -482,7 +482,7 @@ int run_fmg_global(sr_fmg_s* h, const double* ftop, double* utop, cudaStream_t s
   }
   for (int g = 1; g <= top; ++g) {
     Level& L = h->glev[g];
-    LAUNCH(h, kProlongSet, L.tot_prolong, 8, 9, s,
+    LAUNCH(h, kProlongSet, L.tot_prolong, 46.0 / 8.0, 9, s,
            launch_prolong(h->glev[g - 1].view, ug(g - 1), nullptr, L.view, ug(g), 0, s));
     FieldView f = view_global(L, fg(g));
     int rc = smooth(h, L, h->fmg, ug(g), f, s);
@@ -527,7 +527,7 @@ int run_sr(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
     // u_k <- Pi u_{k-1} on Omega^C_k u Omega^GSR_k, then S^alpha on Omega^C_k
     {
       const Level& C = (k == 1) ? L0 : h->slev[k - 1];
-      LAUNCH(h, kProlongSet, Lk.tot_prolong, 8, 9, s,
+      LAUNCH(h, kProlongSet, Lk.tot_prolong, 46.0 / 8.0, 9, s,
              launch_prolong(C.view, C.u, nullptr, Lk.view, Lk.u, 0, s));
       int rc = smooth(h, Lk, h->fmg, Lk.u, fview(k), s);
       if (rc) return rc;
@@ -558,7 +558,7 @@ int run_sr(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
     for (int j = 1; j <= k; ++j) {
       Level& Lj = h->slev[j];
       const Level& C = (j == 1) ? L0 : h->slev[j - 1];
-      LAUNCH(h, kProlongAdd, Lj.tot_prolong, 16, 18, s,
+      LAUNCH(h, kProlongAdd, Lj.tot_prolong, 73.0 / 8.0, 18, s,
              launch_prolong(C.view, C.u, C.t, Lj.view, Lj.u, 1, s));
       const FieldView rhs = (j == k) ? fview(k) : view_boxes(Lj, Lj.rhs);
       rc = smooth(h, Lj, h->post, Lj.u, rhs, s);
