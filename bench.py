@@ -120,7 +120,7 @@ def ncu_traffic(kernel):
     """DRAM traffic per launch of `kernel` from the committed ncu summary, if
     the kernel source is unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", f"ncu_{kernel}.md")
-    src = os.path.join(ROOT, "paper_1406_7808_gb300", "csrc", "kernels_fp64.cu")
+    src = os.path.join(ROOT, "paper_1406_7808_gb300", "csrc", "kernels.cu")
     if not os.path.exists(path) or not os.path.exists(src):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -129,7 +129,7 @@ def ncu_traffic(kernel):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernels_fp64.cu sha256[:16]") != sha:
+    if vals.get("kernels.cu sha256[:16]") != sha:
         return None
     try:
         return float(vals["dram bytes per launch (scaled to the bench workload)"])
@@ -271,7 +271,7 @@ def run_ours(args):
     sr.profile(False)
     dominant = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dominant]
-    achieved = d["fp64_ops"] / (d["ms"] / 1e3) / 1e12
+    achieved = d["ops"] / (d["ms"] / 1e3) / 1e12
     hbm_peak = None
     try:
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -282,14 +282,14 @@ def run_ours(args):
                 "traffic": ncu_traffic(dominant),
                 "peak_note": "float64 pipe: 2 lanes/clk/SM x 152 SMs x 2070 MHz (derived)",
                 "launches": d["launches"] // args.steps,
-                "fp64_ops_per_launch": d["fp64_ops"] / d["launches"],
+                "fp64_ops_per_launch": d["ops"] / d["launches"],
                 "ms_per_launch": d["ms"] / d["launches"],
                 "hbm_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9,
                 "hbm_frac_of_measured": (d["bytes"] / (d["ms"] / 1e3) / 1e9 / hbm_peak)
                 if hbm_peak else None}
     kernels = {k: {"ms_per_solve": v["ms"] / args.steps,
                    "share": v["ms"] / sum(x["ms"] for x in prof.values()),
-                   "tfp64ops": v["fp64_ops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] else None}
+                   "tfp64ops": v["ops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] else None}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
 
     # the same solve without segmental refinement (plain FMG), same f

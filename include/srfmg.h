@@ -53,8 +53,9 @@ extern "C" {
 
 /* precision modes */
 #define SR_FP64 0   /* every step in float64 */
-#define SR_MIXED 1  /* float32 smoothing and transfers inside a float64 defect
-                       correction loop (not in this version: SR_ERR_INVALID) */
+#define SR_MIXED 1  /* float32 smoothing, residuals and transfers inside a float64
+                       defect-correction loop; coarse right-hand sides (tau) and
+                       the coarsest solve in float64 arithmetic */
 
 typedef struct sr_fmg_s* sr_fmg_t;
 
@@ -74,8 +75,13 @@ typedef struct sr_fmg_s* sr_fmg_t;
  *   alpha, nu1, nu2   Chebyshev degrees of the F(alpha, nu1, nu2) cycle (1, 2, 2).
  *   cheb_lo, cheb_hi  Chebyshev interval as fractions of lambda_max(D^-1 A) = 2
  *             (D = 6 N^2 the diagonal); defaults 1/6 and 1.
- *   precision SR_FP64.
- *   n_outer   reserved for SR_MIXED (defect-correction passes).
+ *   precision SR_FP64, or SR_MIXED: the whole FMG / SR-FMG solve S32 runs in
+ *             float32 storage and arithmetic (tau right-hand sides and the
+ *             coarsest solve in float64 arithmetic) inside float64 defect
+ *             correction: u = S32(f), then n_outer - 1 times
+ *             u += S32(f - A u) with the defect in float64 (no counterpart in
+ *             the paper, which states no precision).
+ *   n_outer   SR_MIXED passes, 1..16 (0 = 2).
  */
 typedef struct {
   int n;
@@ -92,7 +98,8 @@ typedef struct {
 } sr_fmg_config;
 
 /* Fill cfg with the defaults for an n^3 grid: plain FMG, F(1,2,2), Chebyshev
- * interval [1/6, 1] * lambda_max, coarsest grid 2^3 or 3^3, SR_FP64. */
+ * interval [1/6, 1] * lambda_max, coarsest grid 2^3 or 3^3, buffers A = 8,
+ * B = 0, SR_FP64, n_outer = 2. */
 void sr_fmg_default_config(sr_fmg_config* cfg, int n);
 
 /* Validate cfg, build the level and segment plan and allocate the device
@@ -138,14 +145,16 @@ int sr_fmg_launches_per_solve(sr_fmg_t h, int* launches);
  * wait for the device.  sr_fmg_profile_read waits for the recorded launches
  * and returns, for one kernel kind (0 <= kind < sr_fmg_profile_kinds()), its
  * name (static string), launch count, summed device time in milliseconds, and
- * the summed algorithmic float64 operations (each add, multiply or fused
- * multiply-add counts one) and bytes (each array element read or written once)
- * of those launches.
+ * the summed algorithmic floating-point operations (each add, multiply or
+ * fused multiply-add counts one) and bytes (each array element read or
+ * written once) of those launches.  Kind names ending in "_f32" are float32
+ * storage and arithmetic, "_mixed" float32 storage with float64 arithmetic,
+ * the others float64.
  */
 int sr_fmg_profile(sr_fmg_t h, int enable);
 int sr_fmg_profile_kinds(void);
 int sr_fmg_profile_read(sr_fmg_t h, int kind, const char** name, long long* launches,
-                        double* ms, double* fp64_ops, double* bytes);
+                        double* ms, double* ops, double* bytes);
 
 /* Human-readable name of a status code (static string). */
 const char* sr_fmg_status_string(int status);

@@ -123,6 +123,17 @@ def solve(f, **kw):
     return u
 
 
+def solve_refined(f, n_outer=2, **kw):
+    """Defect correction around FMG / SR-FMG, all in float64:
+    u = S(f), then n_outer - 1 times u += S(f - A u).  The mixed-precision
+    mode runs the same loop with S in float32; this is its float64 reference."""
+    f = _grid(f)
+    u = solve(f, **kw)
+    for _ in range(n_outer - 1):
+        u = u + solve(residual(u, f), **kw)
+    return u
+
+
 def vcycle(f, u, **kw):
     """One FAS V-cycle FASMGV(L, u, f) on the global grid; returns the new u."""
     f = _grid(f)

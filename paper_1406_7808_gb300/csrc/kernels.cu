@@ -1,4 +1,7 @@
-// FP64 kernels of the FMG / SR-FMG solver (sm_103a).
+// Kernels of the FMG / SR-FMG solver (sm_103a), templated on the storage
+// type: float64 for the FP64 solver, float32 for the inner solver of the
+// mixed-precision mode (whose coarse right-hand sides, coarsest solve and
+// outer defect stay in float64 arithmetic).
 //
 // Every kernel runs over the boxes of one level: blockIdx.y selects the box
 // (one per segment on an SR level, a single box on a global level) and the
@@ -31,23 +34,32 @@ constexpr int kThreads = 256;
 
 // Constants handed to the kernels as parameters so that the compiler cannot
 // fold them into immediates (see above).  Values: one = 1, zero = 0.
+template <typename T>
 struct Fk {
-  double one, zero;
+  T one, zero;
 };
 
-__host__ __device__ inline Fk fk() { return Fk{1.0, 0.0}; }
+template <typename T>
+__host__ __device__ inline Fk<T> fk() {
+  return Fk<T>{T(1), T(0)};
+}
 
 __device__ __forceinline__ long long at(const BoxDesc& b, int x, int y, int z) {
   return b.base + (long long)(z - b.oz) * b.sz + (long long)(y - b.oy) * b.sy + (x - b.ox);
 }
 
-// -v, by flipping the sign bit of the high word on the integer pipe.  The
-// xor is inline PTX so that the compiler cannot turn it back into a float64
-// negation (which would cost a float64 instruction).
-__device__ __forceinline__ double negd(double v) {
+// -v, by flipping the sign bit on the integer pipe.  The xor is inline PTX so
+// that the compiler cannot turn it back into a floating-point negation (which
+// would cost a float64 instruction).
+__device__ __forceinline__ double negx(double v) {
   int hi = __double2hiint(v);
   asm("xor.b32 %0, %0, 0x80000000;" : "+r"(hi));
   return __hiloint2double(hi, __double2loint(v));
+}
+__device__ __forceinline__ float negx(float v) {
+  unsigned b = __float_as_uint(v);
+  asm("xor.b32 %0, %0, 0x80000000;" : "+r"(b));
+  return __uint_as_float(b);
 }
 
 // v or -v, selected on the integer pipe
@@ -56,6 +68,12 @@ __device__ __forceinline__ double neg_if(double v, bool flip) {
   const unsigned m = (unsigned)flip << 31;
   asm("xor.b32 %0, %0, %1;" : "+r"(hi) : "r"(m));
   return __hiloint2double(hi, __double2loint(v));
+}
+__device__ __forceinline__ float neg_if(float v, bool flip) {
+  unsigned b = __float_as_uint(v);
+  const unsigned m = (unsigned)flip << 31;
+  asm("xor.b32 %0, %0, %1;" : "+r"(b) : "r"(m));
+  return __uint_as_float(b);
 }
 
 __device__ __forceinline__ void region_of(const BoxDesc& b, int which, int lo[3], int hi[3]) {
@@ -68,22 +86,24 @@ __device__ __forceinline__ void region_of(const BoxDesc& b, int which, int lo[3]
   for (int d = 0; d < 3; ++d) { lo[d] = l[d]; hi[d] = h[d]; }
 }
 
-// The six neighbours of stored cell c at (x, y, z); a neighbour outside
-// [0, n) is minus the centre value (mirror through u = 0 on the face).
-__device__ __forceinline__ void neighbours(const double* __restrict__ a, long long c,
-                                           const BoxDesc& b, int n, int x, int y, int z,
-                                           double centre, double v[6]) {
-  const double m = negd(centre);
-  v[0] = (x > 0) ? a[c - 1] : m;
-  v[1] = (x < n - 1) ? a[c + 1] : m;
-  v[2] = (y > 0) ? a[c - b.sy] : m;
-  v[3] = (y < n - 1) ? a[c + b.sy] : m;
-  v[4] = (z > 0) ? a[c - b.sz] : m;
-  v[5] = (z < n - 1) ? a[c + b.sz] : m;
+// The six neighbours of stored cell c at (x, y, z), converted to A; a
+// neighbour outside [0, n) is minus the centre value (mirror through u = 0
+// on the face).
+template <typename A, typename T>
+__device__ __forceinline__ void neighbours(const T* __restrict__ a, long long c, const BoxDesc& b,
+                                           int n, int x, int y, int z, T centre, A v[6]) {
+  const T m = negx(centre);
+  v[0] = (A)((x > 0) ? a[c - 1] : m);
+  v[1] = (A)((x < n - 1) ? a[c + 1] : m);
+  v[2] = (A)((y > 0) ? a[c - b.sy] : m);
+  v[3] = (A)((y < n - 1) ? a[c + b.sy] : m);
+  v[4] = (A)((z > 0) ? a[c - b.sz] : m);
+  v[5] = (A)((z < n - 1) ? a[c + b.sz] : m);
 }
 
 // acc + w * (v0 + ... + v5) as six fused multiply-adds
-__device__ __forceinline__ double fma6(double w, const double v[6], double acc) {
+template <typename A>
+__device__ __forceinline__ A fma6(A w, const A v[6], A acc) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) acc = fma(w, v[i], acc);
   return acc;
@@ -105,10 +125,10 @@ __device__ __forceinline__ Cell cell_of(int i, const int lo[3], int ex, int ey) 
 // ---------------------------------------------------------------------------
 
 // r = D^-1 (f - A u) = f h^2/6 - u + (sum of neighbours)/6
-__global__ void __launch_bounds__(kThreads) k_cheb_residual(LevelView L,
-                                                            const double* __restrict__ u,
-                                                            double* __restrict__ r, FieldView f,
-                                                            double cf, double sixth) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_cheb_residual(LevelView L, const T* __restrict__ u,
+                                                            T* __restrict__ r, FieldT<T> f,
+                                                            T cf, T sixth) {
   __shared__ BoxDesc B, FB;
   if (threadIdx.x == 0) {
     B = L.boxes[blockIdx.y];
@@ -121,18 +141,18 @@ __global__ void __launch_bounds__(kThreads) k_cheb_residual(LevelView L,
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
-    const double uc = u[c];
-    double v[6];
-    neighbours(u, c, B, n, q.x, q.y, q.z, uc, v);
-    const double fv = f.p[at(FB, q.x, q.y, q.z)];
-    r[c] = fma6(sixth, v, fma(fv, cf, negd(uc)));
+    const T uc = u[c];
+    T v[6];
+    neighbours<T>(u, c, B, n, q.x, q.y, q.z, uc, v);
+    const T fv = f.p[at(FB, q.x, q.y, q.z)];
+    r[c] = fma6(sixth, v, fma(fv, cf, negx(uc)));
   }
 }
 
 // u += a r + b (sum of the neighbours of r)
-__global__ void __launch_bounds__(kThreads) k_cheb2_update(LevelView L, double* __restrict__ u,
-                                                           const double* __restrict__ r,
-                                                           double a, double b) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_cheb2_update(LevelView L, T* __restrict__ u,
+                                                           const T* __restrict__ r, T a, T b) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
@@ -142,29 +162,29 @@ __global__ void __launch_bounds__(kThreads) k_cheb2_update(LevelView L, double* 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
-    const double rc = r[c];
-    double v[6];
-    neighbours(r, c, B, n, q.x, q.y, q.z, rc, v);
+    const T rc = r[c];
+    T v[6];
+    neighbours<T>(r, c, B, n, q.x, q.y, q.z, rc, v);
     u[c] = fma6(b, v, fma(a, rc, u[c]));
   }
 }
 
 // d = alpha d + beta r (alpha == 0: d = beta r); u += d
-__global__ void __launch_bounds__(kThreads) k_cheb_step(LevelView L, double* __restrict__ u,
-                                                        double* __restrict__ d,
-                                                        const double* __restrict__ r,
-                                                        double alpha, double beta, int write_d,
-                                                        Fk k) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_cheb_step(LevelView L, T* __restrict__ u,
+                                                        T* __restrict__ d,
+                                                        const T* __restrict__ r, T alpha, T beta,
+                                                        int write_d, Fk<T> k) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
   const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
   const int ncell = ex * ey * ez;
-  const bool use_d = alpha != 0.0;
+  const bool use_d = alpha != T(0);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
-    double dn = fma(beta, r[c], k.zero);
+    T dn = fma(beta, r[c], k.zero);
     if (use_d) dn = fma(alpha, d[c], dn);
     if (write_d) d[c] = dn;
     u[c] = fma(dn, k.one, u[c]);
@@ -172,9 +192,10 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step(LevelView L, double* __r
 }
 
 // residual == 0: out = A u = n^2 (6 u - sum);  residual == 1: out = f - A u
-__global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const double* __restrict__ u,
-                                                    double* __restrict__ out, FieldView f,
-                                                    int residual, double c6, double cn, Fk k) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const T* __restrict__ u,
+                                                    T* __restrict__ out, FieldT<T> f,
+                                                    int residual, T c6, T cn, Fk<T> k) {
   __shared__ BoxDesc B, FB;
   if (threadIdx.x == 0) {
     B = L.boxes[blockIdx.y];
@@ -187,11 +208,11 @@ __global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const double* _
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
-    const double uc = u[c];
-    double v[6];
-    neighbours(u, c, B, n, q.x, q.y, q.z, uc, v);
+    const T uc = u[c];
+    T v[6];
+    neighbours<T>(u, c, B, n, q.x, q.y, q.z, uc, v);
     // apply: c6 = 6 n^2, cn = -n^2; residual: c6 = -6 n^2, cn = n^2
-    const double base = residual ? f.p[at(FB, q.x, q.y, q.z)] : k.zero;
+    const T base = residual ? f.p[at(FB, q.x, q.y, q.z)] : k.zero;
     out[c] = fma6(cn, v, fma(c6, uc, base));
   }
 }
@@ -201,13 +222,12 @@ __global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const double* _
 // operator values add up to n^2 (3 S - O), O the sum of the 24 neighbours
 // across the outer faces of the 2x2x2 block (each inner face cancels), so
 //   rho = (sum of f)/8 - (3 n^2/8) S + (n^2/8) O,   uhat = S/8.
-__global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F,
-                                                             const double* __restrict__ u,
-                                                             FieldView f, LevelView C,
-                                                             double* __restrict__ uhat_dst,
-                                                             double* __restrict__ rho_dst,
-                                                             double cS, double cO, double eighth,
-                                                             Fk k) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F, const T* __restrict__ u,
+                                                             FieldT<T> f, LevelView C,
+                                                             T* __restrict__ uhat_dst,
+                                                             T* __restrict__ rho_dst, T cS, T cO,
+                                                             T eighth, Fk<T> k) {
   __shared__ BoxDesc B, FB, CB;
   if (threadIdx.x == 0) {
     B = F.boxes[blockIdx.y];
@@ -225,14 +245,14 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F,
     const int x0 = 2 * q.x, y0 = 2 * q.y, z0 = 2 * q.z;
     const long long c0 = at(B, x0, y0, z0);
     const long long sy = B.sy, sz = B.sz;
-    double v[2][2][2];
+    T v[2][2][2];
 #pragma unroll
     for (int cz = 0; cz < 2; ++cz)
 #pragma unroll
       for (int cy = 0; cy < 2; ++cy)
 #pragma unroll
         for (int cx = 0; cx < 2; ++cx) v[cz][cy][cx] = u[c0 + cz * sz + cy * sy + cx];
-    double fs;
+    T fs;
     {
       const long long f0 = at(FB, x0, y0, z0);
       const long long fy = FB.sy, fz = FB.sz;
@@ -244,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F,
       fs = fma(f.p[f0 + fz + fy], k.one, fs);
       fs = fma(f.p[f0 + fz + fy + 1], k.one, fs);
     }
-    double S = fma(v[0][0][0], k.one, v[0][0][1]);
+    T S = fma(v[0][0][0], k.one, v[0][0][1]);
     S = fma(v[0][1][0], k.one, S);
     S = fma(v[0][1][1], k.one, S);
     S = fma(v[1][0][0], k.one, S);
@@ -254,30 +274,30 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F,
     // the 24 outer neighbours, mirrored with a sign flip outside the domain
     const bool xl = x0 > 0, xr = x0 + 2 < n, yl = y0 > 0, yr = y0 + 2 < n, zl = z0 > 0,
                zr = z0 + 2 < n;
-    double O = k.zero;
+    T O = k.zero;
 #pragma unroll
     for (int cz = 0; cz < 2; ++cz)
 #pragma unroll
       for (int cy = 0; cy < 2; ++cy) {
         const long long row = c0 + cz * sz + cy * sy;
-        O = fma(xl ? u[row - 1] : negd(v[cz][cy][0]), k.one, O);
-        O = fma(xr ? u[row + 2] : negd(v[cz][cy][1]), k.one, O);
+        O = fma(xl ? u[row - 1] : negx(v[cz][cy][0]), k.one, O);
+        O = fma(xr ? u[row + 2] : negx(v[cz][cy][1]), k.one, O);
       }
 #pragma unroll
     for (int cz = 0; cz < 2; ++cz)
 #pragma unroll
       for (int cx = 0; cx < 2; ++cx) {
         const long long col = c0 + cz * sz + cx;
-        O = fma(yl ? u[col - sy] : negd(v[cz][0][cx]), k.one, O);
-        O = fma(yr ? u[col + 2 * sy] : negd(v[cz][1][cx]), k.one, O);
+        O = fma(yl ? u[col - sy] : negx(v[cz][0][cx]), k.one, O);
+        O = fma(yr ? u[col + 2 * sy] : negx(v[cz][1][cx]), k.one, O);
       }
 #pragma unroll
     for (int cy = 0; cy < 2; ++cy)
 #pragma unroll
       for (int cx = 0; cx < 2; ++cx) {
         const long long pil = c0 + cy * sy + cx;
-        O = fma(zl ? u[pil - sz] : negd(v[0][cy][cx]), k.one, O);
-        O = fma(zr ? u[pil + 2 * sz] : negd(v[1][cy][cx]), k.one, O);
+        O = fma(zl ? u[pil - sz] : negx(v[0][cy][cx]), k.one, O);
+        O = fma(zr ? u[pil + 2 * sz] : negx(v[1][cy][cx]), k.one, O);
       }
     const long long cc = at(CB, q.x, q.y, q.z);
     rho_dst[cc] = fma(cS, S, fma(cO, O, fma(fs, eighth, k.zero)));
@@ -286,13 +306,14 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F,
 }
 
 // rhs = rho + A u inside the restriction region of the matching fine box,
-// A u elsewhere in the compute region; t = u on the whole stored box
+// A u elsewhere in the compute region (float64 arithmetic); t = u on the
+// whole stored box
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView F,
-                                                         const double* __restrict__ u,
-                                                         const double* __restrict__ rho,
-                                                         double* __restrict__ rhs,
-                                                         double* __restrict__ t, double c6,
-                                                         double cn, Fk k) {
+                                                         const T* __restrict__ u,
+                                                         const T* __restrict__ rho,
+                                                         T* __restrict__ rhs, T* __restrict__ t,
+                                                         double c6, double cn, Fk<double> k) {
   __shared__ BoxDesc B, FBx;
   if (threadIdx.x == 0) {
     B = C.boxes[blockIdx.y];
@@ -314,7 +335,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView 
     const bool inside_domain = q.x >= 0 && q.x < n && q.y >= 0 && q.y < n && q.z >= 0 && q.z < n;
     if (!inside_domain) continue;
     const long long c = at(B, q.x, q.y, q.z);
-    const double uc = u[c];
+    const T uc = u[c];
     t[c] = uc;
     const bool compute = q.x >= B.lo[0] && q.x < B.hi[0] && q.y >= B.lo[1] && q.y < B.hi[1] &&
                          q.z >= B.lo[2] && q.z < B.hi[2];
@@ -322,17 +343,19 @@ __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView 
     const bool inF = q.x >= FBx.rlo[0] && q.x < FBx.rhi[0] && q.y >= FBx.rlo[1] &&
                      q.y < FBx.rhi[1] && q.z >= FBx.rlo[2] && q.z < FBx.rhi[2];
     double v[6];
-    neighbours(u, c, B, n, q.x, q.y, q.z, uc, v);
-    rhs[c] = fma6(cn, v, fma(c6, uc, inF ? rho[c] : k.zero));
+    neighbours<double>(u, c, B, n, q.x, q.y, q.z, uc, v);
+    rhs[c] = (T)fma6(cn, v, fma(c6, (double)uc, inF ? (double)rho[c] : k.zero));
   }
 }
 
-// u = t, rhs = rho + A t on the whole (global) transition level
+// u = t, rhs = rho + A t on the whole (global) transition level (float64
+// arithmetic)
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
-                                                             const double* __restrict__ t,
-                                                             const double* __restrict__ rho,
-                                                             double* __restrict__ u,
-                                                             double* __restrict__ rhs, double c6,
+                                                             const T* __restrict__ t,
+                                                             const T* __restrict__ rho,
+                                                             T* __restrict__ u,
+                                                             T* __restrict__ rhs, double c6,
                                                              double cn) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[0];
@@ -343,11 +366,11 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
-    const double tc = t[c];
+    const T tc = t[c];
     double v[6];
-    neighbours(t, c, B, n, q.x, q.y, q.z, tc, v);
+    neighbours<double>(t, c, B, n, q.x, q.y, q.z, tc, v);
     u[c] = tc;
-    rhs[c] = fma6(cn, v, fma(c6, tc, rho[c]));
+    rhs[c] = (T)fma6(cn, v, fma(c6, (double)tc, (double)rho[c]));
   }
 }
 
@@ -357,11 +380,11 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
 // coarse neighbourhood.  add == 0: uf = P uc;  add == 1: uf += P (uc - tc).
 // Coarse cells outside the domain are mirrored with a sign flip; a neighbour
 // is read only if a child inside the fine region needs it.
-__global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const double* __restrict__ uc,
-                                                      const double* __restrict__ tc, LevelView F,
-                                                      double* __restrict__ uf, int add,
-                                                      double three, double w64, double mone,
-                                                      Fk k) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const T* __restrict__ uc,
+                                                      const T* __restrict__ tc, LevelView F,
+                                                      T* __restrict__ uf, int add, T three,
+                                                      T w64, T mone, Fk<T> k) {
   __shared__ BoxDesc B, CB;
   if (threadIdx.x == 0) {
     B = F.boxes[blockIdx.y];
@@ -387,18 +410,18 @@ __global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const double*
       hi_ok[d] = 2 * X[d] + 1 < phi[d];
     }
     // x pass over the 3x3 (z, y) lines of the coarse neighbourhood
-    double px[3][3][2];
+    T px[3][3][2];
 #pragma unroll
     for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy) {
         const bool need = (dz != 0 || lo_ok[2]) && (dz != 2 || hi_ok[2]) && (dy != 0 || lo_ok[1]) &&
                           (dy != 2 || hi_ok[1]);
-        double v[3];
+        T v[3];
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
           const bool needx = need && (dx != 0 || lo_ok[0]) && (dx != 2 || hi_ok[0]);
-          double val = k.zero;
+          T val = k.zero;
           if (needx) {
             int x = X[0] + dx - 1, y = X[1] + dy - 1, z = X[2] + dz - 1;
             bool flip = false;
@@ -414,7 +437,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const double*
         px[dz][dy][0] = fma(three, v[1], v[0]);
         px[dz][dy][1] = fma(three, v[1], v[2]);
       }
-    double py[3][2][2];
+    T py[3][2][2];
 #pragma unroll
     for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
@@ -434,7 +457,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const double*
         for (int cx = 0; cx < 2; ++cx) {
           const int fx = 2 * X[0] + cx;
           if (fx < plo[0] || fx >= phi[0]) continue;
-          const double e = fma(three, py[1][cy][cx], py[cz == 0 ? 0 : 2][cy][cx]);
+          const T e = fma(three, py[1][cy][cx], py[cz == 0 ? 0 : 2][cy][cx]);
           const long long c = at(B, fx, fy, fz);
           uf[c] = fma(w64, e, add ? uf[c] : k.zero);
         }
@@ -443,9 +466,10 @@ __global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const double*
   }
 }
 
-// One warp per row of the dense inverse.
-__global__ void k_coarse_solve(LevelView L, const double* __restrict__ minv, FieldView f,
-                               double* __restrict__ u, Fk k) {
+// One warp per row of the dense inverse (float64 arithmetic).
+template <typename T>
+__global__ void k_coarse_solve(LevelView L, const double* __restrict__ minv, FieldT<T> f,
+                               T* __restrict__ u, Fk<double> k) {
   const BoxDesc B = L.boxes[0];
   const BoxDesc FB = f.boxes[0];
   const int n = L.n, m = n * n * n;
@@ -455,24 +479,28 @@ __global__ void k_coarse_solve(LevelView L, const double* __restrict__ minv, Fie
   double s = k.zero;
   for (int j = lane; j < m; j += 32) {
     const int x = j % n, y = (j / n) % n, z = j / (n * n);
-    s = fma(minv[(long long)warp * m + j], f.p[at(FB, x, y, z)], s);
+    s = fma(minv[(long long)warp * m + j], (double)f.p[at(FB, x, y, z)], s);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s = fma(__shfl_xor_sync(0xffffffffu, s, o), k.one, s);
   if (lane == 0) {
     const int x = warp % n, y = (warp / n) % n, z = warp / (n * n);
-    u[at(B, x, y, z)] = s;
+    u[at(B, x, y, z)] = (T)s;
   }
 }
 
 __device__ __forceinline__ bool not_finite(double v) {
   return ((__double_as_longlong(v) >> 52) & 0x7ff) == 0x7ff;
 }
+__device__ __forceinline__ bool not_finite(float v) {
+  return ((__float_as_uint(v) >> 23) & 0xff) == 0xff;
+}
 
-__global__ void __launch_bounds__(kThreads) k_restrict_global(int nf, const double* __restrict__ ff,
-                                                              double* __restrict__ fc, int check,
-                                                              unsigned int* status, double eighth,
-                                                              Fk k) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_restrict_global(int nf, const T* __restrict__ ff,
+                                                              T* __restrict__ fc, int check,
+                                                              unsigned int* status, T eighth,
+                                                              Fk<T> k) {
   const int nc = nf / 2;
   const long long ncell = (long long)nc * nc * nc;
   bool bad = false;
@@ -483,9 +511,9 @@ __global__ void __launch_bounds__(kThreads) k_restrict_global(int nf, const doub
     const int y = (int)(t % nc), z = (int)(t / nc);
     const long long f0 = ((long long)(2 * z) * nf + 2 * y) * nf + 2 * x;
     const long long py = nf, pz = (long long)nf * nf;
-    const double a[8] = {ff[f0], ff[f0 + 1], ff[f0 + py], ff[f0 + py + 1],
-                         ff[f0 + pz], ff[f0 + pz + 1], ff[f0 + pz + py], ff[f0 + pz + py + 1]};
-    double s = k.zero;
+    const T a[8] = {ff[f0], ff[f0 + 1], ff[f0 + py], ff[f0 + py + 1],
+                    ff[f0 + pz], ff[f0 + pz + 1], ff[f0 + pz + py], ff[f0 + pz + py + 1]};
+    T s = k.zero;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       if (check) bad |= not_finite(a[j]);
@@ -496,9 +524,10 @@ __global__ void __launch_bounds__(kThreads) k_restrict_global(int nf, const doub
   if (check && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
 }
 
-__global__ void __launch_bounds__(kThreads) k_gather_genuine(LevelView L,
-                                                             const double* __restrict__ u,
-                                                             double* __restrict__ out) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_gather_genuine(LevelView L, const T* __restrict__ u,
+                                                             double* __restrict__ out, int add,
+                                                             Fk<double> k) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
@@ -509,7 +538,52 @@ __global__ void __launch_bounds__(kThreads) k_gather_genuine(LevelView L,
   const long long n = L.n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, lo, ex, ey);
-    out[(q.z * n + q.y) * n + q.x] = u[at(B, q.x, q.y, q.z)];
+    const long long o = (q.z * n + q.y) * n + q.x;
+    const double v = (double)u[at(B, q.x, q.y, q.z)];
+    out[o] = add ? fma(v, k.one, out[o]) : v;
+  }
+}
+
+// d = float(f - A u) with float64 arithmetic, or d = float(f) without u
+__global__ void __launch_bounds__(kThreads) k_defect(int n, const double* __restrict__ f,
+                                                     const double* __restrict__ u,
+                                                     float* __restrict__ d, unsigned int* status,
+                                                     double c6, double cn) {
+  const long long ncell = (long long)n * n * n;
+  const long long sy = n, sz = (long long)n * n;
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double fv = f[i];
+    bad |= not_finite(fv);
+    if (!u) {
+      d[i] = (float)fv;
+      continue;
+    }
+    const int x = (int)(i % n);
+    const long long t = i / n;
+    const int y = (int)(t % n), z = (int)(t / n);
+    const double uc = u[i];
+    const double m = negx(uc);
+    double v[6];
+    v[0] = (x > 0) ? u[i - 1] : m;
+    v[1] = (x < n - 1) ? u[i + 1] : m;
+    v[2] = (y > 0) ? u[i - sy] : m;
+    v[3] = (y < n - 1) ? u[i + sy] : m;
+    v[4] = (z > 0) ? u[i - sz] : m;
+    v[5] = (z < n - 1) ? u[i + sz] : m;
+    d[i] = (float)fma6(cn, v, fma(c6, uc, fv));
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
+}
+
+__global__ void __launch_bounds__(kThreads) k_accumulate(long long cells, const float* __restrict__ e,
+                                                         double* __restrict__ u, int add,
+                                                         Fk<double> k) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cells;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)e[i];
+    u[i] = add ? fma(v, k.one, u[i]) : v;
   }
 }
 
@@ -519,104 +593,160 @@ dim3 grid_for(const LevelView& L, int cells) {
   return dim3((unsigned)bx, (unsigned)L.nbox, 1);
 }
 
+unsigned flat_blocks(long long cells) {
+  long long blocks = (cells + kThreads - 1) / kThreads;
+  if (blocks > 152LL * 64) blocks = 152LL * 64;
+  if (blocks < 1) blocks = 1;
+  return (unsigned)blocks;
+}
+
 double sq(int n) { return (double)n * (double)n; }
 
 }  // namespace
 
-cudaError_t launch_cheb_residual(const LevelView& L, const double* u, double* r, FieldView f,
+template <typename T>
+cudaError_t launch_cheb_residual(const LevelView& L, const T* u, T* r, FieldT<T> f,
                                  cudaStream_t s) {
-  const double cf = 1.0 / (6.0 * sq(L.n));
-  k_cheb_residual<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, cf, 1.0 / 6.0);
+  const T cf = T(1.0 / (6.0 * sq(L.n)));
+  k_cheb_residual<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, cf, T(1.0 / 6.0));
   return cudaGetLastError();
 }
 
-cudaError_t launch_cheb2_update(const LevelView& L, double* u, const double* r, double a, double b,
+template <typename T>
+cudaError_t launch_cheb2_update(const LevelView& L, T* u, const T* r, double a, double b,
                                 cudaStream_t s) {
-  k_cheb2_update<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, a, b);
+  k_cheb2_update<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, T(a), T(b));
   return cudaGetLastError();
 }
 
-cudaError_t launch_cheb_step(const LevelView& L, double* u, double* d, const double* r,
-                             double alpha, double beta, int write_d, cudaStream_t s) {
-  k_cheb_step<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, d, r, alpha, beta, write_d,
-                                                            fk());
+template <typename T>
+cudaError_t launch_cheb_step(const LevelView& L, T* u, T* d, const T* r, double alpha,
+                             double beta, int write_d, cudaStream_t s) {
+  k_cheb_step<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, d, r, T(alpha), T(beta),
+                                                               write_d, fk<T>());
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply(const LevelView& L, const double* u, double* out, cudaStream_t s) {
-  FieldView none{nullptr, L.boxes, 0};
-  k_apply<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, out, none, 0, 6.0 * sq(L.n),
-                                                        -sq(L.n), fk());
+template <typename T>
+cudaError_t launch_apply(const LevelView& L, const T* u, T* out, cudaStream_t s) {
+  FieldT<T> none{nullptr, L.boxes, 0};
+  k_apply<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, out, none, 0, T(6.0 * sq(L.n)),
+                                                           T(-sq(L.n)), fk<T>());
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const LevelView& L, const double* u, FieldView f, double* r,
-                            cudaStream_t s) {
-  k_apply<<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, 1, -6.0 * sq(L.n), sq(L.n),
-                                                        fk());
+template <typename T>
+cudaError_t launch_residual(const LevelView& L, const T* u, FieldT<T> f, T* r, cudaStream_t s) {
+  k_apply<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, 1, T(-6.0 * sq(L.n)),
+                                                           T(sq(L.n)), fk<T>());
   return cudaGetLastError();
 }
 
-cudaError_t launch_resid_restrict(const LevelView& F, const double* u, FieldView f,
-                                  const LevelView& C, double* uhat_dst, double* rho_dst,
-                                  cudaStream_t s) {
+template <typename T>
+cudaError_t launch_resid_restrict(const LevelView& F, const T* u, FieldT<T> f,
+                                  const LevelView& C, T* uhat_dst, T* rho_dst, cudaStream_t s) {
   const double n2 = sq(F.n);
-  k_resid_restrict<<<grid_for(F, F.max_restrict), kThreads, 0, s>>>(
-      F, u, f, C, uhat_dst, rho_dst, -3.0 * n2 / 8.0, n2 / 8.0, 0.125, fk());
+  k_resid_restrict<T><<<grid_for(F, F.max_restrict), kThreads, 0, s>>>(
+      F, u, f, C, uhat_dst, rho_dst, T(-3.0 * n2 / 8.0), T(n2 / 8.0), T(0.125), fk<T>());
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_rhs(const LevelView& C, const LevelView& F, const double* u,
-                              const double* rho, double* rhs, double* t, cudaStream_t s) {
-  k_coarse_rhs<<<grid_for(C, C.max_stored), kThreads, 0, s>>>(C, F, u, rho, rhs, t,
-                                                              6.0 * sq(C.n), -sq(C.n), fk());
+template <typename T>
+cudaError_t launch_coarse_rhs(const LevelView& C, const LevelView& F, const T* u, const T* rho,
+                              T* rhs, T* t, cudaStream_t s) {
+  k_coarse_rhs<T><<<grid_for(C, C.max_stored), kThreads, 0, s>>>(C, F, u, rho, rhs, t,
+                                                                 6.0 * sq(C.n), -sq(C.n),
+                                                                 fk<double>());
   return cudaGetLastError();
 }
 
-cudaError_t launch_transition_rhs(const LevelView& C, const double* t, const double* rho,
-                                  double* u, double* rhs, cudaStream_t s) {
-  k_transition_rhs<<<grid_for(C, C.max_cells), kThreads, 0, s>>>(C, t, rho, u, rhs,
-                                                                  6.0 * sq(C.n), -sq(C.n));
+template <typename T>
+cudaError_t launch_transition_rhs(const LevelView& C, const T* t, const T* rho, T* u, T* rhs,
+                                  cudaStream_t s) {
+  k_transition_rhs<T><<<grid_for(C, C.max_cells), kThreads, 0, s>>>(C, t, rho, u, rhs,
+                                                                     6.0 * sq(C.n), -sq(C.n));
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong(const LevelView& C, const double* uc, const double* tc,
-                           const LevelView& F, double* uf, int add, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_prolong(const LevelView& C, const T* uc, const T* tc, const LevelView& F,
+                           T* uf, int add, cudaStream_t s) {
   // one thread per coarse cell over the children in the prolongation range:
   // at most about max_prolong / 8 plus the partial blocks on the faces
   int edge = 1;
   while ((long long)edge * edge * edge < F.max_prolong) ++edge;
   const int half = edge / 2 + 2;
-  k_prolong<<<grid_for(F, half * half * half), kThreads, 0, s>>>(C, uc, tc, F, uf, add, 3.0,
-                                                                 1.0 / 64.0, -1.0, fk());
+  k_prolong<T><<<grid_for(F, half * half * half), kThreads, 0, s>>>(
+      C, uc, tc, F, uf, add, T(3.0), T(1.0 / 64.0), T(-1.0), fk<T>());
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldView f, double* u,
+template <typename T>
+cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldT<T> f, T* u,
                                 cudaStream_t s) {
   const int m = L.n * L.n * L.n;
   const int warps_per_block = 8;
   const int blocks = (m + warps_per_block - 1) / warps_per_block;
-  k_coarse_solve<<<blocks, warps_per_block * 32, 0, s>>>(L, minv, f, u, fk());
+  k_coarse_solve<T><<<blocks, warps_per_block * 32, 0, s>>>(L, minv, f, u, fk<double>());
   return cudaGetLastError();
 }
 
-cudaError_t launch_restrict_global(int nf, const double* ff, double* fc, int check,
-                                   unsigned int* status, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_restrict_global(int nf, const T* ff, T* fc, int check, unsigned int* status,
+                                   cudaStream_t s) {
   const long long nc = nf / 2;
-  const long long cells = nc * nc * nc;
-  long long blocks = (cells + kThreads - 1) / kThreads;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  if (blocks < 1) blocks = 1;
-  k_restrict_global<<<(unsigned)blocks, kThreads, 0, s>>>(nf, ff, fc, check, status, 0.125,
-                                                          fk());
+  k_restrict_global<T><<<flat_blocks(nc * nc * nc), kThreads, 0, s>>>(nf, ff, fc, check, status,
+                                                                      T(0.125), fk<T>());
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_genuine(const LevelView& L, const double* u, double* out,
+template <typename T>
+cudaError_t launch_gather_genuine(const LevelView& L, const T* u, double* out, int add,
                                   cudaStream_t s) {
-  k_gather_genuine<<<grid_for(L, L.max_genuine), kThreads, 0, s>>>(L, u, out);
+  k_gather_genuine<T><<<grid_for(L, L.max_genuine), kThreads, 0, s>>>(L, u, out, add,
+                                                                      fk<double>());
   return cudaGetLastError();
 }
+
+cudaError_t launch_defect(int n, const double* f, const double* u, float* d,
+                          unsigned int* status, cudaStream_t s) {
+  const long long cells = (long long)n * n * n;
+  k_defect<<<flat_blocks(cells), kThreads, 0, s>>>(n, f, u, d, status, -6.0 * sq(n), sq(n));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(long long cells, const float* e, double* u, int add,
+                              cudaStream_t s) {
+  k_accumulate<<<flat_blocks(cells), kThreads, 0, s>>>(cells, e, u, add, fk<double>());
+  return cudaGetLastError();
+}
+
+#define SRFMG_INSTANTIATE(T)                                                                   \
+  template cudaError_t launch_cheb_residual<T>(const LevelView&, const T*, T*, FieldT<T>,      \
+                                               cudaStream_t);                                  \
+  template cudaError_t launch_cheb2_update<T>(const LevelView&, T*, const T*, double, double,  \
+                                              cudaStream_t);                                   \
+  template cudaError_t launch_cheb_step<T>(const LevelView&, T*, T*, const T*, double, double, \
+                                           int, cudaStream_t);                                 \
+  template cudaError_t launch_apply<T>(const LevelView&, const T*, T*, cudaStream_t);          \
+  template cudaError_t launch_residual<T>(const LevelView&, const T*, FieldT<T>, T*,           \
+                                          cudaStream_t);                                       \
+  template cudaError_t launch_resid_restrict<T>(const LevelView&, const T*, FieldT<T>,         \
+                                                const LevelView&, T*, T*, cudaStream_t);       \
+  template cudaError_t launch_coarse_rhs<T>(const LevelView&, const LevelView&, const T*,      \
+                                            const T*, T*, T*, cudaStream_t);                   \
+  template cudaError_t launch_transition_rhs<T>(const LevelView&, const T*, const T*, T*, T*,  \
+                                                cudaStream_t);                                 \
+  template cudaError_t launch_prolong<T>(const LevelView&, const T*, const T*,                 \
+                                         const LevelView&, T*, int, cudaStream_t);             \
+  template cudaError_t launch_coarse_solve<T>(const LevelView&, const double*, FieldT<T>, T*,  \
+                                              cudaStream_t);                                   \
+  template cudaError_t launch_restrict_global<T>(int, const T*, T*, int, unsigned int*,        \
+                                                 cudaStream_t);                                \
+  template cudaError_t launch_gather_genuine<T>(const LevelView&, const T*, double*, int,      \
+                                                cudaStream_t);
+
+SRFMG_INSTANTIATE(double)
+SRFMG_INSTANTIATE(float)
 
 }  // namespace srfmg

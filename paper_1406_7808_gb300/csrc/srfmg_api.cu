@@ -1,8 +1,9 @@
 // Host side of the solver: configuration checks, the level / segment plan,
-// device workspace, the launch sequence of FMG and SR-FMG, and the C ABI
-// declared in include/srfmg.h.
+// device workspace, the launch sequence of FMG and SR-FMG, the float64
+// defect-correction loop of the mixed-precision mode, and the C ABI declared
+// in include/srfmg.h.
 //
-// Launch sequence (Sec. 3 and Sec. 4 of the paper):
+// Launch sequence of one FMG / SR-FMG solve (Sec. 3 and Sec. 4 of the paper):
 //   f hierarchy      f_{k-1} = 8-child average of f_k, every level
 //   FMG              coarsest exact solve, then per global level: prolongation,
 //                    S^alpha, one FAS V-cycle (Fig. "Full multigrid")
@@ -14,6 +15,10 @@
 //                    Omega^C u Omega^GSR and S^nu2) (Figs. "FMG segmental
 //                    refinement", "FAS V-cycle segmental refinement")
 //   output           genuine cells of the finest level into u
+// Mixed precision (SR_MIXED): that solve runs in float32 storage and
+// arithmetic (coarse right-hand sides and the coarsest solve in float64
+// arithmetic) inside n_outer passes of float64 defect correction:
+//   pass 1: u = S32(f);  pass p > 1: d = f - A u (float64), u += S32(d).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,10 +36,10 @@ namespace {
 // ---------------------------------------------------------------------------
 // plan
 
-struct Level {
+// geometry of one level: its boxes on the host and the device
+struct Geom {
   int n = 0;
   int nbox = 0;
-  bool global = true;
   long long slot = 0;            // elements per box (SR levels)
   std::vector<BoxDesc> hboxes;
   BoxDesc* dboxes = nullptr;     // device copy of hboxes
@@ -42,25 +47,51 @@ struct Level {
   LevelView view{};
   // totals over the boxes, for the algorithmic work counts of the profiler
   double tot_cells = 0, tot_prolong = 0, tot_restrict = 0, tot_genuine = 0;
-  double *u = nullptr, *t = nullptr, *rhs = nullptr, *r = nullptr, *rho = nullptr,
-         *d = nullptr, *f = nullptr;
+};
+
+// a level's arrays in storage type T
+template <typename T>
+struct Level : Geom {
+  T *u = nullptr, *t = nullptr, *rhs = nullptr, *r = nullptr, *rho = nullptr, *d = nullptr,
+    *f = nullptr;
+};
+
+template <typename T>
+struct Hier {
+  std::vector<Level<T>> glev;  // global levels, glev[G-1] is level 0
+  std::vector<Level<T>> slev;  // SR levels, slev[k], k = 1..K
 };
 
 struct Cheb {
   int nu = 0;
-  double a = 0, b = 0;            // degree-2 polynomial form
+  double a = 0, b = 0;              // degree-2 polynomial form
   std::vector<double> alpha, beta;  // recurrence steps
 };
 
-// kernel kinds for the per-kernel profile
+// kernel kinds for the per-kernel profile: float64 storage and arithmetic;
+// "_f32": float32 storage and arithmetic; "_mixed": float32 storage, float64
+// arithmetic
 enum Kind {
   kChebResidual, kCheb2Update, kChebStep, kResidRestrict, kCoarseRhs, kTransitionRhs,
-  kProlongSet, kProlongAdd, kCoarseSolve, kRestrictF, kGather, kApply, kKinds
+  kProlongSet, kProlongAdd, kCoarseSolve, kRestrictF, kGather, kApply,
+  kChebResidualF32, kCheb2UpdateF32, kChebStepF32, kResidRestrictF32, kCoarseRhsMixed,
+  kTransitionRhsMixed, kProlongSetF32, kProlongAddF32, kCoarseSolveMixed, kRestrictFF32,
+  kGatherMixed, kDefect, kAccumulate, kKinds
 };
 const char* const kKindName[kKinds] = {
   "cheb_residual", "cheb2_update", "cheb_step", "resid_restrict", "coarse_rhs",
   "transition_rhs", "prolong", "prolong_correct", "coarse_solve", "restrict_f",
-  "gather_genuine", "apply"};
+  "gather_genuine", "apply",
+  "cheb_residual_f32", "cheb2_update_f32", "cheb_step_f32", "resid_restrict_f32",
+  "coarse_rhs_mixed", "transition_rhs_mixed", "prolong_f32", "prolong_correct_f32",
+  "coarse_solve_mixed", "restrict_f_f32", "gather_genuine_mixed", "defect", "accumulate"};
+
+// kind of a kernel for storage type T: float64 kinds shift to their float32
+// counterparts (same order)
+template <typename T>
+int kind_of(int k64) {
+  return sizeof(T) == 8 ? k64 : k64 + kChebResidualF32;
+}
 
 struct ProfRec {
   int kind;
@@ -81,10 +112,12 @@ struct Profile {
 struct sr_fmg_s {
   sr_fmg_config cfg{};
   int device = 0;
+  bool mixed = false;              // SR_MIXED: float32 inner solver
   int K = 0;                       // SR levels
-  int G = 0;                       // global levels, glev[G-1] is level 0
-  std::vector<Level> glev;
-  std::vector<Level> slev;         // slev[k], k = 1..K
+  int G = 0;                       // global levels
+  Hier<double> h64;                // levels of the float64 solver
+  Hier<float> h32;                 // levels of the float32 inner solver
+  float* defect = nullptr;         // SR_MIXED: float32 defect, n^3
   double* minv = nullptr;          // inverse of the coarsest operator
   unsigned int* status = nullptr;  // device status bits
   Cheb pre, post, fmg;
@@ -94,6 +127,9 @@ struct sr_fmg_s {
   double* hbuf_u = nullptr;
   int launches = 0;                // kernel launches queued by the last solve
   Profile prof;
+
+  Hier<double>& hier(double*) { return h64; }
+  Hier<float>& hier(float*) { return h32; }
 };
 
 namespace {
@@ -116,8 +152,8 @@ cudaEvent_t take_event(Profile& p) {
 }
 
 // Every kernel launch of a solve goes through here: it counts the launch and,
-// when profiling, brackets it with events and records the algorithmic float64
-// operations and bytes of the launch (units x per-unit counts).
+// when profiling, brackets it with events and records the algorithmic
+// floating-point operations and bytes of the launch (units x per-unit counts).
 template <class F>
 int launch(sr_fmg_s* h, int kind, double units, double ops_per_unit, double bytes_per_unit,
            cudaStream_t s, F&& fn) {
@@ -166,7 +202,8 @@ void schedule(const sr_fmg_config& c, int* J) {
 
 int check_config(const sr_fmg_config* c) {
   if (!c) return SR_ERR_INVALID;
-  if (c->precision != SR_FP64) return SR_ERR_INVALID;
+  if (c->precision != SR_FP64 && c->precision != SR_MIXED) return SR_ERR_INVALID;
+  if (c->precision == SR_MIXED && (c->n_outer < 0 || c->n_outer > 16)) return SR_ERR_INVALID;
   if (c->alpha < 0 || c->nu1 < 0 || c->nu2 < 0 || c->alpha > 16 || c->nu1 > 16 || c->nu2 > 16)
     return SR_ERR_INVALID;
   if (!(c->cheb_lo > 0.0 && c->cheb_hi > c->cheb_lo && c->cheb_hi < 4.0)) return SR_ERR_INVALID;
@@ -255,7 +292,7 @@ long long prod(const int lo[3], const int hi[3]) {
   return (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
 }
 
-int finish_level(sr_fmg_s* h, Level& L) {
+int finish_level(sr_fmg_s* h, Geom& L) {
   L.nbox = (int)L.hboxes.size();
   int rc = dalloc(h, &L.dboxes, L.hboxes.size());
   if (rc) return rc;
@@ -322,50 +359,56 @@ std::vector<double> coarsest_inverse(int n) {
   return minv;
 }
 
-int build_global_levels(sr_fmg_s* h, int ntop, bool finest_is_user) {
+// global levels of ntop down to the coarsest grid; with top_user the finest
+// level's u is the caller's array (no allocation); the finest level never
+// allocates f, t, rhs or rho (it reads f from the caller or the defect)
+template <typename T>
+int build_global_levels(sr_fmg_s* h, Hier<T>& H, int ntop, bool top_user) {
   const int m = halvings_to_coarsest(ntop, h->cfg.n_coarse);
   h->G = m + 1;
-  h->glev.resize(h->G);
+  H.glev.resize(h->G);
   const bool need_d = h->cfg.alpha > 2 || h->cfg.nu1 > 2 || h->cfg.nu2 > 2;
+  const bool sr = h->K > 0;
   for (int g = 0; g < h->G; ++g) {
-    Level& L = h->glev[g];
+    Level<T>& L = H.glev[g];
     L.n = ntop >> (h->G - 1 - g);
-    L.global = true;
     L.hboxes.assign(1, whole_box(L.n));
     if (g == 0) for (int d = 0; d < 3; ++d) { L.hboxes[0].rlo[d] = 0; L.hboxes[0].rhi[d] = 0; }
     int rc = finish_level(h, L);
     if (rc) return rc;
     const size_t cells = (size_t)L.n * L.n * L.n;
-    const bool top = (g == h->G - 1);
+    const bool finest = (g == h->G - 1) && !sr;
     if ((rc = dalloc(h, &L.r, cells))) return rc;
     if (need_d && (rc = dalloc(h, &L.d, cells))) return rc;
-    if (top && finest_is_user) continue;  // u and f are the caller's arrays
-    if ((rc = dalloc(h, &L.u, cells))) return rc;
+    if (!(finest && top_user) && (rc = dalloc(h, &L.u, cells))) return rc;
+    if (finest) continue;
     if ((rc = dalloc(h, &L.t, cells))) return rc;
     if ((rc = dalloc(h, &L.rhs, cells))) return rc;
     if ((rc = dalloc(h, &L.rho, cells))) return rc;
     if ((rc = dalloc(h, &L.f, cells))) return rc;
   }
-  const int nc = h->glev[0].n;
-  std::vector<double> minv = coarsest_inverse(nc);
-  int rc = dalloc(h, &h->minv, minv.size());
-  if (rc) return rc;
-  CK(cudaMemcpy(h->minv, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (!h->minv) {
+    const int nc = H.glev[0].n;
+    std::vector<double> minv = coarsest_inverse(nc);
+    int rc = dalloc(h, &h->minv, minv.size());
+    if (rc) return rc;
+    CK(cudaMemcpy(h->minv, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   return SR_OK;
 }
 
-int build_sr_levels(sr_fmg_s* h) {
+template <typename T>
+int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
   const sr_fmg_config& c = h->cfg;
   const int K = h->K;
   int J[SR_FMG_MAXK];
   schedule(c, J);
   const int nseg1 = c.n / c.seg;
   const bool need_d = c.alpha > 2 || c.nu1 > 2 || c.nu2 > 2;
-  h->slev.resize(K + 1);
+  H.slev.resize(K + 1);
   for (int k = 1; k <= K; ++k) {
-    Level& L = h->slev[k];
+    Level<T>& L = H.slev[k];
     L.n = c.n >> (K - k);
-    L.global = false;
     const int sk = c.seg >> (K - k);
     const int s0 = c.seg >> K;
     std::vector<BoxDesc> boxes;
@@ -422,163 +465,211 @@ int build_sr_levels(sr_fmg_s* h) {
 }
 
 // ---------------------------------------------------------------------------
-// launch sequence
+// launch sequence, for storage type T
 
-FieldView view_global(const Level& L, const double* p) { return FieldView{p, L.dglobal, 1}; }
-FieldView view_boxes(const Level& L, const double* p) { return FieldView{p, L.dboxes, 0}; }
+template <typename T>
+FieldT<T> view_global(const Geom& L, const T* p) { return FieldT<T>{p, L.dglobal, 1}; }
+template <typename T>
+FieldT<T> view_boxes(const Geom& L, const T* p) { return FieldT<T>{p, L.dboxes, 0}; }
 
-// algorithmic per-cell counts (float64 operations; bytes with each array
-// element read or written once) of each kernel
-int smooth(sr_fmg_s* h, const Level& L, const Cheb& c, double* u, FieldView f, cudaStream_t s) {
+// algorithmic per-cell counts (floating-point operations; bytes with each
+// array element read or written once) of each kernel
+template <typename T>
+int smooth(sr_fmg_s* h, const Level<T>& L, const Cheb& c, T* u, FieldT<T> f, cudaStream_t s) {
   if (c.nu == 0) return SR_OK;
   const double cells = L.tot_cells;
+  const double w = sizeof(T);
   if (c.nu == 2) {
-    LAUNCH(h, kChebResidual, cells, 7, 24, s, launch_cheb_residual(L.view, u, L.r, f, s));
-    LAUNCH(h, kCheb2Update, cells, 7, 24, s, launch_cheb2_update(L.view, u, L.r, c.a, c.b, s));
+    LAUNCH(h, kind_of<T>(kChebResidual), cells, 7, 3 * w, s,
+           launch_cheb_residual<T>(L.view, u, L.r, f, s));
+    LAUNCH(h, kind_of<T>(kCheb2Update), cells, 7, 3 * w, s,
+           launch_cheb2_update<T>(L.view, u, L.r, c.a, c.b, s));
     return SR_OK;
   }
   for (int m = 0; m < c.nu; ++m) {
-    LAUNCH(h, kChebResidual, cells, 7, 24, s, launch_cheb_residual(L.view, u, L.r, f, s));
+    LAUNCH(h, kind_of<T>(kChebResidual), cells, 7, 3 * w, s,
+           launch_cheb_residual<T>(L.view, u, L.r, f, s));
     const int write_d = (c.nu > 1 && m < c.nu - 1) ? 1 : 0;
     const bool with_d = write_d || c.alpha[m] != 0.0;
-    LAUNCH(h, kChebStep, cells, with_d ? 3 : 2, with_d ? 40 : 24, s,
-           launch_cheb_step(L.view, u, L.d, L.r, c.alpha[m], c.beta[m], write_d, s));
+    LAUNCH(h, kind_of<T>(kChebStep), cells, with_d ? 3 : 2, (with_d ? 5 : 3) * w, s,
+           launch_cheb_step<T>(L.view, u, L.d, L.r, c.alpha[m], c.beta[m], write_d, s));
   }
   return SR_OK;
 }
 
-// FASMGV on global level g (Fig. "FAS multigrid V-cycle"); u is L.u (or the
-// caller's u on the finest plain level).
-int vcycle_global(sr_fmg_s* h, int g, double* u, FieldView rhs, cudaStream_t s) {
-  Level& L = h->glev[g];
+// FASMGV on global level g (Fig. "FAS multigrid V-cycle"); u is the level's
+// u (or the caller's u on the finest plain FP64 level).
+template <typename T>
+int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStream_t s) {
+  Level<T>& L = H.glev[g];
+  const double w = sizeof(T);
   if (g == 0) {
     const double m = L.tot_cells;
-    LAUNCH(h, kCoarseSolve, m * m, 1, 8, s, launch_coarse_solve(L.view, h->minv, rhs, u, s));
+    LAUNCH(h, kind_of<T>(kCoarseSolve), m * m, 1, 8, s,
+           launch_coarse_solve<T>(L.view, h->minv, rhs, u, s));
     return SR_OK;
   }
-  Level& C = h->glev[g - 1];
+  Level<T>& C = H.glev[g - 1];
   int rc = smooth(h, L, h->pre, u, rhs, s);
   if (rc) return rc;
-  LAUNCH(h, kResidRestrict, L.tot_restrict, 41, 144, s,
-         launch_resid_restrict(L.view, u, rhs, C.view, C.u, C.rho, s));
-  LAUNCH(h, kCoarseRhs, C.tot_cells, 7, 32, s,
-         launch_coarse_rhs(C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
-  rc = vcycle_global(h, g - 1, C.u, view_global(C, C.rhs), s);
+  LAUNCH(h, kind_of<T>(kResidRestrict), L.tot_restrict, 42, 18 * w, s,
+         launch_resid_restrict<T>(L.view, u, rhs, C.view, C.u, C.rho, s));
+  LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, 7, 4 * w, s,
+         launch_coarse_rhs<T>(C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
+  rc = vcycle_global(h, H, g - 1, C.u, view_global<T>(C, C.rhs), s);
   if (rc) return rc;
-  LAUNCH(h, kProlongAdd, L.tot_prolong, 73.0 / 8.0, 18, s,
-         launch_prolong(C.view, C.u, C.t, L.view, u, 1, s));
+  LAUNCH(h, kind_of<T>(kProlongAdd), L.tot_prolong, 73.0 / 8.0, 2.25 * w, s,
+         launch_prolong<T>(C.view, C.u, C.t, L.view, u, 1, s));
   return smooth(h, L, h->post, u, rhs, s);
 }
 
-// the f hierarchy, FMG over the global levels (Fig. "Full multigrid")
-int run_fmg_global(sr_fmg_s* h, const double* ftop, double* utop, cudaStream_t s) {
+// FMG over the global levels (Fig. "Full multigrid"); ftop / utop are the
+// finest global level's f and u when there are no SR levels
+template <typename T>
+int run_fmg_global(sr_fmg_s* h, Hier<T>& H, const T* ftop, T* utop, cudaStream_t s) {
   const int top = h->G - 1;
-  auto fg = [&](int g) -> const double* { return (g == top && !h->K) ? ftop : h->glev[g].f; };
-  auto ug = [&](int g) -> double* { return (g == top && !h->K) ? utop : h->glev[g].u; };
+  const bool plain = h->K == 0;
+  auto fg = [&](int g) -> const T* { return (g == top && plain) ? ftop : H.glev[g].f; };
+  auto ug = [&](int g) -> T* { return (g == top && plain) ? utop : H.glev[g].u; };
   {
-    const double m = h->glev[0].tot_cells;
-    LAUNCH(h, kCoarseSolve, m * m, 1, 8, s,
-           launch_coarse_solve(h->glev[0].view, h->minv, view_global(h->glev[0], fg(0)), ug(0), s));
+    const double m = H.glev[0].tot_cells;
+    LAUNCH(h, kind_of<T>(kCoarseSolve), m * m, 1, 8, s,
+           launch_coarse_solve<T>(H.glev[0].view, h->minv, view_global<T>(H.glev[0], fg(0)),
+                                  ug(0), s));
   }
+  const double w = sizeof(T);
   for (int g = 1; g <= top; ++g) {
-    Level& L = h->glev[g];
-    LAUNCH(h, kProlongSet, L.tot_prolong, 46.0 / 8.0, 9, s,
-           launch_prolong(h->glev[g - 1].view, ug(g - 1), nullptr, L.view, ug(g), 0, s));
-    FieldView f = view_global(L, fg(g));
+    Level<T>& L = H.glev[g];
+    LAUNCH(h, kind_of<T>(kProlongSet), L.tot_prolong, 46.0 / 8.0, 1.125 * w, s,
+           launch_prolong<T>(H.glev[g - 1].view, ug(g - 1), nullptr, L.view, ug(g), 0, s));
+    FieldT<T> f = view_global<T>(L, fg(g));
     int rc = smooth(h, L, h->fmg, ug(g), f, s);
     if (rc) return rc;
-    rc = vcycle_global(h, g, ug(g), f, s);
+    rc = vcycle_global(h, H, g, ug(g), f, s);
     if (rc) return rc;
   }
   return SR_OK;
 }
 
-int f_hierarchy(sr_fmg_s* h, const double* f, cudaStream_t s) {
-  const double* src = f;
+// f_{k-1} = average of f_k down all levels, from the finest f (n^3)
+template <typename T>
+int f_hierarchy(sr_fmg_s* h, Hier<T>& H, const T* f, int check, cudaStream_t s) {
+  const T* src = f;
   int nsrc = h->cfg.n;
-  int check = 1;
+  const double w = sizeof(T);
   for (int k = h->K - 1; k >= 1; --k) {
-    const double nc = h->slev[k].n;
-    LAUNCH(h, kRestrictF, nc * nc * nc, 8, 72, s,
-           launch_restrict_global(nsrc, src, h->slev[k].f, check, h->status, s));
+    const double nc = H.slev[k].n;
+    LAUNCH(h, kind_of<T>(kRestrictF), nc * nc * nc, 8, 9 * w, s,
+           launch_restrict_global<T>(nsrc, src, H.slev[k].f, check, h->status, s));
     check = 0;
-    src = h->slev[k].f;
-    nsrc = h->slev[k].n;
+    src = H.slev[k].f;
+    nsrc = H.slev[k].n;
   }
   for (int g = h->G - (h->K ? 1 : 2); g >= 0; --g) {
-    const double nc = h->glev[g].n;
-    LAUNCH(h, kRestrictF, nc * nc * nc, 8, 72, s,
-           launch_restrict_global(nsrc, src, h->glev[g].f, check, h->status, s));
+    const double nc = H.glev[g].n;
+    LAUNCH(h, kind_of<T>(kRestrictF), nc * nc * nc, 8, 9 * w, s,
+           launch_restrict_global<T>(nsrc, src, H.glev[g].f, check, h->status, s));
     check = 0;
-    src = h->glev[g].f;
-    nsrc = h->glev[g].n;
+    src = H.glev[g].f;
+    nsrc = H.glev[g].n;
   }
   return SR_OK;
 }
 
-int run_sr(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
+// the SR stages k = 1..K after the global FMG; the genuine finest cells go to
+// u (add == 0) or are added to it (add == 1)
+template <typename T>
+int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t s) {
   const int K = h->K;
-  Level& L0 = h->glev[h->G - 1];
-  auto fview = [&](int k) -> FieldView {
-    return view_global(h->slev[k], k == K ? f : h->slev[k].f);
+  Level<T>& L0 = H.glev[h->G - 1];
+  const double w = sizeof(T);
+  auto fview = [&](int k) -> FieldT<T> {
+    return view_global<T>(H.slev[k], k == K ? f : H.slev[k].f);
   };
   for (int k = 1; k <= K; ++k) {
-    Level& Lk = h->slev[k];
+    Level<T>& Lk = H.slev[k];
     // u_k <- Pi u_{k-1} on Omega^C_k u Omega^GSR_k, then S^alpha on Omega^C_k
     {
-      const Level& C = (k == 1) ? L0 : h->slev[k - 1];
-      LAUNCH(h, kProlongSet, Lk.tot_prolong, 46.0 / 8.0, 9, s,
-             launch_prolong(C.view, C.u, nullptr, Lk.view, Lk.u, 0, s));
+      const Level<T>& C = (k == 1) ? L0 : H.slev[k - 1];
+      LAUNCH(h, kind_of<T>(kProlongSet), Lk.tot_prolong, 46.0 / 8.0, 1.125 * w, s,
+             launch_prolong<T>(C.view, C.u, nullptr, Lk.view, Lk.u, 0, s));
       int rc = smooth(h, Lk, h->fmg, Lk.u, fview(k), s);
       if (rc) return rc;
     }
     // FASMGVSR(k): down-leg
     for (int j = k; j >= 1; --j) {
-      Level& Lj = h->slev[j];
-      const FieldView rhs = (j == k) ? fview(k) : view_boxes(Lj, Lj.rhs);
+      Level<T>& Lj = H.slev[j];
+      const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
       int rc = smooth(h, Lj, h->pre, Lj.u, rhs, s);
       if (rc) return rc;
       if (j > 1) {
-        Level& C = h->slev[j - 1];
-        LAUNCH(h, kResidRestrict, Lj.tot_restrict, 41, 144, s,
-               launch_resid_restrict(Lj.view, Lj.u, rhs, C.view, C.u, C.rho, s));
-        LAUNCH(h, kCoarseRhs, C.tot_cells, 7, 32, s,
-               launch_coarse_rhs(C.view, Lj.view, C.u, C.rho, C.rhs, C.t, s));
+        Level<T>& C = H.slev[j - 1];
+        LAUNCH(h, kind_of<T>(kResidRestrict), Lj.tot_restrict, 42, 18 * w, s,
+               launch_resid_restrict<T>(Lj.view, Lj.u, rhs, C.view, C.u, C.rho, s));
+        LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, 7, 4 * w, s,
+               launch_coarse_rhs<T>(C.view, Lj.view, C.u, C.rho, C.rhs, C.t, s));
       } else {
-        LAUNCH(h, kResidRestrict, Lj.tot_restrict, 41, 144, s,
-               launch_resid_restrict(Lj.view, Lj.u, rhs, L0.view, L0.t, L0.rho, s));
+        LAUNCH(h, kind_of<T>(kResidRestrict), Lj.tot_restrict, 42, 18 * w, s,
+               launch_resid_restrict<T>(Lj.view, Lj.u, rhs, L0.view, L0.t, L0.rho, s));
       }
     }
     // transition level: u_0 <- \hat I u_1, t_0 = u_0, r_0 = rho_0 + L_0 u_0, FASMGV
-    LAUNCH(h, kTransitionRhs, L0.tot_cells, 7, 32, s,
-           launch_transition_rhs(L0.view, L0.t, L0.rho, L0.u, L0.rhs, s));
-    int rc = vcycle_global(h, h->G - 1, L0.u, view_global(L0, L0.rhs), s);
+    LAUNCH(h, kind_of<T>(kTransitionRhs), L0.tot_cells, 7, 4 * w, s,
+           launch_transition_rhs<T>(L0.view, L0.t, L0.rho, L0.u, L0.rhs, s));
+    int rc = vcycle_global(h, H, h->G - 1, L0.u, view_global<T>(L0, L0.rhs), s);
     if (rc) return rc;
     // up-leg
     for (int j = 1; j <= k; ++j) {
-      Level& Lj = h->slev[j];
-      const Level& C = (j == 1) ? L0 : h->slev[j - 1];
-      LAUNCH(h, kProlongAdd, Lj.tot_prolong, 73.0 / 8.0, 18, s,
-             launch_prolong(C.view, C.u, C.t, Lj.view, Lj.u, 1, s));
-      const FieldView rhs = (j == k) ? fview(k) : view_boxes(Lj, Lj.rhs);
+      Level<T>& Lj = H.slev[j];
+      const Level<T>& C = (j == 1) ? L0 : H.slev[j - 1];
+      LAUNCH(h, kind_of<T>(kProlongAdd), Lj.tot_prolong, 73.0 / 8.0, 2.25 * w, s,
+             launch_prolong<T>(C.view, C.u, C.t, Lj.view, Lj.u, 1, s));
+      const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
       rc = smooth(h, Lj, h->post, Lj.u, rhs, s);
       if (rc) return rc;
     }
   }
-  LAUNCH(h, kGather, h->slev[K].tot_genuine, 0, 16, s,
-         launch_gather_genuine(h->slev[K].view, h->slev[K].u, u, s));
+  LAUNCH(h, kind_of<T>(kGather), H.slev[K].tot_genuine, add ? 1 : 0, w + (add ? 16 : 8), s,
+         launch_gather_genuine<T>(H.slev[K].view, H.slev[K].u, u, add, s));
+  return SR_OK;
+}
+
+// one FMG / SR-FMG solve of A x = f in storage type T.  With T = double and
+// no SR levels the solve works in the caller's out directly; otherwise the
+// result goes to out (add == 1: out += x).
+template <typename T>
+int solve_once(sr_fmg_s* h, const T* f, double* out, int add, int check, cudaStream_t s) {
+  Hier<T>& H = h->hier((T*)nullptr);
+  int rc = f_hierarchy<T>(h, H, f, check, s);
+  if (rc) return rc;
+  const bool user_top = (sizeof(T) == 8) && h->K == 0;
+  T* utop = user_top ? reinterpret_cast<T*>(out) : H.glev[h->G - 1].u;
+  rc = run_fmg_global<T>(h, H, f, utop, s);
+  if (rc) return rc;
+  if (h->K) return run_sr<T>(h, H, f, out, add, s);
+  if (!user_top) {
+    const long long cells = (long long)h->cfg.n * h->cfg.n * h->cfg.n;
+    LAUNCH(h, kAccumulate, (double)cells, add ? 1 : 0, add ? 20 : 12, s,
+           launch_accumulate(cells, reinterpret_cast<const float*>(utop), out, add, s));
+  }
   return SR_OK;
 }
 
 int enqueue_solve(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
   h->launches = 0;
   CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned int), s));
-  int rc = f_hierarchy(h, f, s);
-  if (rc) return rc;
-  rc = run_fmg_global(h, f, u, s);
-  if (rc) return rc;
-  if (h->K) rc = run_sr(h, f, u, s);
-  return rc;
+  if (!h->mixed) return solve_once<double>(h, f, u, 0, 1, s);
+  // float64 defect correction around the float32 solve
+  const int n = h->cfg.n;
+  const double cells = (double)n * n * n;
+  const int passes = h->cfg.n_outer > 0 ? h->cfg.n_outer : 2;
+  for (int p = 1; p <= passes; ++p) {
+    LAUNCH(h, kDefect, cells, p == 1 ? 0 : 7, p == 1 ? 12 : 20, s,
+           launch_defect(n, f, p == 1 ? nullptr : u, h->defect, h->status, s));
+    int rc = solve_once<float>(h, h->defect, u, p > 1 ? 1 : 0, 0, s);
+    if (rc) return rc;
+  }
+  return SR_OK;
 }
 
 bool is_device_ptr(const void* p) {
@@ -650,7 +741,7 @@ void sr_fmg_default_config(sr_fmg_config* cfg, int n) {
   cfg->cheb_lo = 1.0 / 6.0;
   cfg->cheb_hi = 1.0;
   cfg->precision = SR_FP64;
-  cfg->n_outer = 0;
+  cfg->n_outer = 2;
 }
 
 int sr_fmg_create(sr_fmg_t* out, const sr_fmg_config* cfg) {
@@ -670,13 +761,21 @@ int sr_fmg_create(sr_fmg_t* out, const sr_fmg_config* cfg) {
     delete h;
     return SR_ERR_CUDA;
   }
+  h->mixed = cfg->precision == SR_MIXED;
   h->K = (cfg->seg > 0) ? cfg->K : 0;
   h->pre = chebyshev(cfg->nu1, cfg->cheb_lo, cfg->cheb_hi);
   h->post = chebyshev(cfg->nu2, cfg->cheb_lo, cfg->cheb_hi);
   h->fmg = chebyshev(cfg->alpha, cfg->cheb_lo, cfg->cheb_hi);
   rc = dalloc(h, &h->status, 1);
-  if (!rc) rc = build_global_levels(h, cfg->n >> h->K, h->K == 0);
-  if (!rc && h->K) rc = build_sr_levels(h);
+  if (!h->mixed) {
+    if (!rc) rc = build_global_levels<double>(h, h->h64, cfg->n >> h->K, h->K == 0);
+    if (!rc && h->K) rc = build_sr_levels<double>(h, h->h64);
+  } else {
+    const size_t cells = (size_t)cfg->n * cfg->n * cfg->n;
+    if (!rc) rc = dalloc(h, &h->defect, cells);
+    if (!rc) rc = build_global_levels<float>(h, h->h32, cfg->n >> h->K, false);
+    if (!rc && h->K) rc = build_sr_levels<float>(h, h->h32);
+  }
   if (rc) {
     free_all(h);
     delete h;
@@ -772,7 +871,7 @@ int sr_fmg_profile(sr_fmg_t h, int enable) {
 int sr_fmg_profile_kinds(void) { return kKinds; }
 
 int sr_fmg_profile_read(sr_fmg_t h, int kind, const char** name, long long* launches,
-                        double* ms, double* fp64_ops, double* bytes) {
+                        double* ms, double* ops, double* bytes) {
   if (!h || kind < 0 || kind >= kKinds) return SR_ERR_INVALID;
   DeviceGuard g(h->device);
   int rc = collect_profile(h);
@@ -780,7 +879,7 @@ int sr_fmg_profile_read(sr_fmg_t h, int kind, const char** name, long long* laun
   if (name) *name = kKindName[kind];
   if (launches) *launches = h->prof.launches[kind];
   if (ms) *ms = h->prof.ms[kind];
-  if (fp64_ops) *fp64_ops = h->prof.ops[kind];
+  if (ops) *ops = h->prof.ops[kind];
   if (bytes) *bytes = h->prof.bytes[kind];
   return SR_OK;
 }
@@ -800,13 +899,13 @@ const char* sr_fmg_status_string(int status) {
 }
 
 // ---------------------------------------------------------------------------
-// single components on whole grids
+// single components on whole grids (float64)
 
 namespace {
 
 struct TmpLevel {
   sr_fmg_s h;
-  Level L;
+  Level<double> L;
   ~TmpLevel() { free_all(&h); }
 };
 
@@ -825,7 +924,7 @@ int sr_op_apply(int n, const double* u, double* out, void* stream) {
   TmpLevel T;
   int rc = tmp_level(T, n);
   if (rc) return rc;
-  CK(launch_apply(T.L.view, u, out, (cudaStream_t)stream));
+  CK(launch_apply<double>(T.L.view, u, out, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
 }
@@ -835,7 +934,8 @@ int sr_op_residual(int n, const double* f, const double* u, double* r, void* str
   TmpLevel T;
   int rc = tmp_level(T, n);
   if (rc) return rc;
-  CK(launch_residual(T.L.view, u, view_global(T.L, f), r, (cudaStream_t)stream));
+  CK(launch_residual<double>(T.L.view, u, view_global<double>(T.L, f), r,
+                             (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
 }
@@ -851,7 +951,7 @@ int sr_op_smooth(int n, int nu, double cheb_lo, double cheb_hi, const double* f,
   if (!rc) rc = dalloc(&T.h, &T.L.d, cells);
   if (rc) return rc;
   Cheb c = chebyshev(nu, cheb_lo, cheb_hi);
-  rc = smooth(&T.h, T.L, c, u, view_global(T.L, f), (cudaStream_t)stream);
+  rc = smooth<double>(&T.h, T.L, c, u, view_global<double>(T.L, f), (cudaStream_t)stream);
   if (rc) return rc;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
@@ -862,7 +962,7 @@ int sr_op_restrict(int n, const double* a, double* ac, void* stream) {
   TmpLevel T;
   int rc = dalloc(&T.h, &T.h.status, 1);
   if (rc) return rc;
-  CK(launch_restrict_global(n, a, ac, 0, T.h.status, (cudaStream_t)stream));
+  CK(launch_restrict_global<double>(n, a, ac, 0, T.h.status, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
 }
@@ -873,7 +973,7 @@ int sr_op_prolong(int nc, const double* ac, double* af, void* stream) {
   int rc = tmp_level(C, nc);
   if (!rc) rc = tmp_level(F, 2 * nc);
   if (rc) return rc;
-  CK(launch_prolong(C.L.view, ac, nullptr, F.L.view, af, 0, (cudaStream_t)stream));
+  CK(launch_prolong<double>(C.L.view, ac, nullptr, F.L.view, af, 0, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
 }
@@ -888,7 +988,8 @@ int sr_op_coarse_solve(int n, const double* f, double* u, void* stream) {
   rc = dalloc(&T.h, &dm, minv.size());
   if (rc) return rc;
   CK(cudaMemcpy(dm, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice));
-  CK(launch_coarse_solve(T.L.view, dm, view_global(T.L, f), u, (cudaStream_t)stream));
+  CK(launch_coarse_solve<double>(T.L.view, dm, view_global<double>(T.L, f), u,
+                                 (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
 }
@@ -898,11 +999,13 @@ int sr_op_vcycle(const sr_fmg_config* cfg, const double* f, double* u, void* str
   sr_fmg_config c = *cfg;
   c.seg = 0;
   c.K = 0;
+  c.precision = SR_FP64;
   sr_fmg_t h = nullptr;
   int rc = sr_fmg_create(&h, &c);
   if (rc) return rc;
   const int top = h->G - 1;
-  rc = vcycle_global(h, top, u, view_global(h->glev[top], f), (cudaStream_t)stream);
+  rc = vcycle_global<double>(h, h->h64, top, u, view_global<double>(h->h64.glev[top], f),
+                             (cudaStream_t)stream);
   if (!rc && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = SR_ERR_CUDA;
   sr_fmg_destroy(h);
   return rc;

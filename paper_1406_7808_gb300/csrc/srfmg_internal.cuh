@@ -1,6 +1,7 @@
 // Internal definitions shared by the solver's translation units: the box
 // descriptors that describe where each level lives in device memory, and the
-// launchers of the FP64 kernels.
+// launchers of the kernels (kernels.cu), instantiated for float64 (the FP64
+// solver) and float32 (the inner solver of the mixed-precision mode).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -13,7 +14,7 @@ namespace srfmg {
 // stored with a one-cell ghost shell that holds the frozen SR ghost values.
 // Element (x, y, z) of a box lives at
 //   base + (z - oz) * sz + (y - oy) * sy + (x - ox)
-// in every array of its level.
+// in every array of its level (offsets in elements, whatever the type).
 struct BoxDesc {
   int lo[3], hi[3];    // compute region Omega^C
   int rlo[3], rhi[3];  // restriction target on the next coarser level
@@ -40,62 +41,88 @@ struct LevelView {
 // A field read with a possibly different layout than the level's boxes (the
 // caller's global f on the finest SR level): single != 0 means every box
 // reads through boxes[0].
-struct FieldView {
-  const double* p;
+template <typename T>
+struct FieldT {
+  const T* p;
   const BoxDesc* boxes;
   int single;
 };
+using FieldView = FieldT<double>;
 
 enum Region { kCompute = 0, kProlong = 1, kRestrict = 2, kGenuine = 3 };
 
-// ---- launchers (kernels_fp64.cu); all enqueue on stream and return the
-// ---- launch status.
+// ---- launchers; all enqueue on stream and return the launch status.  T is
+// ---- the storage and arithmetic type, except where noted.
 
 // r = D^-1 (f - A u) on the compute region, D = 6 n^2.
-cudaError_t launch_cheb_residual(const LevelView& L, const double* u, double* r, FieldView f,
+template <typename T>
+cudaError_t launch_cheb_residual(const LevelView& L, const T* u, T* r, FieldT<T> f,
                                  cudaStream_t s);
 // Chebyshev degree 2 finish: u += a r + b * (sum of the 6 neighbours of r),
 // neighbours outside the domain mirrored with a sign flip, ghosts inside the
 // domain read as stored (zero for the residual array).
-cudaError_t launch_cheb2_update(const LevelView& L, double* u, const double* r, double a,
-                                double b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cheb2_update(const LevelView& L, T* u, const T* r, double a, double b,
+                                cudaStream_t s);
 // One step of the Chebyshev recurrence: d = alpha d + beta r, u += d
 // (d untouched and unused when write_d == 0 and alpha == 0).
-cudaError_t launch_cheb_step(const LevelView& L, double* u, double* d, const double* r,
-                             double alpha, double beta, int write_d, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cheb_step(const LevelView& L, T* u, T* d, const T* r, double alpha,
+                             double beta, int write_d, cudaStream_t s);
 // out = A u on the compute region.
-cudaError_t launch_apply(const LevelView& L, const double* u, double* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply(const LevelView& L, const T* u, T* out, cudaStream_t s);
 // r = f - A u on the compute region.
-cudaError_t launch_residual(const LevelView& L, const double* u, FieldView f, double* r,
-                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual(const LevelView& L, const T* u, FieldT<T> f, T* r, cudaStream_t s);
 // For every coarse cell of the fine boxes' restriction region:
 // uhat = average of the 8 children of u, rho = average of the 8 children of
 // (f - A u).  uhat_dst and rho_dst are arrays of the coarse level.
-cudaError_t launch_resid_restrict(const LevelView& F, const double* u, FieldView f,
-                                  const LevelView& C, double* uhat_dst, double* rho_dst,
-                                  cudaStream_t s);
+template <typename T>
+cudaError_t launch_resid_restrict(const LevelView& F, const T* u, FieldT<T> f,
+                                  const LevelView& C, T* uhat_dst, T* rho_dst, cudaStream_t s);
 // Coarse right-hand side of the FAS cycle (Eq. eq:cresid2 and its SR form):
 // rhs = rho + A u inside the fine boxes' restriction region, rhs = A u on the
-// rest of the compute region; t = u on the whole stored box.
-cudaError_t launch_coarse_rhs(const LevelView& C, const LevelView& F, const double* u,
-                              const double* rho, double* rhs, double* t, cudaStream_t s);
+// rest of the compute region; t = u on the whole stored box.  Arithmetic in
+// float64 whatever T.
+template <typename T>
+cudaError_t launch_coarse_rhs(const LevelView& C, const LevelView& F, const T* u, const T* rho,
+                              T* rhs, T* t, cudaStream_t s);
 // Transition level: u = t (the owner-written restricted solution) and
-// rhs = rho + A t on the whole (global) level.
-cudaError_t launch_transition_rhs(const LevelView& C, const double* t, const double* rho,
-                                  double* u, double* rhs, cudaStream_t s);
+// rhs = rho + A t on the whole (global) level; float64 arithmetic.
+template <typename T>
+cudaError_t launch_transition_rhs(const LevelView& C, const T* t, const T* rho, T* u, T* rhs,
+                                  cudaStream_t s);
 // Prolongation onto the fine boxes' prolongation range:
 // add == 0: uf = P uc;  add == 1: uf += P (uc - tc).
-cudaError_t launch_prolong(const LevelView& C, const double* uc, const double* tc,
-                           const LevelView& F, double* uf, int add, cudaStream_t s);
-// Coarsest grid: u = Minv f, Minv the dense inverse (m x m, m = n^3).
-cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldView f, double* u,
+template <typename T>
+cudaError_t launch_prolong(const LevelView& C, const T* uc, const T* tc, const LevelView& F,
+                           T* uf, int add, cudaStream_t s);
+// Coarsest grid: u = Minv f, Minv the dense float64 inverse (m x m, m = n^3);
+// float64 arithmetic.
+template <typename T>
+cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldT<T> f, T* u,
                                 cudaStream_t s);
 // f_c = 8-child average of f_f on whole global levels; sets *status |= 1 if
 // an input value is not finite (check != 0).
-cudaError_t launch_restrict_global(int nf, const double* ff, double* fc, int check,
-                                   unsigned int* status, cudaStream_t s);
-// Copy the genuine cells of every box of L into the global n^3 array out.
-cudaError_t launch_gather_genuine(const LevelView& L, const double* u, double* out,
+template <typename T>
+cudaError_t launch_restrict_global(int nf, const T* ff, T* fc, int check, unsigned int* status,
+                                   cudaStream_t s);
+// Genuine cells of every box of L into the global n^3 float64 array out:
+// out = u (add == 0) or out += u (add == 1).
+template <typename T>
+cudaError_t launch_gather_genuine(const LevelView& L, const T* u, double* out, int add,
                                   cudaStream_t s);
+
+// ---- float64 defect correction around the float32 inner solver
+
+// d = float(f - A u) on the whole n^3 grid (float64 arithmetic, unpadded
+// arrays); with u == nullptr, d = float(f).  Sets *status |= 1 if f holds a
+// value that is not finite.
+cudaError_t launch_defect(int n, const double* f, const double* u, float* d,
+                          unsigned int* status, cudaStream_t s);
+// u = e (add == 0) or u += e (add == 1) on n^3 cells, e float32.
+cudaError_t launch_accumulate(long long cells, const float* e, double* u, int add,
+                              cudaStream_t s);
 
 }  // namespace srfmg

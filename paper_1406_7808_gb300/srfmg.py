@@ -122,7 +122,8 @@ def buffer_schedule(A, B, K):
 
 
 def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, nu2=2,
-                cheb_lo=1.0 / 6.0, cheb_hi=1.0, precision=SR_FP64, n_outer=0):
+                cheb_lo=1.0 / 6.0, cheb_hi=1.0, precision=SR_FP64, n_outer=2, mixed=False):
+    """sr_fmg_config for an n^3 grid (mixed=True selects SR_MIXED)."""
     c = Config()
     load().sr_fmg_default_config(ctypes.byref(c), int(n))
     c.n_coarse, c.seg, c.K, c.A, c.B = n_coarse, seg, K, A, B
@@ -134,7 +135,7 @@ def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, 
             c.J[i] = int(v)
     c.alpha, c.nu1, c.nu2 = alpha, nu1, nu2
     c.cheb_lo, c.cheb_hi = cheb_lo, cheb_hi
-    c.precision, c.n_outer = precision, n_outer
+    c.precision, c.n_outer = (SR_MIXED if mixed else precision), n_outer
     return c
 
 
@@ -198,7 +199,9 @@ class Solver:
         _check(load().sr_fmg_profile(self._h, int(bool(enable))), "sr_fmg_profile")
 
     def profile_read(self):
-        """{kernel: dict(launches, ms, fp64_ops, bytes)} for kernels that ran."""
+        """{kernel: dict(launches, ms, ops, bytes)} for kernels that ran; ops are
+        the algorithmic floating-point operations (float32 for kinds ending in
+        _f32, float64 otherwise)."""
         lib = load()
         out = {}
         for k in range(lib.sr_fmg_profile_kinds()):
@@ -210,7 +213,7 @@ class Solver:
                                            ctypes.byref(nbytes)), "sr_fmg_profile_read")
             if launches.value:
                 out[name.value.decode()] = dict(launches=launches.value, ms=ms.value,
-                                                fp64_ops=ops.value, bytes=nbytes.value)
+                                                ops=ops.value, bytes=nbytes.value)
         return out
 
     def solve(self, f, out=None):

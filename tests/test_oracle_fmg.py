@@ -92,3 +92,17 @@ def test_rejects_bad_sizes(oracle_mod):
     assert oracle_mod.check_config(n=20) != 0  # 20 -> 10 -> 5 never reaches 2 or 3
     assert oracle_mod.check_config(n=24) == 0
     assert oracle_mod.check_config(n=32, n_coarse=3) != 0
+
+
+def test_defect_correction_reference_converges(oracle_mod):
+    """oracle.solve_refined (the float64 reference of the mixed-precision mode):
+    each pass of u += S(f - A u) cuts the algebraic error by a large factor."""
+    n = 64
+    kw = dict(seg=16, K=2, A=8, B=0)
+    f, uex = inputs.manufactured(n, 1)
+    uh = exact.dst_solve(f)
+    e_disc = np.abs(uh - uex).max()
+    errs = [np.abs(oracle_mod.solve_refined(f, p, **kw) - uh).max() for p in (1, 2, 3)]
+    assert errs[0] > e_disc  # one SR-FMG pass leaves algebraic error above e_disc
+    assert errs[1] < 0.05 * e_disc
+    assert errs[2] < errs[1] / 20
