@@ -184,6 +184,37 @@ int sr_op_coarse_solve(int n, const double* f, double* u, void* stream);
 int sr_op_vcycle(const sr_fmg_config* cfg, const double* f, double* u, void* stream);
 
 /*
+ * Batched solves (many right-hand sides on grids of any sizes and
+ * configurations).  A batch groups existing handles (not owned: destroy the
+ * batch before its handles); problem i is solved by hs[i].  The first solve
+ * for a set of f / u device pointers captures every problem's solve into one
+ * CUDA graph whose branches run on capture streams forked from stream
+ * (biggest problems first, each to the least loaded branch); later solves
+ * with the same pointers relaunch that graph with one cudaGraphLaunch.  The
+ * first batch solve must not itself be issued during a stream capture.
+ *   sr_fmg_batch_solve        blocking; returns the first failing status
+ *   sr_fmg_batch_solve_async  queue only; sr_fmg_batch_check waits and reports
+ *   sr_fmg_batch_autotune     times the graph with 1, 2, 4, ... 32 branches
+ *                             (at most count) and keeps the fastest; results
+ *                             do not depend on the choice
+ *   sr_fmg_solve_batched      one-shot: batch, solve, release
+ * Errors: SR_ERR_INVALID for null or non-device pointers, repeated handles or
+ * outputs, f overlapping its u; SR_ERR_CUDA for failed capture or launch.
+ */
+typedef struct sr_fmg_batch_s* sr_fmg_batch_t;
+int sr_fmg_batch_create(sr_fmg_batch_t* out, const sr_fmg_t* hs, int count);
+int sr_fmg_batch_destroy(sr_fmg_batch_t b);
+int sr_fmg_batch_solve(sr_fmg_batch_t b, const double* const* f, double* const* u, void* stream);
+int sr_fmg_batch_solve_async(sr_fmg_batch_t b, const double* const* f, double* const* u,
+                             void* stream);
+int sr_fmg_batch_check(sr_fmg_batch_t b, void* stream);
+int sr_fmg_batch_autotune(sr_fmg_batch_t b, const double* const* f, double* const* u,
+                          void* stream, int* streams_out, float* ms_out);
+int sr_fmg_batch_set_streams(sr_fmg_batch_t b, int streams);
+int sr_fmg_solve_batched(sr_fmg_t* hs, const double* const* f, double* const* u, int count,
+                         void* stream);
+
+/*
  * Chebyshev smoother that allocates nothing (the paper has no counterpart:
  * this is a service for callers that cannot allocate device memory where they
  * smooth, e.g. when all device memory is handed out by another allocator or

@@ -723,6 +723,13 @@ int collect_profile(sr_fmg_s* h) {
 
 }  // namespace
 
+int srfmg::enqueue_solve_unchecked(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
+  DeviceGuard g(h->device);
+  return enqueue_solve(h, f, u, s);
+}
+
+int srfmg::handle_n(const sr_fmg_s* h) { return h->cfg.n; }
+
 extern "C" {
 
 void sr_fmg_default_config(sr_fmg_config* cfg, int n) {

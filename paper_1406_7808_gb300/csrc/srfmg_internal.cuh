@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct sr_fmg_s;  // solver handle (srfmg_api.cu)
+
 namespace srfmg {
 
 // One box of cells of a level grid.  A global level is a single box covering
@@ -124,5 +126,11 @@ cudaError_t launch_defect(int n, const double* f, const double* u, float* d,
 // u = e (add == 0) or u += e (add == 1) on n^3 cells, e float32.
 cudaError_t launch_accumulate(long long cells, const float* e, double* u, int add,
                               cudaStream_t s);
+
+// Queue one solve of handle h on stream without validating the pointers
+// (the batch path validates them before stream capture); srfmg_api.cu.
+int enqueue_solve_unchecked(::sr_fmg_s* h, const double* f, double* u, cudaStream_t s);
+// n of the handle's grid
+int handle_n(const ::sr_fmg_s* h);
 
 }  // namespace srfmg

@@ -90,6 +90,17 @@ def load():
                                         ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]
+    lib.sr_fmg_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int]
+    lib.sr_fmg_batch_destroy.argtypes = [_VP]
+    for name in ("sr_fmg_batch_solve", "sr_fmg_batch_solve_async"):
+        getattr(lib, name).argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]
+    lib.sr_fmg_batch_check.argtypes = [_VP, _VP]
+    lib.sr_fmg_batch_autotune.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP,
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_float)]
+    lib.sr_fmg_batch_set_streams.argtypes = [_VP, ctypes.c_int]
+    lib.sr_fmg_solve_batched.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                         ctypes.POINTER(_VP), ctypes.c_int, _VP]
     lib.sr_op_apply.argtypes = [ctypes.c_int, _VP, _VP, _VP]
     lib.sr_op_residual.argtypes = [ctypes.c_int, _VP, _VP, _VP, _VP]
     lib.sr_op_smooth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -248,6 +259,83 @@ class Solver:
             ctypes.c_void_p(out.data_ptr())
         _check(load().sr_fmg_solve_host(self._h, fp, up, _stream()), "sr_fmg_solve_host")
         return out
+
+
+class Batch:
+    """Many solves (grids of any sizes) run as one CUDA graph launch.
+
+    solvers: Solver objects, one per problem (kept alive by the batch).
+    solve(fs, us): fs, us lists of float64 CUDA tensors, problem i solved by
+    solvers[i]; the graph is captured on the first call for a pointer set and
+    relaunched afterwards."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        hs = (_VP * len(self.solvers))(*[s._h for s in self.solvers])
+        b = _VP()
+        _check(load().sr_fmg_batch_create(ctypes.byref(b), hs, len(self.solvers)),
+               "sr_fmg_batch_create")
+        self._b = b
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().sr_fmg_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _ptrs(self, fs, us):
+        if len(fs) != len(self.solvers) or len(us) != len(self.solvers):
+            raise ValueError("one f and one u per problem")
+        fp = (_VP * len(fs))(*[_dev(f, s.n, "f").value for f, s in zip(fs, self.solvers)])
+        up = (_VP * len(us))(*[_dev(u, s.n, "u").value for u, s in zip(us, self.solvers)])
+        return fp, up
+
+    def solve(self, fs, us):
+        fp, up = self._ptrs(fs, us)
+        _check(load().sr_fmg_batch_solve(self._b, fp, up, _stream()), "sr_fmg_batch_solve")
+        return us
+
+    def solve_async(self, fs, us):
+        fp, up = self._ptrs(fs, us)
+        _check(load().sr_fmg_batch_solve_async(self._b, fp, up, _stream()),
+               "sr_fmg_batch_solve_async")
+        return us
+
+    def check(self):
+        _check(load().sr_fmg_batch_check(self._b, _stream()), "sr_fmg_batch_check")
+
+    def autotune(self, fs, us):
+        """Time the graph with 1, 2, 4, ... branches and keep the fastest;
+        returns (branches, ms per batch)."""
+        fp, up = self._ptrs(fs, us)
+        best, ms = ctypes.c_int(), ctypes.c_float()
+        _check(load().sr_fmg_batch_autotune(self._b, fp, up, _stream(), ctypes.byref(best),
+                                            ctypes.byref(ms)), "sr_fmg_batch_autotune")
+        return best.value, ms.value
+
+    def set_streams(self, streams):
+        _check(load().sr_fmg_batch_set_streams(self._b, int(streams)), "sr_fmg_batch_set_streams")
+
+
+def solve_batched(solvers, fs, us):
+    """One-shot batched solve through sr_fmg_solve_batched."""
+    hs = (_VP * len(solvers))(*[s._h for s in solvers])
+    fp = (_VP * len(fs))(*[_dev(f, s.n, "f").value for f, s in zip(fs, solvers)])
+    up = (_VP * len(us))(*[_dev(u, s.n, "u").value for u, s in zip(us, solvers)])
+    _check(load().sr_fmg_solve_batched(hs, fp, up, len(solvers), _stream()),
+           "sr_fmg_solve_batched")
+    return us
 
 
 # ---- single components on whole grids (for parity tests) ----

@@ -1,0 +1,41 @@
+"""Named workloads (grid sizes, segment geometry, buffer schedule, precision)
+used by the benchmark, the smoke check and the tests.  Configuration only:
+no arithmetic of the method lives here."""
+
+# SR-FMG FP64: 256^3 cells, 512 segments of 32^3, K = 3, J = (8, 8, 8)
+SR256 = dict(n=256, seg=32, K=3, A=8, B=0)
+# plain FMG FP64 on the same grid
+PLAIN256 = dict(n=256)
+# mixed-precision SR-FMG: 512^3 cells, 512 segments of 64^3, K = 4, J = 8
+MIXED512 = dict(n=512, seg=64, K=4, A=8, B=0, mixed=True, n_outer=2)
+
+# batched: 16 right-hand sides each of 64^3, 128^3, 192^3, 256^3 cells,
+# mixed precision, manufactured f with seeds 100 + i
+BATCH_SIZES = (64, 128, 192, 256)
+BATCH_PER_SIZE = 16
+
+# segment shapes the autotuner may choose from, per grid size: every
+# candidate keeps 4 genuine cells per segment side on the transition level
+# and J = 8 buffer cells per side (Eq. eq:nb with A = 8, B = 0)
+SEGMENT_CANDIDATES = {
+    64: [dict(seg=16, K=2), dict(seg=32, K=3), dict(seg=64, K=4)],
+    128: [dict(seg=16, K=2), dict(seg=32, K=3), dict(seg=64, K=4)],
+    192: [dict(seg=32, K=3), dict(seg=64, K=4)],
+    256: [dict(seg=32, K=3), dict(seg=64, K=4)],
+}
+
+
+def batch_problems(sizes=BATCH_SIZES, per_size=BATCH_PER_SIZE):
+    """[(n, seed)] for the batched workload, sizes interleaved."""
+    out = []
+    i = 0
+    for _ in range(per_size):
+        for n in sizes:
+            out.append((n, 100 + i))
+            i += 1
+    return out
+
+
+def config(kw):
+    """Solver keyword arguments without the grid size."""
+    return {k: v for k, v in kw.items() if k != "n"}
