@@ -124,6 +124,104 @@ __device__ __forceinline__ Cell cell_of(int i, const int lo[3], int ex, int ey) 
 
 // ---------------------------------------------------------------------------
 
+// The two smoother passes, r = D^-1 (f - A u) = f h^2/6 - u + (sum of
+// neighbours)/6 and u += a r + b (sum of the neighbours of r), in column
+// (z-marching) form: the threads of a block take consecutive cells of the
+// box's flattened (x, y) plane (so warps stay full whatever the box width),
+// and each thread walks a chunk of kZChunk cells in z, carrying the
+// z-neighbours in registers.  blockIdx.x enumerates (plane block, z chunk).
+constexpr int kZThreads = 256, kZChunk = 16;
+
+struct ZTiles {
+  int nplane, nzc;  // plane blocks, z chunks
+};
+
+__device__ __forceinline__ bool ztile(const BoxDesc& B, ZTiles t, int& x, int& y, int& z0,
+                                      int& z1) {
+  const int tz = blockIdx.x / t.nplane, pb = blockIdx.x - tz * t.nplane;
+  const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1];
+  const int i = pb * kZThreads + threadIdx.x;
+  const int iy = i / ex;
+  x = B.lo[0] + (i - iy * ex);
+  y = B.lo[1] + iy;
+  z0 = B.lo[2] + tz * kZChunk;
+  z1 = min(z0 + kZChunk, B.hi[2]);
+  return iy < ey && z0 < z1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_cheb_residual_zm(LevelView L,
+                                                               const T* __restrict__ u,
+                                                               T* __restrict__ r, FieldT<T> f,
+                                                               T cf, T sixth, ZTiles tiles) {
+  __shared__ BoxDesc B, FB;
+  if (threadIdx.x == 0) {
+    B = L.boxes[blockIdx.y];
+    FB = f.single ? f.boxes[0] : f.boxes[blockIdx.y];
+  }
+  __syncthreads();
+  int x, y, z0, z1;
+  if (!ztile(B, tiles, x, y, z0, z1)) return;
+  const int n = L.n;
+  const long long sy = B.sy, sz = B.sz, fsz = FB.sz;
+  long long c = at(B, x, y, z0);
+  long long fc = at(FB, x, y, z0);
+  T uc = u[c];
+  T um = (z0 > 0) ? u[c - sz] : negx(uc);
+  for (int z = z0; z < z1; ++z) {
+    const T m = negx(uc);
+    const T up = (z < n - 1) ? u[c + sz] : m;
+    T v[6];
+    v[0] = (x > 0) ? u[c - 1] : m;
+    v[1] = (x < n - 1) ? u[c + 1] : m;
+    v[2] = (y > 0) ? u[c - sy] : m;
+    v[3] = (y < n - 1) ? u[c + sy] : m;
+    v[4] = um;
+    v[5] = up;
+    const T fv = f.p[fc];
+    r[c] = fma6(sixth, v, fma(fv, cf, m));
+    um = uc;
+    uc = up;
+    c += sz;
+    fc += fsz;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_cheb2_update_zm(LevelView L, T* __restrict__ u,
+                                                              const T* __restrict__ r, T a, T b,
+                                                              ZTiles tiles) {
+  __shared__ BoxDesc B;
+  if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
+  __syncthreads();
+  int x, y, z0, z1;
+  if (!ztile(B, tiles, x, y, z0, z1)) return;
+  const int n = L.n;
+  const long long sy = B.sy, sz = B.sz;
+  long long c = at(B, x, y, z0);
+  T rc = r[c];
+  T rm = (z0 > 0) ? r[c - sz] : negx(rc);
+  for (int z = z0; z < z1; ++z) {
+    const T m = negx(rc);
+    const T rp = (z < n - 1) ? r[c + sz] : m;
+    T v[6];
+    v[0] = (x > 0) ? r[c - 1] : m;
+    v[1] = (x < n - 1) ? r[c + 1] : m;
+    v[2] = (y > 0) ? r[c - sy] : m;
+    v[3] = (y < n - 1) ? r[c + sy] : m;
+    v[4] = rm;
+    v[5] = rp;
+    u[c] = fma6(b, v, fma(a, rc, u[c]));
+    rm = rc;
+    rc = rp;
+    c += sz;
+  }
+}
+
+// Per-cell form of the two smoother passes (one thread per cell, x-fastest
+// over the box's compute region), used for float64: there the float64 pipe
+// binds and fully packed warps matter more than the index arithmetic the
+// column form saves.
 // r = D^-1 (f - A u) = f h^2/6 - u + (sum of neighbours)/6
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_cheb_residual(LevelView L, const T* __restrict__ u,
@@ -374,17 +472,21 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
   }
 }
 
-// Trilinear prolongation, one coarse cell and its 2x2x2 children per thread.
-// With 1D weights 3/4 (own coarse cell) and 1/4 (neighbour on the child's
-// side), each child is (1/64) x the z, y, x passes of 3 a + b over the 3x3x3
-// coarse neighbourhood.  add == 0: uf = P uc;  add == 1: uf += P (uc - tc).
-// Coarse cells outside the domain are mirrored with a sign flip; a neighbour
-// is read only if a child inside the fine region needs it.
+// Trilinear prolongation.  With 1D weights 3/4 (own coarse cell) and 1/4
+// (neighbour on the child's side), a child is (1/64) x the x, y, z passes of
+// 3 a + b.  Each thread owns a coarse (x, y) column of the fine box's
+// prolongation range and walks a chunk of coarse z: for every coarse plane it
+// reads the 3x3 neighbourhood once and forms the 2x2 (x, y)-interpolated
+// values; a child in z combines the plane of its coarse cell with the plane
+// on its side.  add == 0: uf = P uc;  add == 1: uf += P uc.  Coarse cells
+// outside the domain are mirrored with a sign flip; a coarse value is read
+// only if a child inside the fine range needs it.
+constexpr int kPZChunk = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const T* __restrict__ uc,
-                                                      const T* __restrict__ tc, LevelView F,
-                                                      T* __restrict__ uf, int add, T three,
-                                                      T w64, T mone, Fk<T> k) {
+                                                      LevelView F, T* __restrict__ uf, int add,
+                                                      T three, T w64, int nplane, Fk<T> k) {
   __shared__ BoxDesc B, CB;
   if (threadIdx.x == 0) {
     B = F.boxes[blockIdx.y];
@@ -398,71 +500,133 @@ __global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const T* __re
     clo[d] = plo[d] >> 1;
     cex[d] = ((phi[d] - 1) >> 1) + 1 - clo[d];
   }
-  const int ncell = cex[0] * cex[1] * cex[2];
+  const int tz = blockIdx.x / nplane, pb = blockIdx.x - tz * nplane;
+  const int i = pb * kThreads + threadIdx.x;
+  const int iy = i / cex[0];
+  if (iy >= cex[1]) return;
+  const int X = clo[0] + (i - iy * cex[0]), Y = clo[1] + iy;
+  const int Z0 = clo[2] + tz * kPZChunk;
+  const int Z1 = min(Z0 + kPZChunk, clo[2] + cex[2]);
+  if (Z0 >= Z1) return;
   const int nc = C.n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
-    const Cell q = cell_of(i, clo, cex[0], cex[1]);
-    const int X[3] = {q.x, q.y, q.z};
-    bool lo_ok[3], hi_ok[3];  // even child (needs X-1) / odd child (needs X+1) inside the region
+  // columns of the 3x3 neighbourhood: mirrored index, sign flip, needed?
+  int xi[3], yi[3];
+  bool fx[3], fy[3], nx[3], ny[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      lo_ok[d] = 2 * X[d] >= plo[d];
-      hi_ok[d] = 2 * X[d] + 1 < phi[d];
+  for (int d = 0; d < 3; ++d) {
+    int x = X + d - 1, y = Y + d - 1;
+    fx[d] = x < 0 || x >= nc;
+    fy[d] = y < 0 || y >= nc;
+    xi[d] = x < 0 ? 0 : (x >= nc ? nc - 1 : x);
+    yi[d] = y < 0 ? 0 : (y >= nc ? nc - 1 : y);
+  }
+  nx[0] = 2 * X >= plo[0];
+  nx[1] = true;
+  nx[2] = 2 * X + 1 < phi[0];
+  ny[0] = 2 * Y >= plo[1];
+  ny[1] = true;
+  ny[2] = 2 * Y + 1 < phi[1];
+  // 2x2 (x, y)-interpolated values of coarse plane Z (unscaled)
+  auto plane = [&](int Z, T q[2][2]) {
+    const bool fz = Z < 0 || Z >= nc;
+    const int zi = Z < 0 ? 0 : (Z >= nc ? nc - 1 : Z);
+    T px[3][2];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+      T v[3];
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        T val = k.zero;
+        if (nx[dx] && ny[dy]) val = neg_if(uc[at(CB, xi[dx], yi[dy], zi)], fx[dx] ^ fy[dy] ^ fz);
+        v[dx] = val;
+      }
+      px[dy][0] = fma(three, v[1], v[0]);
+      px[dy][1] = fma(three, v[1], v[2]);
     }
-    // x pass over the 3x3 (z, y) lines of the coarse neighbourhood
-    T px[3][3][2];
 #pragma unroll
-    for (int dz = 0; dz < 3; ++dz)
+    for (int cx = 0; cx < 2; ++cx) {
+      q[0][cx] = fma(three, px[1][cx], px[0][cx]);
+      q[1][cx] = fma(three, px[1][cx], px[2][cx]);
+    }
+  };
+  T qm[2][2], qc[2][2], qp[2][2];
+  if (2 * Z0 >= plo[2]) {
+    plane(Z0 - 1, qm);
+  } else {
 #pragma unroll
-      for (int dy = 0; dy < 3; ++dy) {
-        const bool need = (dz != 0 || lo_ok[2]) && (dz != 2 || hi_ok[2]) && (dy != 0 || lo_ok[1]) &&
-                          (dy != 2 || hi_ok[1]);
-        T v[3];
+    for (int a = 0; a < 4; ++a) qm[a / 2][a % 2] = k.zero;
+  }
+  plane(Z0, qc);
+  for (int Z = Z0; Z < Z1; ++Z) {
+    // the fine values this step updates, loaded before the arithmetic
+    T old[2][2][2];
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-          const bool needx = need && (dx != 0 || lo_ok[0]) && (dx != 2 || hi_ok[0]);
-          T val = k.zero;
-          if (needx) {
-            int x = X[0] + dx - 1, y = X[1] + dy - 1, z = X[2] + dz - 1;
-            bool flip = false;
-            if (x < 0) { x = 0; flip = !flip; } else if (x >= nc) { x = nc - 1; flip = !flip; }
-            if (y < 0) { y = 0; flip = !flip; } else if (y >= nc) { y = nc - 1; flip = !flip; }
-            if (z < 0) { z = 0; flip = !flip; } else if (z >= nc) { z = nc - 1; flip = !flip; }
-            const long long ci = at(CB, x, y, z);
-            val = add ? fma(tc[ci], mone, uc[ci]) : uc[ci];
-            val = neg_if(val, flip);
-          }
-          v[dx] = val;
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+      for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx) {
+          const int fz = 2 * Z + cz, fy = 2 * Y + cy, fxx = 2 * X + cx;
+          const bool in = fz >= plo[2] && fz < phi[2] && fy >= plo[1] && fy < phi[1] &&
+                          fxx >= plo[0] && fxx < phi[0];
+          old[cz][cy][cx] = (add && in) ? uf[at(B, fxx, fy, fz)] : k.zero;
         }
-        px[dz][dy][0] = fma(three, v[1], v[0]);
-        px[dz][dy][1] = fma(three, v[1], v[2]);
-      }
-    T py[3][2][2];
+    const bool odd_in = 2 * Z + 1 < phi[2];
+    if (odd_in) {
+      plane(Z + 1, qp);
+    } else {
 #pragma unroll
-    for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-      for (int cx = 0; cx < 2; ++cx) {
-        py[dz][0][cx] = fma(three, px[dz][1][cx], px[dz][0][cx]);
-        py[dz][1][cx] = fma(three, px[dz][1][cx], px[dz][2][cx]);
-      }
+      for (int a = 0; a < 4; ++a) qp[a / 2][a % 2] = k.zero;
+    }
 #pragma unroll
     for (int cz = 0; cz < 2; ++cz) {
-      const int fz = 2 * X[2] + cz;
+      const int fz = 2 * Z + cz;
       if (fz < plo[2] || fz >= phi[2]) continue;
 #pragma unroll
       for (int cy = 0; cy < 2; ++cy) {
-        const int fy = 2 * X[1] + cy;
+        const int fy = 2 * Y + cy;
         if (fy < plo[1] || fy >= phi[1]) continue;
 #pragma unroll
         for (int cx = 0; cx < 2; ++cx) {
-          const int fx = 2 * X[0] + cx;
-          if (fx < plo[0] || fx >= phi[0]) continue;
-          const T e = fma(three, py[1][cy][cx], py[cz == 0 ? 0 : 2][cy][cx]);
-          const long long c = at(B, fx, fy, fz);
-          uf[c] = fma(w64, e, add ? uf[c] : k.zero);
+          const int fxx = 2 * X + cx;
+          if (fxx < plo[0] || fxx >= phi[0]) continue;
+          const T e = fma(three, qc[cy][cx], cz == 0 ? qm[cy][cx] : qp[cy][cx]);
+          uf[at(B, fxx, fy, fz)] = fma(w64, e, old[cz][cy][cx]);
         }
       }
     }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      qm[a / 2][a % 2] = qc[a / 2][a % 2];
+      qc[a / 2][a % 2] = qp[a / 2][a % 2];
+    }
+  }
+}
+
+// e = u - t on every stored cell of the boxes that lies inside the domain
+// (compute cells and frozen SR ghosts): the coarse-grid correction w - t of
+// the FAS V-cycle, ready for prolongation
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_diff(LevelView C, const T* __restrict__ u,
+                                                   const T* __restrict__ t, T* __restrict__ e,
+                                                   T mone) {
+  __shared__ BoxDesc B;
+  if (threadIdx.x == 0) B = C.boxes[blockIdx.y];
+  __syncthreads();
+  const int n = C.n;
+  const bool shell = B.ox < B.lo[0];
+  int lo[3], hi[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = shell ? max(B.lo[d] - 1, 0) : B.lo[d];
+    hi[d] = shell ? min(B.hi[d] + 1, n) : B.hi[d];
+  }
+  const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
+  const int ncell = ex * ey * ez;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
+    const Cell q = cell_of(i, lo, ex, ey);
+    const long long c = at(B, q.x, q.y, q.z);
+    e[c] = fma(t[c], mone, u[c]);
   }
 }
 
@@ -604,18 +768,39 @@ double sq(int n) { return (double)n * (double)n; }
 
 }  // namespace
 
+ZTiles ztiles(const LevelView& L) {
+  const int plane = L.max_ex * L.max_ey;  // bounds every box's (x, y) plane
+  return ZTiles{(plane + kZThreads - 1) / kZThreads, (L.max_ez + kZChunk - 1) / kZChunk};
+}
+
+dim3 zgrid(const LevelView& L, ZTiles t) {
+  return dim3((unsigned)(t.nplane * t.nzc), (unsigned)L.nbox, 1);
+}
+
+// float64: per-cell form; float32: column form
 template <typename T>
 cudaError_t launch_cheb_residual(const LevelView& L, const T* u, T* r, FieldT<T> f,
                                  cudaStream_t s) {
   const T cf = T(1.0 / (6.0 * sq(L.n)));
-  k_cheb_residual<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, cf, T(1.0 / 6.0));
+  if (sizeof(T) == 8) {
+    k_cheb_residual<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, cf,
+                                                                     T(1.0 / 6.0));
+  } else {
+    const ZTiles t = ztiles(L);
+    k_cheb_residual_zm<T><<<zgrid(L, t), kZThreads, 0, s>>>(L, u, r, f, cf, T(1.0 / 6.0), t);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_cheb2_update(const LevelView& L, T* u, const T* r, double a, double b,
                                 cudaStream_t s) {
-  k_cheb2_update<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, T(a), T(b));
+  if (sizeof(T) == 8) {
+    k_cheb2_update<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, T(a), T(b));
+  } else {
+    const ZTiles t = ztiles(L);
+    k_cheb2_update_zm<T><<<zgrid(L, t), kZThreads, 0, s>>>(L, u, r, T(a), T(b), t);
+  }
   return cudaGetLastError();
 }
 
@@ -669,15 +854,21 @@ cudaError_t launch_transition_rhs(const LevelView& C, const T* t, const T* rho, 
 }
 
 template <typename T>
-cudaError_t launch_prolong(const LevelView& C, const T* uc, const T* tc, const LevelView& F,
-                           T* uf, int add, cudaStream_t s) {
-  // one thread per coarse cell over the children in the prolongation range:
-  // at most about max_prolong / 8 plus the partial blocks on the faces
-  int edge = 1;
-  while ((long long)edge * edge * edge < F.max_prolong) ++edge;
-  const int half = edge / 2 + 2;
-  k_prolong<T><<<grid_for(F, half * half * half), kThreads, 0, s>>>(
-      C, uc, tc, F, uf, add, T(3.0), T(1.0 / 64.0), T(-1.0), fk<T>());
+cudaError_t launch_prolong(const LevelView& C, const T* uc, const LevelView& F, T* uf, int add,
+                           cudaStream_t s) {
+  // coarse columns: every fine box's prolongation range spans at most
+  // max_e + 2 fine cells per side, i.e. max_e / 2 + 2 coarse cells
+  const int cx = F.max_ex / 2 + 2, cy = F.max_ey / 2 + 2, cz = F.max_ez / 2 + 2;
+  const int nplane = (cx * cy + kThreads - 1) / kThreads;
+  const int nzc = (cz + kPZChunk - 1) / kPZChunk;
+  k_prolong<T><<<dim3((unsigned)(nplane * nzc), (unsigned)F.nbox), kThreads, 0, s>>>(
+      C, uc, F, uf, add, T(3.0), T(1.0 / 64.0), nplane, fk<T>());
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaStream_t s) {
+  k_diff<T><<<grid_for(C, C.max_stored), kThreads, 0, s>>>(C, u, t, e, T(-1.0));
   return cudaGetLastError();
 }
 
@@ -737,8 +928,9 @@ cudaError_t launch_accumulate(long long cells, const float* e, double* u, int ad
                                             const T*, T*, T*, cudaStream_t);                   \
   template cudaError_t launch_transition_rhs<T>(const LevelView&, const T*, const T*, T*, T*,  \
                                                 cudaStream_t);                                 \
-  template cudaError_t launch_prolong<T>(const LevelView&, const T*, const T*,                 \
-                                         const LevelView&, T*, int, cudaStream_t);             \
+  template cudaError_t launch_prolong<T>(const LevelView&, const T*, const LevelView&, T*, int, \
+                                         cudaStream_t);                                        \
+  template cudaError_t launch_diff<T>(const LevelView&, const T*, const T*, T*, cudaStream_t);  \
   template cudaError_t launch_coarse_solve<T>(const LevelView&, const double*, FieldT<T>, T*,  \
                                               cudaStream_t);                                   \
   template cudaError_t launch_restrict_global<T>(int, const T*, T*, int, unsigned int*,        \

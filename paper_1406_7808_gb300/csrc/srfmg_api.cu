@@ -76,7 +76,7 @@ enum Kind {
   kProlongSet, kProlongAdd, kCoarseSolve, kRestrictF, kGather, kApply,
   kChebResidualF32, kCheb2UpdateF32, kChebStepF32, kResidRestrictF32, kCoarseRhsMixed,
   kTransitionRhsMixed, kProlongSetF32, kProlongAddF32, kCoarseSolveMixed, kRestrictFF32,
-  kGatherMixed, kDefect, kAccumulate, kKinds
+  kGatherMixed, kDefect, kAccumulate, kDiff, kDiffF32, kKinds
 };
 const char* const kKindName[kKinds] = {
   "cheb_residual", "cheb2_update", "cheb_step", "resid_restrict", "coarse_rhs",
@@ -84,12 +84,14 @@ const char* const kKindName[kKinds] = {
   "gather_genuine", "apply",
   "cheb_residual_f32", "cheb2_update_f32", "cheb_step_f32", "resid_restrict_f32",
   "coarse_rhs_mixed", "transition_rhs_mixed", "prolong_f32", "prolong_correct_f32",
-  "coarse_solve_mixed", "restrict_f_f32", "gather_genuine_mixed", "defect", "accumulate"};
+  "coarse_solve_mixed", "restrict_f_f32", "gather_genuine_mixed", "defect", "accumulate",
+  "correction", "correction_f32"};
 
 // kind of a kernel for storage type T: float64 kinds shift to their float32
 // counterparts (same order)
 template <typename T>
 int kind_of(int k64) {
+  if (k64 == kDiff) return sizeof(T) == 8 ? kDiff : kDiffF32;
   return sizeof(T) == 8 ? k64 : k64 + kChebResidualF32;
 }
 
@@ -317,6 +319,9 @@ int finish_level(sr_fmg_s* h, Geom& L) {
     mx(v.max_prolong, prod(b.plo, b.phi));
     mx(v.max_restrict, prod(b.rlo, b.rhi));
     mx(v.max_genuine, prod(b.glo, b.ghi));
+    mx(v.max_ex, b.hi[0] - b.lo[0]);
+    mx(v.max_ey, b.hi[1] - b.lo[1]);
+    mx(v.max_ez, b.hi[2] - b.lo[2]);
     L.tot_cells += (double)prod(b.lo, b.hi);
     L.tot_prolong += (double)prod(b.plo, b.phi);
     L.tot_restrict += (double)prod(b.rlo, b.rhi);
@@ -518,8 +523,10 @@ int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStrea
          launch_coarse_rhs<T>(C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
   rc = vcycle_global(h, H, g - 1, C.u, view_global<T>(C, C.rhs), s);
   if (rc) return rc;
-  LAUNCH(h, kind_of<T>(kProlongAdd), L.tot_prolong, 73.0 / 8.0, 2.25 * w, s,
-         launch_prolong<T>(C.view, C.u, C.t, L.view, u, 1, s));
+  LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
+         launch_diff<T>(C.view, C.u, C.t, C.rho, s));
+  LAUNCH(h, kind_of<T>(kProlongAdd), L.tot_prolong, 26.0 / 8.0, 2.125 * w, s,
+         launch_prolong<T>(C.view, C.rho, L.view, u, 1, s));
   return smooth(h, L, h->post, u, rhs, s);
 }
 
@@ -540,8 +547,8 @@ int run_fmg_global(sr_fmg_s* h, Hier<T>& H, const T* ftop, T* utop, cudaStream_t
   const double w = sizeof(T);
   for (int g = 1; g <= top; ++g) {
     Level<T>& L = H.glev[g];
-    LAUNCH(h, kind_of<T>(kProlongSet), L.tot_prolong, 46.0 / 8.0, 1.125 * w, s,
-           launch_prolong<T>(H.glev[g - 1].view, ug(g - 1), nullptr, L.view, ug(g), 0, s));
+    LAUNCH(h, kind_of<T>(kProlongSet), L.tot_prolong, 26.0 / 8.0, 1.125 * w, s,
+           launch_prolong<T>(H.glev[g - 1].view, ug(g - 1), L.view, ug(g), 0, s));
     FieldT<T> f = view_global<T>(L, fg(g));
     int rc = smooth(h, L, h->fmg, ug(g), f, s);
     if (rc) return rc;
@@ -591,8 +598,8 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
     // u_k <- Pi u_{k-1} on Omega^C_k u Omega^GSR_k, then S^alpha on Omega^C_k
     {
       const Level<T>& C = (k == 1) ? L0 : H.slev[k - 1];
-      LAUNCH(h, kind_of<T>(kProlongSet), Lk.tot_prolong, 46.0 / 8.0, 1.125 * w, s,
-             launch_prolong<T>(C.view, C.u, nullptr, Lk.view, Lk.u, 0, s));
+      LAUNCH(h, kind_of<T>(kProlongSet), Lk.tot_prolong, 26.0 / 8.0, 1.125 * w, s,
+             launch_prolong<T>(C.view, C.u, Lk.view, Lk.u, 0, s));
       int rc = smooth(h, Lk, h->fmg, Lk.u, fview(k), s);
       if (rc) return rc;
     }
@@ -622,8 +629,10 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
     for (int j = 1; j <= k; ++j) {
       Level<T>& Lj = H.slev[j];
       const Level<T>& C = (j == 1) ? L0 : H.slev[j - 1];
-      LAUNCH(h, kind_of<T>(kProlongAdd), Lj.tot_prolong, 73.0 / 8.0, 2.25 * w, s,
-             launch_prolong<T>(C.view, C.u, C.t, Lj.view, Lj.u, 1, s));
+      LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
+             launch_diff<T>(C.view, C.u, C.t, C.rho, s));
+      LAUNCH(h, kind_of<T>(kProlongAdd), Lj.tot_prolong, 26.0 / 8.0, 2.125 * w, s,
+             launch_prolong<T>(C.view, C.rho, Lj.view, Lj.u, 1, s));
       const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
       rc = smooth(h, Lj, h->post, Lj.u, rhs, s);
       if (rc) return rc;
@@ -980,7 +989,7 @@ int sr_op_prolong(int nc, const double* ac, double* af, void* stream) {
   int rc = tmp_level(C, nc);
   if (!rc) rc = tmp_level(F, 2 * nc);
   if (rc) return rc;
-  CK(launch_prolong<double>(C.L.view, ac, nullptr, F.L.view, af, 0, (cudaStream_t)stream));
+  CK(launch_prolong<double>(C.L.view, ac, F.L.view, af, 0, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
 }

@@ -38,6 +38,7 @@ struct LevelView {
   int max_prolong;       // largest prolongation-range cell count
   int max_restrict;      // largest restriction-target cell count
   int max_genuine;       // largest genuine-region cell count
+  int max_ex, max_ey, max_ez;  // largest compute-region extents
 };
 
 // A field read with a possibly different layout than the level's boxes (the
@@ -96,10 +97,14 @@ template <typename T>
 cudaError_t launch_transition_rhs(const LevelView& C, const T* t, const T* rho, T* u, T* rhs,
                                   cudaStream_t s);
 // Prolongation onto the fine boxes' prolongation range:
-// add == 0: uf = P uc;  add == 1: uf += P (uc - tc).
+// add == 0: uf = P uc;  add == 1: uf += P uc.
 template <typename T>
-cudaError_t launch_prolong(const LevelView& C, const T* uc, const T* tc, const LevelView& F,
-                           T* uf, int add, cudaStream_t s);
+cudaError_t launch_prolong(const LevelView& C, const T* uc, const LevelView& F, T* uf, int add,
+                           cudaStream_t s);
+// e = u - t on the stored cells of every box that lie inside the domain (the
+// coarse-grid correction w - t of the FAS V-cycle).
+template <typename T>
+cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaStream_t s);
 // Coarsest grid: u = Minv f, Minv the dense float64 inverse (m x m, m = n^3);
 // float64 arithmetic.
 template <typename T>

@@ -99,6 +99,7 @@ extern "C" int sr_op_smooth_noalloc(int n, int nu, double cheb_lo, double cheb_h
   L.n = n;
   L.max_cells = L.max_stored = L.max_prolong = L.max_genuine = n * n * n;
   L.max_restrict = (n / 2) * (n / 2) * (n / 2);
+  L.max_ex = L.max_ey = L.max_ez = n;
   const FieldView fv{f, desc, 1};
 
   // Chebyshev iteration on D^-1 A over [cheb_lo, cheb_hi] * 2 (the same

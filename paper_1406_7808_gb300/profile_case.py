@@ -4,8 +4,10 @@ captures (ncu): each case runs a fixed, seeded workload once and exits.
   python -m paper_1406_7808_gb300.profile_case smooth --n 256
       one Chebyshev degree-2 smoothing of a whole n^3 grid (two kernels:
       cheb_residual, cheb2_update)
-  python -m paper_1406_7808_gb300.profile_case solve --n 256 [--plain] [--warmup 1]
-      warm-up solves then one solve of the benchmark configuration
+  python -m paper_1406_7808_gb300.profile_case solve --n 256 [--plain] [--mixed] [--warmup 1]
+      warm-up solves then one solve of the benchmark configuration (SR,
+      32^3 segments, K = 3, J = 8; --plain without segments; --mixed in the
+      mixed-precision mode)
 """
 import argparse
 import os
@@ -25,6 +27,7 @@ def main():
     p.add_argument("case", choices=["smooth", "solve"])
     p.add_argument("--n", type=int, default=256)
     p.add_argument("--plain", action="store_true")
+    p.add_argument("--mixed", action="store_true")
     p.add_argument("--warmup", type=int, default=1)
     a = p.parse_args()
     build.build()
@@ -36,6 +39,8 @@ def main():
         srfmg.op_smooth(u, ft, 2)
     else:
         kw = {} if a.plain else dict(seg=32, K=3, A=8, B=0)
+        if a.mixed:
+            kw["mixed"] = True
         with srfmg.Solver(a.n, **kw) as s:
             ut = torch.empty_like(ft)
             for _ in range(a.warmup):
