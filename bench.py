@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the mixed-precision and batched measurements")
     return p.parse_args()
 
 
@@ -126,8 +128,8 @@ def ncu_traffic(kernel):
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
+        if ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(": ", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernels.cu sha256[:16]") != sha:
         return None
@@ -203,7 +205,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1406_7808_gb300 import build, inputs, srfmg
+    from paper_1406_7808_gb300 import build, inputs, srfmg, workloads
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -299,7 +301,9 @@ def run_ours(args):
     plain.check()
     u_plain = ut.cpu().numpy()
     plain_ms = timed(plain, args.steps) / args.steps
+    plain_bytes = profiled_bytes(plain, ft, ut)
     plain.close()
+    sr_bytes = sum(v["bytes"] for v in prof.values()) / args.steps
 
     # end to end through the C ABI from pinned host memory
     fh = torch.from_numpy(f).pin_memory()
@@ -311,6 +315,12 @@ def run_ours(args):
         sr.solve_host(fh.numpy(), uh.numpy())
     e2e_s = max_over_ranks(time.perf_counter() - t0) / args.steps
     sr.close()
+    del fh, uh
+
+    mixed = batch = None
+    if not args.no_extras:
+        mixed = measure_mixed(args, timed_fn=max_over_ranks, world=world, rank=rank)
+        batch = measure_batch(args, max_over_ranks, world)
 
     if rank != 0:
         if world > 1:
@@ -340,6 +350,39 @@ def run_ours(args):
         u_or, cpu = cpu_baseline(f)
         acc["max_rel_diff_vs_oracle"] = float(np.abs(u_sr - u_or).max() / np.abs(u_or).max())
 
+    if mixed is not None and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        mf, _ = inputs.manufactured(mixed["n"], 1)
+        okw = {k: v for k, v in workloads.config(workloads.MIXED512).items()
+               if k not in ("mixed", "n_outer")}
+        ref = oracle.solve_refined(mf, workloads.MIXED512["n_outer"], n_threads=os.cpu_count(),
+                                   **okw)
+        diff = float(np.abs(mixed.pop("u") - ref).max())
+        h = 1.0 / mixed["n"]
+        e_disc = abs(np.pi ** 2 * h * h / (4 * np.sin(np.pi * h / 2) ** 2) - 1) * \
+            np.cos(np.pi * h / 2) ** 3
+        mixed["max_abs_diff_vs_oracle_fp64_loop"] = diff
+        mixed["bound"] = "0.1 e_disc"
+        mixed["e_disc"] = float(e_disc)
+        mixed["within_bound"] = bool(diff <= 0.1 * e_disc)
+    elif mixed is not None:
+        mixed.pop("u", None)
+    hbm = hbm_peak or None
+    comparison = {
+        "plain_fmg_fp64_256": {"dof_s": world * N ** 3 / (plain_ms / 1e3), "ms": plain_ms,
+                               "hbm_gbs": plain_bytes / (plain_ms / 1e3) / 1e9,
+                               "hbm_frac_of_measured": plain_bytes / (plain_ms / 1e3) / 1e9 / hbm
+                               if hbm else None},
+        "sr_fmg_fp64_256": {"dof_s": value, "ms": ms,
+                            "hbm_gbs": sr_bytes / (ms / 1e3) / 1e9,
+                            "hbm_frac_of_measured": sr_bytes / (ms / 1e3) / 1e9 / hbm
+                            if hbm else None},
+        "mixed_sr_512": mixed,
+        "batched_mixed": batch,
+    }
+    if mixed is not None and hbm:
+        mixed["hbm_frac_of_measured"] = mixed["hbm_gbs"] / hbm
+
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -358,10 +401,89 @@ def run_ours(args):
         "clocks": clocks,
         "accuracy": acc,
         "kernels": kernels,
+        "comparison": comparison,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def profiled_bytes(solver, ft, ut, reps=2):
+    """Algorithmic bytes of one solve, from the library's per-kernel profile."""
+    solver.profile(True)
+    for _ in range(reps):
+        solver.solve_async(ft, ut)
+    solver.check()
+    prof = solver.profile_read()
+    solver.profile(False)
+    return sum(v["bytes"] for v in prof.values()) / reps
+
+
+def _time_loop(step, steps, stream=None):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_mixed(args, timed_fn, world, rank):
+    """Mixed-precision SR-FMG, 512^3 cells, 64^3-cell segments, K = 4 (f of
+    the manufactured problem at seed 1)."""
+    import numpy as np
+    import torch
+    from paper_1406_7808_gb300 import inputs, srfmg, workloads
+    kw = workloads.MIXED512
+    n = kw["n"]
+    f, _ = inputs.manufactured(n, 1 + rank)
+    ft = torch.from_numpy(f).cuda()
+    ut = torch.empty_like(ft)
+    with srfmg.Solver(n, **workloads.config(kw)) as s:
+        for _ in range(args.warmup):
+            s.solve_async(ft, ut)
+        s.check()
+        u = ut.cpu().numpy()
+        total = timed_fn(_time_loop(lambda: s.solve_async(ft, ut), args.steps))
+        s.check()
+        ms = total / args.steps
+        nbytes = profiled_bytes(s, ft, ut)
+    return {"n": n, "config": workloads.config(kw), "dof_s": world * n ** 3 / (ms / 1e3),
+            "ms": ms, "hbm_gbs": nbytes / (ms / 1e3) / 1e9, "u": u}
+
+
+def measure_batch(args, timed_fn, world):
+    """64 right-hand sides (16 each of 64^3, 128^3, 192^3, 256^3), mixed
+    precision, one CUDA graph launch per batch, autotuned segment shapes and
+    graph branches."""
+    import torch
+    from paper_1406_7808_gb300 import autotune, inputs, srfmg, workloads
+    problems = workloads.batch_problems()
+    solvers, choices = autotune.tuned_batch(problems)
+    fs = [torch.from_numpy(inputs.manufactured(n, seed)[0]).cuda() for n, seed in problems]
+    us = [torch.empty_like(f) for f in fs]
+    b = srfmg.Batch(solvers)
+    branches, _ = b.autotune(fs, us)
+    for _ in range(args.warmup):
+        b.solve_async(fs, us)
+    b.check()
+    steps = max(3, args.steps // 4)
+    total = timed_fn(_time_loop(lambda: b.solve_async(fs, us), steps))
+    b.check()
+    ms = total / steps
+    dof = sum(n ** 3 for n, _ in problems)
+    b.close()
+    for s in solvers:
+        s.close()
+    return {"problems": len(problems), "sizes": list(workloads.BATCH_SIZES),
+            "dof_per_batch": dof, "ms_per_batch": ms, "dof_s": world * dof / (ms / 1e3),
+            "graph_branches": branches, "timed_batches": steps,
+            "segment_choice": {str(n): {k: v for k, v in c[0].items() if k in ("seg", "K")}
+                               for n, c in choices.items()}}
 
 
 class _Null:
