@@ -76,6 +76,19 @@ __device__ __forceinline__ float neg_if(float v, bool flip) {
   return __uint_as_float(b);
 }
 
+// float -> double on the integer pipe (the conversion instruction would use
+// the float64 pipe): exact for normal floats and zero; float32 subnormals
+// (below 1.2e-38) become zero; the solver's values are finite.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned sign = b & 0x80000000u;
+  const unsigned hi = e ? (sign | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)) : sign;
+  const unsigned lo = e ? (b << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 __device__ __forceinline__ void region_of(const BoxDesc& b, int which, int lo[3], int hi[3]) {
   const int* l = b.lo;
   const int* h = b.hi;
@@ -90,15 +103,24 @@ __device__ __forceinline__ void region_of(const BoxDesc& b, int which, int lo[3]
 // neighbour outside [0, n) is minus the centre value (mirror through u = 0
 // on the face).
 template <typename A, typename T>
+__device__ __forceinline__ A acc_of(T x) {
+  return (A)x;
+}
+template <>
+__device__ __forceinline__ double acc_of<double, float>(float x) {
+  return widen(x);
+}
+
+template <typename A, typename T>
 __device__ __forceinline__ void neighbours(const T* __restrict__ a, long long c, const BoxDesc& b,
                                            int n, int x, int y, int z, T centre, A v[6]) {
   const T m = negx(centre);
-  v[0] = (A)((x > 0) ? a[c - 1] : m);
-  v[1] = (A)((x < n - 1) ? a[c + 1] : m);
-  v[2] = (A)((y > 0) ? a[c - b.sy] : m);
-  v[3] = (A)((y < n - 1) ? a[c + b.sy] : m);
-  v[4] = (A)((z > 0) ? a[c - b.sz] : m);
-  v[5] = (A)((z < n - 1) ? a[c + b.sz] : m);
+  v[0] = acc_of<A>((x > 0) ? a[c - 1] : m);
+  v[1] = acc_of<A>((x < n - 1) ? a[c + 1] : m);
+  v[2] = acc_of<A>((y > 0) ? a[c - b.sy] : m);
+  v[3] = acc_of<A>((y < n - 1) ? a[c + b.sy] : m);
+  v[4] = acc_of<A>((z > 0) ? a[c - b.sz] : m);
+  v[5] = acc_of<A>((z < n - 1) ? a[c + b.sz] : m);
 }
 
 // acc + w * (v0 + ... + v5) as six fused multiply-adds
@@ -442,7 +464,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView 
                      q.y < FBx.rhi[1] && q.z >= FBx.rlo[2] && q.z < FBx.rhi[2];
     double v[6];
     neighbours<double>(u, c, B, n, q.x, q.y, q.z, uc, v);
-    rhs[c] = (T)fma6(cn, v, fma(c6, (double)uc, inF ? (double)rho[c] : k.zero));
+    rhs[c] = (T)fma6(cn, v, fma(c6, widen(uc), inF ? widen(rho[c]) : k.zero));
   }
 }
 
@@ -468,7 +490,7 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
     double v[6];
     neighbours<double>(t, c, B, n, q.x, q.y, q.z, tc, v);
     u[c] = tc;
-    rhs[c] = (T)fma6(cn, v, fma(c6, (double)tc, (double)rho[c]));
+    rhs[c] = (T)fma6(cn, v, fma(c6, widen(tc), widen(rho[c])));
   }
 }
 
@@ -643,7 +665,7 @@ __global__ void k_coarse_solve(LevelView L, const double* __restrict__ minv, Fie
   double s = k.zero;
   for (int j = lane; j < m; j += 32) {
     const int x = j % n, y = (j / n) % n, z = j / (n * n);
-    s = fma(minv[(long long)warp * m + j], (double)f.p[at(FB, x, y, z)], s);
+    s = fma(minv[(long long)warp * m + j], widen(f.p[at(FB, x, y, z)]), s);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s = fma(__shfl_xor_sync(0xffffffffu, s, o), k.one, s);
@@ -703,7 +725,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_genuine(LevelView L, const 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, lo, ex, ey);
     const long long o = (q.z * n + q.y) * n + q.x;
-    const double v = (double)u[at(B, q.x, q.y, q.z)];
+    const double v = widen(u[at(B, q.x, q.y, q.z)]);
     out[o] = add ? fma(v, k.one, out[o]) : v;
   }
 }
@@ -746,7 +768,7 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(long long cells, const 
                                                          Fk<double> k) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cells;
        i += (long long)gridDim.x * blockDim.x) {
-    const double v = (double)e[i];
+    const double v = widen(e[i]);
     u[i] = add ? fma(v, k.one, u[i]) : v;
   }
 }
