@@ -31,6 +31,7 @@ METRIC = "3D Poisson FMG fine-grid DOF/s, SR vs plain, at discretization error; 
 N = 256
 SR = dict(seg=32, K=3, A=8, B=0)
 SEED = 0
+VSOLVE_RTOL = 1e-4  # relative residual of the V-cycle comparison solver (Sec. 5.3)
 # float64 lanes per clock per SM (two FMA-capable lanes) x SMs x max SM clock
 FP64_LANES_PER_CLK_SM = 2
 GB300_SMS = 152
@@ -302,6 +303,20 @@ def run_ours(args):
     u_plain = ut.cpu().numpy()
     plain_ms = timed(plain, args.steps) / args.steps
     plain_bytes = profiled_bytes(plain, ft, ut)
+    # the paper's comparison solver: V-cycles from zero to a relative
+    # residual of 1e-4 (Sec. 5.3), same f
+    vs = None
+    if not args.no_extras:
+        plain.vsolve(ft, ut.zero_(), rtol=VSOLVE_RTOL)
+        barrier()
+        vstate = {}
+
+        def vstep():
+            _, vstate["cycles"], vstate["rel"] = plain.vsolve(ft, ut.zero_(), rtol=VSOLVE_RTOL)
+        vs_ms = max_over_ranks(_time_loop(vstep, args.steps, stream)) / args.steps
+        vs = {"rtol": VSOLVE_RTOL, "ms": vs_ms, "dof_s": world * N ** 3 / (vs_ms / 1e3),
+              "cycles": vstate["cycles"], "rel_resid": vstate["rel"],
+              "e": float(np.abs(ut.cpu().numpy() - u_exact).max())}
     plain.close()
     sr_bytes = sum(v["bytes"] for v in prof.values()) / args.steps
 
@@ -344,6 +359,8 @@ def run_ours(args):
     acc["e_sr"] = float(np.abs(u_sr - u_exact).max())
     acc["e_plain"] = float(np.abs(u_plain - u_exact).max())
     acc["e_r"] = acc["e_sr"] / acc["e_plain"]
+    if vs is not None:
+        vs["e_over_e_plain_fmg"] = vs["e"] / acc["e_plain"]
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -377,6 +394,7 @@ def run_ours(args):
                             "hbm_gbs": sr_bytes / (ms / 1e3) / 1e9,
                             "hbm_frac_of_measured": sr_bytes / (ms / 1e3) / 1e9 / hbm
                             if hbm else None},
+        "vcycle_solve_fp64_256": vs,
         "mixed_sr_512": mixed,
         "batched_mixed": batch,
     }
@@ -424,10 +442,10 @@ def _time_loop(step, steps, stream=None):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
+    e0.record(stream)
     for _ in range(steps):
         step()
-    e1.record()
+    e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
 

@@ -82,6 +82,9 @@ typedef struct sr_fmg_s* sr_fmg_t;
  *             u += S32(f - A u) with the defect in float64 (no counterpart in
  *             the paper, which states no precision).
  *   n_outer   SR_MIXED passes, 1..16 (0 = 2).
+ *   mbs       maximum buffer schedule (Sec. 5.2.1): J_1 = A (even) and
+ *             J_k = 2^(k-1) J_1, so every coarser compute region is exactly
+ *             the support of the next finer one; overrides A, B and J.
  */
 typedef struct {
   int n;
@@ -95,6 +98,7 @@ typedef struct {
   double cheb_lo, cheb_hi;
   int precision;
   int n_outer;
+  int mbs;
 } sr_fmg_config;
 
 /* Fill cfg with the defaults for an n^3 grid: plain FMG, F(1,2,2), Chebyshev
@@ -134,6 +138,24 @@ int sr_fmg_check(sr_fmg_t h, void* stream);
  * device, solves, copies the solution to u_host, waits for stream.  Page-
  * locked host buffers give the fastest copies; pageable memory also works. */
 int sr_fmg_solve_host(sr_fmg_t h, const double* f_host, double* u_host, void* stream);
+
+/*
+ * Iterative V-cycle solver, the comparison solver of Sec. 5.3 (V-cycles to
+ * a relative residual tolerance; Fig. "Errors of all solvers"): starting
+ * from the values in u_dev (zero them for the paper's setting), apply the
+ * FAS V-cycle of Fig. "FAS multigrid V-cycle" on the global grid until
+ *   ||f - A u||_inf <= rtol * ||f||_inf      or      max_cycles cycles ran.
+ * h must be a plain float64 handle (seg == 0 or K == 0, SR_FP64), else
+ * SR_ERR_INVALID.  f_dev, u_dev: device arrays of n^3 doubles, C order
+ * [z][y][x], not overlapping; the caller owns them.  rtol >= 0,
+ * max_cycles >= 0.  On return *cycles = V-cycles applied and *rel_resid =
+ * the final ||f - A u||_inf / ||f||_inf (0 when both are 0, HUGE_VAL when
+ * only f is 0); SR_OK also when max_cycles ran out before rtol was met
+ * (compare *rel_resid with rtol).  Synchronous: it reads the residual norm
+ * back after every cycle.  SR_ERR_NONFINITE if f or a residual is not finite.
+ */
+int sr_fmg_vsolve(sr_fmg_t h, const double* f_dev, double* u_dev, double rtol, int max_cycles,
+                  int* cycles, double* rel_resid, void* stream);
 
 /* Number of kernel launches the handle's last queued solve made. */
 int sr_fmg_launches_per_solve(sr_fmg_t h, int* launches);

@@ -50,6 +50,9 @@ def _lib():
         for name in ("or_solve", "or_vcycle"):
             getattr(lib, name).argtypes = [ctypes.POINTER(OrConfig), _DP, _DP]
             getattr(lib, name).restype = ctypes.c_int
+        lib.or_vsolve.argtypes = [ctypes.POINTER(OrConfig), _DP, _DP, ctypes.c_double,
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP]
+        lib.or_vsolve.restype = ctypes.c_int
         lib.or_check_config.argtypes = [ctypes.POINTER(OrConfig)]
         lib.or_apply.argtypes = [ctypes.c_int, _DP, _DP]
         lib.or_smooth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP, _DP]
@@ -88,6 +91,16 @@ def buffer_schedule(A, B, K):
     J = (ctypes.c_int * max(K, 1))()
     _lib().or_buffer_schedule(A, B, K, J)
     return [J[i] for i in range(K)]
+
+
+def mbs_schedule(J1, K):
+    """Maximum buffer schedule (Sec. 5.2.1): the coarser compute regions are
+    exactly the supports of the finer ones, Omega^C_k = Omega^F_k for k < K,
+    i.e. J_{k+1} = 2 J_k, starting from J_1."""
+    J = [J1]
+    for _ in range(K - 1):
+        J.append(2 * J[-1])
+    return J
 
 
 def make_config(n, seg=0, K=0, J=None, A=4, B=1, alpha=1, nu1=2, nu2=2,
@@ -142,6 +155,21 @@ def vcycle(f, u, **kw):
     c = make_config(f.shape[0], **kw)
     _check(_lib().or_vcycle(ctypes.byref(c), _p(f), _p(u)), "vcycle")
     return u
+
+
+def vsolve(f, u0=None, rtol=1e-4, max_cycles=100, **kw):
+    """Iterative V-cycle solver (the comparison solver of Sec. 5.3): FASMGV
+    from u0 (zero by default) until ||f - A u||_inf <= rtol ||f||_inf.
+    Returns (u, cycles, relative residual)."""
+    f = _grid(f)
+    u = np.zeros_like(f) if u0 is None else _grid(u0, f.shape[0]).copy()
+    kw = {k: v for k, v in kw.items() if k not in ("seg", "K", "J", "A", "B")}
+    c = make_config(f.shape[0], **kw)
+    cycles = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    _check(_lib().or_vsolve(ctypes.byref(c), _p(f), _p(u), float(rtol), int(max_cycles),
+                            ctypes.byref(cycles), ctypes.byref(rel)), "vsolve")
+    return u, cycles.value, rel.value
 
 
 def apply(u):

@@ -774,6 +774,62 @@ int or_vcycle(const or_config* c, const double* f, double* u) {
   return st;
 }
 
+/* max |f - A u| over the n^3 cells of global level L (uses L->r) */
+static double residual_max(GLevel* L, const double* f) {
+  const Box* b = &L->box;
+  residual(b, L->u, f, L->r);
+  double m = 0.0;
+  for (int k = 0; k < b->n; ++k)
+    for (int j = 0; j < b->n; ++j)
+      for (int i = 0; i < b->n; ++i) {
+        const double v = fabs(L->r[at(b, i, j, k)]);
+        if (!(v <= m)) m = v; /* a NaN sticks */
+      }
+  return m;
+}
+
+/* Iterative V-cycle solver (the comparison solver of Sec. 5.3, Fig. "Errors
+ * of all solvers"): starting from the u passed in, apply FASMGV on the
+ * global grid until ||f - A u||_inf <= rtol ||f||_inf or max_cycles cycles
+ * have run.  *cycles = V-cycles applied, *rel = final ||f - A u|| / ||f||
+ * (0 when both norms are 0).  Returns 0, or -6 if a residual is not finite. */
+int or_vsolve(const or_config* c, const double* f, double* u, double rtol, int max_cycles,
+              int* cycles, double* rel) {
+  or_config pc = *c;
+  pc.seg = 0;
+  pc.K = 0;
+  int st = or_check_config(&pc);
+  if (st) return st;
+  if (max_cycles < 0 || !(rtol >= 0.0)) return -1;
+  Solver S;
+  st = solver_init(&S, &pc, c->n);
+  if (!st) {
+    GLevel* L = &S.gl[S.G - 1];
+    const long cells = (long)c->n * c->n * c->n;
+    double fnorm = 0.0;
+    for (long q = 0; q < cells; ++q)
+      if (!(fabs(f[q]) <= fnorm)) fnorm = fabs(f[q]);
+    load_grid(&L->box, L->f, f);
+    load_grid(&L->box, L->u, u);
+    int it = 0;
+    double r = residual_max(L, L->f);
+    for (;;) {
+      const double q = (fnorm > 0.0) ? r / fnorm : (r > 0.0 ? INFINITY : 0.0);
+      *rel = q;
+      if (!isfinite(r)) { st = -6; break; }
+      if (q <= rtol || it >= max_cycles) break;
+      fasmgv(&S, S.G - 1, L->f);
+      ++it;
+      r = residual_max(L, L->f);
+    }
+    *cycles = it;
+    store_grid(&L->box, L->u, u);
+    if (!st) st = S.status;
+  }
+  solver_free(&S);
+  return st;
+}
+
 /* ---- single components on a whole n^3 grid (unpadded C-order arrays) ---- */
 
 int or_apply(int n, const double* u, double* out) {

@@ -763,6 +763,53 @@ __global__ void __launch_bounds__(kThreads) k_defect(int n, const double* __rest
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
 }
 
+// *norm = max over the n^3 cells of |f - A u| (float64; |f| without u), as
+// the bit pattern of a non-negative double (which orders like the unsigned
+// integer); sets *status |= 1 if a value is not finite.  *norm must hold 0
+// on entry.
+__global__ void __launch_bounds__(kThreads) k_resid_norm(int n, const double* __restrict__ f,
+                                                         const double* __restrict__ u,
+                                                         unsigned long long* norm,
+                                                         unsigned int* status, double c6,
+                                                         double cn) {
+  const long long ncell = (long long)n * n * n;
+  const long long sy = n, sz = (long long)n * n;
+  unsigned long long m = 0;
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
+       i += (long long)gridDim.x * blockDim.x) {
+    double r = f[i];
+    if (u) {
+      const int x = (int)(i % n);
+      const long long t = i / n;
+      const int y = (int)(t % n), z = (int)(t / n);
+      const double uc = u[i];
+      const double mu = negx(uc);
+      double v[6];
+      v[0] = (x > 0) ? u[i - 1] : mu;
+      v[1] = (x < n - 1) ? u[i + 1] : mu;
+      v[2] = (y > 0) ? u[i - sy] : mu;
+      v[3] = (y < n - 1) ? u[i + sy] : mu;
+      v[4] = (z > 0) ? u[i - sz] : mu;
+      v[5] = (z < n - 1) ? u[i + sz] : mu;
+      r = fma6(cn, v, fma(c6, uc, r));
+    }
+    bad |= not_finite(r);
+    // |r| by clearing the sign bit on the integer pipe
+    const unsigned long long a = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
+    m = a > m ? a : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, m, o);
+    m = w > m ? w : m;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(status, 1u);
+    atomicMax(norm, m);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_accumulate(long long cells, const float* __restrict__ e,
                                                          double* __restrict__ u, int add,
                                                          Fk<double> k) {
@@ -925,6 +972,14 @@ cudaError_t launch_defect(int n, const double* f, const double* u, float* d,
                           unsigned int* status, cudaStream_t s) {
   const long long cells = (long long)n * n * n;
   k_defect<<<flat_blocks(cells), kThreads, 0, s>>>(n, f, u, d, status, -6.0 * sq(n), sq(n));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_norm(int n, const double* f, const double* u, unsigned long long* norm,
+                              unsigned int* status, cudaStream_t s) {
+  const long long cells = (long long)n * n * n;
+  k_resid_norm<<<flat_blocks(cells), kThreads, 0, s>>>(n, f, u, norm, status, -6.0 * sq(n),
+                                                       sq(n));
   return cudaGetLastError();
 }
 

@@ -76,7 +76,7 @@ enum Kind {
   kProlongSet, kProlongAdd, kCoarseSolve, kRestrictF, kGather, kApply,
   kChebResidualF32, kCheb2UpdateF32, kChebStepF32, kResidRestrictF32, kCoarseRhsMixed,
   kTransitionRhsMixed, kProlongSetF32, kProlongAddF32, kCoarseSolveMixed, kRestrictFF32,
-  kGatherMixed, kDefect, kAccumulate, kDiff, kDiffF32, kKinds
+  kGatherMixed, kDefect, kAccumulate, kDiff, kDiffF32, kResidNorm, kKinds
 };
 const char* const kKindName[kKinds] = {
   "cheb_residual", "cheb2_update", "cheb_step", "resid_restrict", "coarse_rhs",
@@ -85,7 +85,7 @@ const char* const kKindName[kKinds] = {
   "cheb_residual_f32", "cheb2_update_f32", "cheb_step_f32", "resid_restrict_f32",
   "coarse_rhs_mixed", "transition_rhs_mixed", "prolong_f32", "prolong_correct_f32",
   "coarse_solve_mixed", "restrict_f_f32", "gather_genuine_mixed", "defect", "accumulate",
-  "correction", "correction_f32"};
+  "correction", "correction_f32", "resid_norm"};
 
 // kind of a kernel for storage type T: float64 kinds shift to their float32
 // counterparts (same order)
@@ -127,6 +127,7 @@ struct sr_fmg_s {
   std::vector<void*> allocs;
   double* hbuf_f = nullptr;        // device staging for sr_fmg_solve_host
   double* hbuf_u = nullptr;
+  unsigned long long* norms = nullptr;  // sr_fmg_vsolve: ||f||, ||f - A u|| as double bits
   int launches = 0;                // kernel launches queued by the last solve
   Profile prof;
 
@@ -193,7 +194,9 @@ int halvings_to_coarsest(int n, int nc) {
 
 void schedule(const sr_fmg_config& c, int* J) {
   for (int k = 1; k <= c.K; ++k) {
-    if (c.use_J) {
+    if (c.mbs) {  // maximum buffer schedule, Sec. 5.2.1
+      J[k - 1] = c.A << (k - 1);
+    } else if (c.use_J) {
       J[k - 1] = c.J[k - 1];
     } else {
       const int v = c.A + c.B * (c.K - k);  // Eq. (eq:nb)
@@ -214,6 +217,7 @@ int check_config(const sr_fmg_config* c) {
   if (halvings_to_coarsest(c->n, c->n_coarse) < 0) return SR_ERR_UNSUPPORTED_SIZE;
   if (c->seg < 0 || c->K < 0 || c->K > SR_FMG_MAXK) return SR_ERR_INVALID;
   if (c->seg == 0 || c->K == 0) return SR_OK;
+  if (c->mbs && (c->A < 0 || c->A % 2 || c->A > 4096 >> c->K)) return SR_ERR_INVALID;
   if (c->n % c->seg) return SR_ERR_INVALID;
   if (c->seg % (1 << c->K)) return SR_ERR_INVALID;
   if (halvings_to_coarsest(c->n >> c->K, c->n_coarse) < 0) return SR_ERR_UNSUPPORTED_SIZE;
@@ -860,6 +864,58 @@ int sr_fmg_solve_host(sr_fmg_t h, const double* f_host, double* u_host, void* st
   if (rc) return rc;
   CK(cudaMemcpyAsync(u_host, h->hbuf_u, bytes, cudaMemcpyDeviceToHost, s));
   return sr_fmg_check(h, stream);
+}
+
+int sr_fmg_vsolve(sr_fmg_t h, const double* f_dev, double* u_dev, double rtol, int max_cycles,
+                  int* cycles, double* rel_resid, void* stream) {
+  if (!h || !f_dev || !u_dev || !cycles || !rel_resid) return SR_ERR_INVALID;
+  if (h->K || h->mixed || !(rtol >= 0.0) || max_cycles < 0) return SR_ERR_INVALID;
+  const int n = h->cfg.n;
+  const size_t bytes = (size_t)n * n * n * sizeof(double);
+  const char* fa = (const char*)f_dev;
+  const char* ua = (const char*)u_dev;
+  if (fa < ua + bytes && ua < fa + bytes) return SR_ERR_INVALID;
+  if (!is_device_ptr(f_dev) || !is_device_ptr(u_dev)) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  if (!h->norms) {
+    int rc = dalloc(h, &h->norms, 2);
+    if (rc) return rc;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const double cells = (double)n * n * n;
+  const int top = h->G - 1;
+  Hier<double>& H = h->h64;
+  *cycles = 0;
+  h->launches = 0;
+  // one norm into slot k (u == nullptr: ||f||), read back on the host
+  auto norm = [&](const double* u, int k, double* out) -> int {
+    CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned int), s));
+    CK(cudaMemsetAsync(h->norms + k, 0, sizeof(unsigned long long), s));
+    LAUNCH(h, kResidNorm, cells, u ? 7 : 0, u ? 16 : 8, s,
+           launch_resid_norm(n, f_dev, u, h->norms + k, h->status, s));
+    unsigned long long bits = 0;
+    unsigned int st = 0;
+    CK(cudaMemcpyAsync(&bits, h->norms + k, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (st & 1u) return SR_ERR_NONFINITE;
+    std::memcpy(out, &bits, sizeof(*out));
+    return SR_OK;
+  };
+  double fnorm = 0.0, r = 0.0;
+  int rc = norm(nullptr, 0, &fnorm);
+  if (rc) return rc;
+  if ((rc = norm(u_dev, 1, &r))) return rc;
+  const FieldT<double> fv = view_global<double>(H.glev[top], f_dev);
+  for (;;) {
+    const double q = fnorm > 0.0 ? r / fnorm : (r > 0.0 ? HUGE_VAL : 0.0);
+    *rel_resid = q;
+    if (q <= rtol || *cycles >= max_cycles) break;
+    if ((rc = vcycle_global<double>(h, H, top, u_dev, fv, s))) return rc;
+    ++*cycles;
+    if ((rc = norm(u_dev, 1, &r))) return rc;
+  }
+  return SR_OK;
 }
 
 int sr_fmg_launches_per_solve(sr_fmg_t h, int* launches) {

@@ -128,6 +128,11 @@ cudaError_t launch_gather_genuine(const LevelView& L, const T* u, double* out, i
 // value that is not finite.
 cudaError_t launch_defect(int n, const double* f, const double* u, float* d,
                           unsigned int* status, cudaStream_t s);
+// *norm = max over the n^3 cells of |f - A u| (float64; |f| when u is null),
+// stored as the bit pattern of the double; *norm must be 0 on entry.  Sets
+// *status |= 1 if a value is not finite.
+cudaError_t launch_resid_norm(int n, const double* f, const double* u, unsigned long long* norm,
+                              unsigned int* status, cudaStream_t s);
 // u = e (add == 0) or u += e (add == 1) on n^3 cells, e float32.
 cudaError_t launch_accumulate(long long cells, const float* e, double* u, int add,
                               cudaStream_t s);

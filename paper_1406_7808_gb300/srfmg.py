@@ -52,6 +52,7 @@ class Config(ctypes.Structure):
         ("cheb_hi", ctypes.c_double),
         ("precision", ctypes.c_int),
         ("n_outer", ctypes.c_int),
+        ("mbs", ctypes.c_int),
     ]
 
 
@@ -83,6 +84,9 @@ def load():
     lib.sr_fmg_status_string.argtypes = [ctypes.c_int]
     lib.sr_fmg_status_string.restype = ctypes.c_char_p
     lib.sr_fmg_launches_per_solve.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
+    lib.sr_fmg_vsolve.argtypes = [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                  _VP]
     lib.sr_fmg_profile.argtypes = [_VP, ctypes.c_int]
     lib.sr_fmg_profile_kinds.argtypes = []
     lib.sr_fmg_profile_read.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -127,14 +131,21 @@ def _check(status, what):
         raise SRFMGError(status, what)
 
 
+def mbs_schedule(J1, K):
+    """Maximum buffer schedule (Sec. 5.2.1): J_k = 2^(k-1) J_1, k = 1..K."""
+    return [J1 << (k - 1) for k in range(1, K + 1)]
+
+
 def buffer_schedule(A, B, K):
     """J_k = 2 floor((A + B (K - k)) / 2), k = 1..K (Eq. eq:nb)."""
     return [2 * ((A + B * (K - k)) // 2) for k in range(1, K + 1)]
 
 
 def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, nu2=2,
-                cheb_lo=1.0 / 6.0, cheb_hi=1.0, precision=SR_FP64, n_outer=2, mixed=False):
-    """sr_fmg_config for an n^3 grid (mixed=True selects SR_MIXED)."""
+                cheb_lo=1.0 / 6.0, cheb_hi=1.0, precision=SR_FP64, n_outer=2, mixed=False,
+                mbs=False):
+    """sr_fmg_config for an n^3 grid (mixed=True selects SR_MIXED; mbs=True the
+    maximum buffer schedule J_k = 2^(k-1) A)."""
     c = Config()
     load().sr_fmg_default_config(ctypes.byref(c), int(n))
     c.n_coarse, c.seg, c.K, c.A, c.B = n_coarse, seg, K, A, B
@@ -147,6 +158,7 @@ def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, 
     c.alpha, c.nu1, c.nu2 = alpha, nu1, nu2
     c.cheb_lo, c.cheb_hi = cheb_lo, cheb_hi
     c.precision, c.n_outer = (SR_MIXED if mixed else precision), n_outer
+    c.mbs = int(bool(mbs))
     return c
 
 
@@ -235,6 +247,19 @@ class Solver:
         _check(load().sr_fmg_solve(self._h, _dev(f, self.n, "f"), _dev(out, self.n, "u"),
                                    _stream()), "sr_fmg_solve")
         return out
+
+    def vsolve(self, f, u=None, rtol=1e-4, max_cycles=100):
+        """Iterative V-cycle solve (plain float64 handle): V-cycles on u (zero
+        if None, else updated in place) until ||f - A u||_inf <= rtol ||f||_inf.
+        Returns (u, cycles, relative residual)."""
+        import torch
+        if u is None:
+            u = torch.zeros_like(f)
+        cycles, rel = ctypes.c_int(), ctypes.c_double()
+        _check(load().sr_fmg_vsolve(self._h, _dev(f, self.n, "f"), _dev(u, self.n, "u"),
+                                    float(rtol), int(max_cycles), ctypes.byref(cycles),
+                                    ctypes.byref(rel), _stream()), "sr_fmg_vsolve")
+        return u, cycles.value, rel.value
 
     def solve_async(self, f, out):
         _check(load().sr_fmg_solve_async(self._h, _dev(f, self.n, "f"), _dev(out, self.n, "u"),

@@ -50,6 +50,8 @@ SR_CASES = [
     (64, dict(seg=16, K=2, A=8, B=0, n_coarse=4)),
     (128, dict(seg=32, K=3, A=8, B=0)),
     (96, dict(seg=24, K=3, A=6, B=0)),
+    (64, dict(seg=16, K=3, J=[2, 4, 8])),      # maximum buffer schedule, Sec. 5.2.1
+    (128, dict(seg=32, K=3, J=[4, 8, 16])),
 ]
 
 
@@ -66,6 +68,17 @@ def test_sr_fmg_parity(gpu, oracle_mod, n, kw):
     f, _ = inputs.manufactured(n, 1)
     ref = oracle_mod.solve(f, **_oracle_kw(kw))
     assert rel(gpu_solve(gpu, f, **kw), ref) < TOL
+
+
+def test_mbs_flag_matches_explicit_schedule(gpu, oracle_mod):
+    """mbs=True with A = J_1 is the explicit schedule J_k = 2^(k-1) J_1."""
+    n = 128
+    f, _ = inputs.manufactured(n, 3)
+    J = oracle_mod.mbs_schedule(4, 3)
+    a = gpu_solve(gpu, f, seg=32, K=3, A=4, mbs=True)
+    b = gpu_solve(gpu, f, seg=32, K=3, J=J)
+    assert np.array_equal(a, b)
+    assert rel(a, oracle_mod.solve(f, seg=32, K=3, J=J)) < TOL
 
 
 def test_sr_fmg_parity_full_size(gpu, oracle_mod):

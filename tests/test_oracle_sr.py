@@ -51,6 +51,7 @@ GEOMETRIES = [
     (24, 12, 2, [2, 2]),
     (48, 16, 2, [4, 2]),
     (32, 8, 2, [0, 0]),
+    (64, 16, 3, [2, 4, 8]),   # maximum buffer schedule (Sec. 5.2.1)
 ]
 
 
@@ -102,6 +103,36 @@ def test_error_ratio_improves_with_buffers(oracle_mod):
         er[(A, B)] = np.abs(u - uex).max() / e_conv
     assert er[(2, 0)] > er[(4, 1)] > er[(8, 0)] > er[(8, 2)] >= 0.99
     assert er[(8, 2)] < 1.1  # acceptable in the sense of Sec. 5.2 (within ~10%)
+
+
+def test_mbs_schedule(oracle_mod):
+    """Sec. 5.2.1: the coarser compute region is the whole support of the
+    finer one, so each level's buffer is twice the next coarser one's (in that
+    level's cells); it is the largest schedule the geometry check accepts."""
+    assert oracle_mod.mbs_schedule(4, 4) == [4, 8, 16, 32]
+    assert oracle_mod.mbs_schedule(2, 1) == [2]
+    J = oracle_mod.mbs_schedule(4, 3)
+    assert oracle_mod.check_config(n=64, seg=16, K=3, J=J) == 0
+    assert oracle_mod.check_config(n=64, seg=16, K=3, J=[J[0], J[1] + 2, J[2]]) != 0
+
+
+def test_mbs_error_ratio_trends(oracle_mod):
+    """Table 3's trend under the maximum buffer schedule: at fixed K and J_1
+    the error ratio falls as the segments grow (larger N_0^V), and at fixed
+    segments it falls as J_1 grows; MBS is never worse than the constant
+    schedule with the same J_1 here."""
+    n, K = 128, 2
+    f, uex = inputs.manufactured(n, 0)
+    e_conv = np.abs(oracle_mod.solve(f) - uex).max()
+
+    def e_r(seg, J):
+        return np.abs(oracle_mod.solve(f, seg=seg, K=K, J=J) - uex).max() / e_conv
+
+    by_seg = [e_r(seg, oracle_mod.mbs_schedule(2, K)) for seg in (16, 32, 64)]
+    assert by_seg[0] > by_seg[1] > by_seg[2] > 1.0
+    mbs4 = e_r(32, oracle_mod.mbs_schedule(4, K))
+    assert mbs4 < by_seg[1]
+    assert mbs4 <= e_r(32, [4, 4]) * (1 + 1e-12)
 
 
 def test_rejects_inconsistent_geometry(oracle_mod):
