@@ -22,8 +22,10 @@
  *                  cell-centred trilinear prolongation.
  *
  * Conventions for every entry point:
- *   - grids are contiguous float64 arrays of n^3 values, index [z][y][x],
- *     x fastest, owned by the caller;
+ *   - grids are contiguous float64 arrays of n^3 values (of nx ny nz values,
+ *     nx = n len[0], ny = n len[1], nz = n len[2], on a rectangular domain),
+ *     index [z][y][x], x fastest, owned by the caller; below "n^3 doubles"
+ *     stands for nx ny nz;
  *   - "device" pointers must be CUDA device memory of the device that was
  *     current when the handle was created; "host" pointers are host memory;
  *   - stream is a cudaStream_t (NULL = the legacy default stream);
@@ -61,20 +63,25 @@ typedef struct sr_fmg_s* sr_fmg_t;
 
 /*
  * Solver configuration.  sr_fmg_default_config fills it for a given n.
- *   n         fine cells per dimension; n must halve down to the coarsest grid.
- *   n_coarse  edge of the coarsest grid, solved exactly (Sec. 3.1, the "else"
- *             branch of FASMGV); 0 = keep halving until 2 or 3 cells remain.
- *             At most 8.
- *   seg       genuine segment edge on the finest level; 0 = plain FMG (no
- *             segmental refinement).  n % seg == 0 and seg % 2^K == 0.
+ *   n         fine cells per unit length (h = 1/n); the fine grid has
+ *             n len[0] x n len[1] x n len[2] cells.  n must halve down to
+ *             the coarsest grid.
+ *   n_coarse  cells per unit length of the coarsest grid, solved exactly
+ *             (Sec. 3.1, the "else" branch of FASMGV); 0 = keep halving until
+ *             2 or 3 remain.  At most 8.
+ *   seg       genuine segment edge on the finest level (segments are cubes);
+ *             0 = plain FMG (no segmental refinement).  n % seg == 0 and
+ *             seg % 2^K == 0.
  *   K         number of SR levels (the K finest levels); 0 = plain FMG.
  *   A, B      buffer schedule J_k = 2 floor((A + B (K - k)) / 2), Eq. (eq:nb),
  *             used when use_J == 0.
  *   use_J, J  when use_J != 0, J[k-1] is the buffer width J_k, k = 1..K;
  *             every J_k must be even and J_{k-1} >= J_k / 2.
  *   alpha, nu1, nu2   Chebyshev degrees of the F(alpha, nu1, nu2) cycle (1, 2, 2).
- *   cheb_lo, cheb_hi  Chebyshev interval as fractions of lambda_max(D^-1 A) = 2
- *             (D = 6 N^2 the diagonal); defaults 1/6 and 1.
+ *   cheb_lo, cheb_hi  Chebyshev interval as fractions of lambda_max(D^-1 A)
+ *             (D = w0 n^2 the diagonal; lambda_max = 2 for the 7-point
+ *             operator, the largest corner value of the symbol / w0 for a
+ *             27-point one); defaults 1/6 and 1.
  *   precision SR_FP64, or SR_MIXED: the whole FMG / SR-FMG solve S32 runs in
  *             float32 storage and arithmetic (tau right-hand sides and the
  *             coarsest solve in float64 arithmetic) inside float64 defect
@@ -85,6 +92,17 @@ typedef struct sr_fmg_s* sr_fmg_t;
  *   mbs       maximum buffer schedule (Sec. 5.2.1): J_1 = A (even) and
  *             J_k = 2^(k-1) J_1, so every coarser compute region is exactly
  *             the support of the next finer one; overrides A, B and J.
+ *   len       the domain [0, len[0]] x [0, len[1]] x [0, len[2]] in unit
+ *             lengths, each 1..64 (0 reads as 1); the paper's experiments
+ *             use (2, 1, 1) with 4 x 2 x 2 segments (Sec. 5.1).
+ *   stencil   7 (0 reads as 7): A u = n^2 (6 u - sum of the 6 face
+ *             neighbours), Eq. (eq:deq) with L = -Delta; or 27:
+ *             A u = n^2 (w0 u - w[0] sum_faces - w[1] sum_edges
+ *             - w[2] sum_corners), w0 = 6 w[0] + 12 w[1] + 8 w[2], the
+ *             paper's "27-point finite volume stencil" (Sec. 5.1).  The
+ *             weights must be consistent with -Delta (w[0] + 4 w[1] + 4 w[2]
+ *             = 1) and give a positive definite operator; 27 requires
+ *             SR_FP64.
  */
 typedef struct {
   int n;
@@ -99,11 +117,14 @@ typedef struct {
   int precision;
   int n_outer;
   int mbs;
+  int len[3];
+  int stencil;
+  double w[3];
 } sr_fmg_config;
 
-/* Fill cfg with the defaults for an n^3 grid: plain FMG, F(1,2,2), Chebyshev
- * interval [1/6, 1] * lambda_max, coarsest grid 2^3 or 3^3, buffers A = 8,
- * B = 0, SR_FP64, n_outer = 2. */
+/* Fill cfg with the defaults for an n^3 grid: unit cube, 7-point operator,
+ * plain FMG, F(1,2,2), Chebyshev interval [1/6, 1] * lambda_max, coarsest
+ * grid 2^3 or 3^3, buffers A = 8, B = 0, SR_FP64, n_outer = 2. */
 void sr_fmg_default_config(sr_fmg_config* cfg, int n);
 
 /* Validate cfg, build the level and segment plan and allocate the device
@@ -204,6 +225,22 @@ int sr_op_restrict(int n, const double* a, double* ac, void* stream);
 int sr_op_prolong(int nc, const double* ac, double* af, void* stream);
 int sr_op_coarse_solve(int n, const double* f, double* u, void* stream);
 int sr_op_vcycle(const sr_fmg_config* cfg, const double* f, double* u, void* stream);
+
+/*
+ * The same components on any grid and operator of the configuration: the
+ * grid has n len[0] x n len[1] x n len[2] cells (cfg->n per unit length),
+ * the operator is cfg->stencil / cfg->w, the smoother interval
+ * cfg->cheb_lo / cfg->cheb_hi.  For restrict cfg describes the fine grid,
+ * for prolong the coarse grid (the output has twice the cells per
+ * dimension).  Arrays unpadded, C order [z][y][x], device memory.
+ */
+int sr_op_apply_ex(const sr_fmg_config* cfg, const double* u, double* out, void* stream);
+int sr_op_residual_ex(const sr_fmg_config* cfg, const double* f, const double* u, double* r,
+                      void* stream);
+int sr_op_smooth_ex(const sr_fmg_config* cfg, int nu, const double* f, double* u, void* stream);
+int sr_op_restrict_ex(const sr_fmg_config* cfg, const double* a, double* ac, void* stream);
+int sr_op_prolong_ex(const sr_fmg_config* cfg, const double* ac, double* af, void* stream);
+int sr_op_coarse_solve_ex(const sr_fmg_config* cfg, const double* f, double* u, void* stream);
 
 /*
  * Batched solves (many right-hand sides on grids of any sizes and

@@ -35,6 +35,9 @@ class OrConfig(ctypes.Structure):
         ("reverse_segments", ctypes.c_int),
         ("n_threads", ctypes.c_int),
         ("n_coarse", ctypes.c_int),
+        ("len", ctypes.c_int * 3),
+        ("stencil", ctypes.c_int),
+        ("w", ctypes.c_double * 3),
     ]
 
 
@@ -54,12 +57,11 @@ def _lib():
                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP]
         lib.or_vsolve.restype = ctypes.c_int
         lib.or_check_config.argtypes = [ctypes.POINTER(OrConfig)]
-        lib.or_apply.argtypes = [ctypes.c_int, _DP, _DP]
-        lib.or_smooth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP, _DP]
-        lib.or_residual.argtypes = [ctypes.c_int, _DP, _DP, _DP]
-        lib.or_restrict.argtypes = [ctypes.c_int, _DP, _DP]
-        lib.or_prolong.argtypes = [ctypes.c_int, _DP, _DP]
-        lib.or_coarse_solve.argtypes = [ctypes.c_int, _DP, _DP]
+        PC = ctypes.POINTER(OrConfig)
+        for name in ("or_apply_g", "or_restrict_g", "or_prolong_g", "or_coarse_solve_g"):
+            getattr(lib, name).argtypes = [PC, _DP, _DP]
+        lib.or_smooth_g.argtypes = [PC, ctypes.c_int, _DP, _DP]
+        lib.or_residual_g.argtypes = [PC, _DP, _DP, _DP]
         lib.or_buffer_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_int)]
         lib.or_buffer_schedule.restype = None
@@ -72,13 +74,24 @@ def _p(a):
     return a.ctypes.data_as(_DP)
 
 
-def _grid(a, n=None):
+def _grid(a, shape=None):
     a = np.ascontiguousarray(a, dtype=np.float64)
-    if a.ndim != 3 or a.shape[0] != a.shape[1] or a.shape[1] != a.shape[2]:
-        raise ValueError("expected an (n, n, n) array")
-    if n is not None and a.shape[0] != n:
+    if a.ndim != 3:
+        raise ValueError("expected a 3D array")
+    if shape is not None and a.shape != tuple(shape):
         raise ValueError("grid size mismatch")
     return a
+
+
+def per_unit(a, lengths=(1, 1, 1)):
+    """Cells per unit length n of an array of shape (n len2, n len1, n len0)
+    ([z][y][x]) on the domain [0, len0] x [0, len1] x [0, len2]."""
+    lx, ly, lz = (int(v) for v in lengths)
+    nz, ny, nx = a.shape
+    n = nx // lx
+    if n < 1 or (nz, ny, nx) != (n * lz, n * ly, n * lx):
+        raise ValueError(f"shape {a.shape} does not match the domain lengths {lengths}")
+    return n
 
 
 def _check(st, what):
@@ -105,7 +118,9 @@ def mbs_schedule(J1, K):
 
 def make_config(n, seg=0, K=0, J=None, A=4, B=1, alpha=1, nu1=2, nu2=2,
                 cheb_lo=1.0 / 6.0, cheb_hi=1.0, reverse_segments=False, n_threads=0,
-                n_coarse=0):
+                n_coarse=0, lengths=(1, 1, 1), stencil=7, weights=None):
+    """n: cells per unit length; lengths: the domain [0, l0] x [0, l1] x [0, l2];
+    stencil 7 or 27 with weights (faces, edges, corners) of the 27-point operator."""
     c = OrConfig()
     c.n, c.seg, c.K = n, seg, K
     if K > 0:
@@ -119,7 +134,32 @@ def make_config(n, seg=0, K=0, J=None, A=4, B=1, alpha=1, nu1=2, nu2=2,
     c.reverse_segments = int(bool(reverse_segments))
     c.n_threads = n_threads
     c.n_coarse = n_coarse
+    for d in range(3):
+        c.len[d] = int(lengths[d])
+    c.stencil = int(stencil)
+    if weights is None and int(stencil) == 27:
+        weights = W27_DEFAULT
+    if weights is not None:
+        for d in range(3):
+            c.w[d] = float(weights[d])
     return c
+
+
+# the 27-point reading used when no weights are given: (14, 3, 1)/30 for the
+# face, edge and corner neighbours (centre 128/30)
+W27_DEFAULT = (14.0 / 30.0, 3.0 / 30.0, 1.0 / 30.0)
+
+
+GEO_KEYS = ("lengths", "stencil", "weights")
+
+
+def _geo(kw):
+    return {k: kw[k] for k in GEO_KEYS if k in kw}
+
+
+def _cfg_for(a, kw):
+    """configuration for array a (its n from the domain lengths in kw)"""
+    return make_config(per_unit(a, kw.get("lengths", (1, 1, 1))), **kw)
 
 
 def check_config(**kw):
@@ -130,7 +170,7 @@ def check_config(**kw):
 def solve(f, **kw):
     """FMG (seg=0 or K=0) or SR-FMG (FASFMGSR) of A u = f; returns u."""
     f = _grid(f)
-    c = make_config(f.shape[0], **kw)
+    c = _cfg_for(f, kw)
     u = np.zeros_like(f)
     _check(_lib().or_solve(ctypes.byref(c), _p(f), _p(u)), "solve")
     return u
@@ -143,16 +183,19 @@ def solve_refined(f, n_outer=2, **kw):
     f = _grid(f)
     u = solve(f, **kw)
     for _ in range(n_outer - 1):
-        u = u + solve(residual(u, f), **kw)
+        u = u + solve(residual(u, f, **_geo(kw)), **kw)
     return u
+
+
+def _plain_kw(kw):
+    return {k: v for k, v in kw.items() if k not in ("seg", "K", "J", "A", "B")}
 
 
 def vcycle(f, u, **kw):
     """One FAS V-cycle FASMGV(L, u, f) on the global grid; returns the new u."""
     f = _grid(f)
-    u = _grid(u, f.shape[0]).copy()
-    kw = {k: v for k, v in kw.items() if k not in ("seg", "K", "J", "A", "B")}
-    c = make_config(f.shape[0], **kw)
+    u = _grid(u, f.shape).copy()
+    c = _cfg_for(f, _plain_kw(kw))
     _check(_lib().or_vcycle(ctypes.byref(c), _p(f), _p(u)), "vcycle")
     return u
 
@@ -162,9 +205,8 @@ def vsolve(f, u0=None, rtol=1e-4, max_cycles=100, **kw):
     from u0 (zero by default) until ||f - A u||_inf <= rtol ||f||_inf.
     Returns (u, cycles, relative residual)."""
     f = _grid(f)
-    u = np.zeros_like(f) if u0 is None else _grid(u0, f.shape[0]).copy()
-    kw = {k: v for k, v in kw.items() if k not in ("seg", "K", "J", "A", "B")}
-    c = make_config(f.shape[0], **kw)
+    u = np.zeros_like(f) if u0 is None else _grid(u0, f.shape).copy()
+    c = _cfg_for(f, _plain_kw(kw))
     cycles = ctypes.c_int(0)
     rel = ctypes.c_double(0.0)
     _check(_lib().or_vsolve(ctypes.byref(c), _p(f), _p(u), float(rtol), int(max_cycles),
@@ -172,53 +214,55 @@ def vsolve(f, u0=None, rtol=1e-4, max_cycles=100, **kw):
     return u, cycles.value, rel.value
 
 
-def apply(u):
-    """A u with A = -Delta_h (7-point, Dirichlet ghosts)."""
+def apply(u, **geo):
+    """A u (7-point A = -Delta_h by default; Dirichlet ghosts, Sec. 3.3)."""
     u = _grid(u)
     out = np.empty_like(u)
-    _check(_lib().or_apply(u.shape[0], _p(u), _p(out)), "apply")
+    _check(_lib().or_apply_g(ctypes.byref(_cfg_for(u, geo)), _p(u), _p(out)), "apply")
     return out
 
 
-def residual(u, f):
+def residual(u, f, **geo):
     u = _grid(u)
-    f = _grid(f, u.shape[0])
+    f = _grid(f, u.shape)
     r = np.empty_like(u)
-    _check(_lib().or_residual(u.shape[0], _p(f), _p(u), _p(r)), "residual")
+    _check(_lib().or_residual_g(ctypes.byref(_cfg_for(u, geo)), _p(f), _p(u), _p(r)),
+           "residual")
     return r
 
 
-def smooth(u, f, nu, cheb_lo=1.0 / 6.0, cheb_hi=1.0):
+def smooth(u, f, nu, cheb_lo=1.0 / 6.0, cheb_hi=1.0, **geo):
     """Chebyshev smoother S^nu(L, u, f) on the whole grid; returns the new u."""
     u = _grid(u).copy()
-    f = _grid(f, u.shape[0])
-    _check(_lib().or_smooth(u.shape[0], nu, cheb_lo, cheb_hi, _p(f), _p(u)), "smooth")
+    f = _grid(f, u.shape)
+    c = _cfg_for(u, dict(geo, cheb_lo=cheb_lo, cheb_hi=cheb_hi))
+    _check(_lib().or_smooth_g(ctypes.byref(c), nu, _p(f), _p(u)), "smooth")
     return u
 
 
-def restrict(a):
-    """8-child average onto the (n/2)^3 grid."""
+def restrict(a, **geo):
+    """8-child average onto the grid with half the cells per dimension."""
     a = _grid(a)
-    n = a.shape[0]
-    out = np.empty((n // 2,) * 3)
-    _check(_lib().or_restrict(n, _p(a), _p(out)), "restrict")
+    out = np.empty(tuple(s // 2 for s in a.shape))
+    _check(_lib().or_restrict_g(ctypes.byref(_cfg_for(a, geo)), _p(a), _p(out)), "restrict")
     return out
 
 
-def prolong(ac):
-    """Cell-centred trilinear interpolation onto the (2 nc)^3 grid."""
+def prolong(ac, **geo):
+    """Cell-centred trilinear interpolation onto the grid with twice the cells
+    per dimension."""
     ac = _grid(ac)
-    nc = ac.shape[0]
-    out = np.empty((2 * nc,) * 3)
-    _check(_lib().or_prolong(nc, _p(ac), _p(out)), "prolong")
+    out = np.empty(tuple(2 * s for s in ac.shape))
+    _check(_lib().or_prolong_g(ctypes.byref(_cfg_for(ac, geo)), _p(ac), _p(out)), "prolong")
     return out
 
 
-def coarse_solve(f):
+def coarse_solve(f, **geo):
     """Exact solve of A u = f by a banded Cholesky factorisation (small grids)."""
     f = _grid(f)
     u = np.empty_like(f)
-    _check(_lib().or_coarse_solve(f.shape[0], _p(f), _p(u)), "coarse_solve")
+    _check(_lib().or_coarse_solve_g(ctypes.byref(_cfg_for(f, geo)), _p(f), _p(u)),
+           "coarse_solve")
     return u
 
 

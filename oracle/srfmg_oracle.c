@@ -58,7 +58,7 @@
 /* configuration (the library it is compared with has its own definition)    */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  int n;            /* fine cells per dimension N = N_M                       */
+  int n;            /* fine cells per unit length N = N_M (h = 1/N)           */
   int seg;          /* genuine segment edge on the finest level; 0 = plain FMG */
   int K;            /* number of SR levels                                     */
   int J[OR_MAXK];   /* J[k-1] = buffer width J_k, k = 1..K (Eq. eq:nb)         */
@@ -66,23 +66,92 @@ typedef struct {
   double cheb_lo, cheb_hi;  /* Chebyshev interval, fractions of lambda_max     */
   int reverse_segments;     /* process segments in reverse order               */
   int n_threads;            /* OpenMP threads over segments (0: runtime default) */
-  int n_coarse;             /* coarsest grid edge; 0: coarsen down to 2 or 3 cells */
+  int n_coarse;             /* coarsest grid, cells per unit length; 0: 2 or 3 */
+  int len[3];               /* domain [0,len0]x[0,len1]x[0,len2]; 0 reads as 1 */
+  int stencil;              /* 7 (0 reads as 7) or 27                          */
+  double w[3];              /* 27-point weights: faces, edges, corners         */
 } or_config;
+
+/* ------------------------------------------------------------------------ */
+/* the operator A u = (1/h^2) (w0 u - w1 (sum of the 6 face neighbours)       */
+/*   - w2 (sum of the 12 edge neighbours) - w3 (sum of the 8 corners)),       */
+/* w0 = 6 w1 + 12 w2 + 8 w3; w1 = 1, w2 = w3 = 0 is the 7-point Laplacian of  */
+/* Eq. (eq:deq); a 27-point stencil (Sec. 5.1) is consistent with -Delta when */
+/* w1 + 4 w2 + 4 w3 = 1.  On the Fourier/sine mode with c_d = cos(theta_d)    */
+/* A has the symbol (1/h^2)(w0 - 2 w1 sum c_d - 4 w2 sum_{d<e} c_d c_e        */
+/* - 8 w3 c_0 c_1 c_2), multilinear in c, so its range over [-1, 1]^3 is      */
+/* taken at the corners: lmax = the largest corner value / w0 bounds the      */
+/* spectrum of D^-1 A, D = w0/h^2.                                            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int pts;                  /* 7 or 27 */
+  double w0, w1, w2, w3;
+  double lmax;              /* sup of the spectrum of D^-1 A */
+} Op;
+
+static double op_symbol(const Op* o, const double c[3]) {
+  return o->w0 - 2.0 * o->w1 * (c[0] + c[1] + c[2]) -
+         4.0 * o->w2 * (c[0] * c[1] + c[0] * c[2] + c[1] * c[2]) - 8.0 * o->w3 * c[0] * c[1] * c[2];
+}
+
+/* 0, or -2 if the stencil is not a consistent, positive definite one */
+static int op_init(Op* o, int stencil, const double w[3]) {
+  memset(o, 0, sizeof(*o));
+  if (stencil == 0 || stencil == 7) {
+    o->pts = 7;
+    o->w1 = 1.0;
+  } else if (stencil == 27) {
+    o->pts = 27;
+    o->w1 = w[0]; o->w2 = w[1]; o->w3 = w[2];
+    if (fabs(o->w1 + 4.0 * o->w2 + 4.0 * o->w3 - 1.0) > 1e-12) return -2;
+  } else {
+    return -2;
+  }
+  o->w0 = 6.0 * o->w1 + 12.0 * o->w2 + 8.0 * o->w3;
+  if (!(o->w0 > 0.0)) return -2;
+  double top = 0.0;
+  for (int v = 0; v < 8; ++v) {
+    const double c[3] = {(v & 1) ? 1.0 : -1.0, (v & 2) ? 1.0 : -1.0, (v & 4) ? 1.0 : -1.0};
+    const double s = op_symbol(o, c);
+    if (v != 7 && !(s > 0.0)) return -2; /* only the constant mode may vanish */
+    if (s > top) top = s;
+  }
+  o->lmax = top / o->w0;
+  return 0;
+}
+
+/* domain lengths and operator of one problem */
+typedef struct {
+  int len[3];
+  Op op;
+} Geo;
+
+static int geo_init(Geo* g, const or_config* c) {
+  for (int d = 0; d < 3; ++d) {
+    g->len[d] = c->len[d] ? c->len[d] : 1;
+    if (g->len[d] < 1 || g->len[d] > 64) return -2;
+  }
+  return op_init(&g->op, c->stencil, c->w);
+}
 
 /* ------------------------------------------------------------------------ */
 /* boxes: a block of cells [lo, hi) of a level grid plus a one-cell shell     */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  int n;                 /* cells per dimension of the whole level grid */
+  const Geo* geo;        /* domain and operator */
+  int n;                 /* cells per unit length of the level grid (h = 1/n) */
+  int nd[3];             /* cells per dimension of the whole level grid, n len[d] */
   int lo[3], hi[3];      /* compute region */
   int ext[3];            /* stored extents hi - lo + 2 */
   long nstore;
 } Box;
 
-static void box_init(Box* b, int n, const int lo[3], const int hi[3]) {
+static void box_init(Box* b, const Geo* g, int n, const int lo[3], const int hi[3]) {
+  b->geo = g;
   b->n = n;
   b->nstore = 1;
   for (int d = 0; d < 3; ++d) {
+    b->nd[d] = n * g->len[d];
     b->lo[d] = lo[d];
     b->hi[d] = hi[d];
     b->ext[d] = hi[d] - lo[d] + 2;
@@ -90,9 +159,9 @@ static void box_init(Box* b, int n, const int lo[3], const int hi[3]) {
   }
 }
 
-static void box_whole(Box* b, int n) {
-  int lo[3] = {0, 0, 0}, hi[3] = {n, n, n};
-  box_init(b, n, lo, hi);
+static void box_whole(Box* b, const Geo* g, int n) {
+  int lo[3] = {0, 0, 0}, hi[3] = {n * g->len[0], n * g->len[1], n * g->len[2]};
+  box_init(b, g, n, lo, hi);
 }
 
 /* storage offset of level cell (i, j, k); valid for lo-1 <= . <= hi */
@@ -111,27 +180,55 @@ static double* zalloc(long n) { return (double*)calloc((size_t)n, sizeof(double)
 /* outside dimension.  Ghosts inside the domain (frozen SR ghosts) are kept.  */
 /* ------------------------------------------------------------------------ */
 static void fill_bc(const Box* b, double* a) {
-  const int n = b->n;
+  const int nx = b->nd[0], ny = b->nd[1], nz = b->nd[2];
   for (int k = b->lo[2] - 1; k <= b->hi[2]; ++k)
     for (int j = b->lo[1] - 1; j <= b->hi[1]; ++j) {
       if (b->lo[0] == 0) a[at(b, -1, j, k)] = -a[at(b, 0, j, k)];
-      if (b->hi[0] == n) a[at(b, n, j, k)] = -a[at(b, n - 1, j, k)];
+      if (b->hi[0] == nx) a[at(b, nx, j, k)] = -a[at(b, nx - 1, j, k)];
     }
   for (int k = b->lo[2] - 1; k <= b->hi[2]; ++k)
     for (int i = b->lo[0] - 1; i <= b->hi[0]; ++i) {
       if (b->lo[1] == 0) a[at(b, i, -1, k)] = -a[at(b, i, 0, k)];
-      if (b->hi[1] == n) a[at(b, i, n, k)] = -a[at(b, i, n - 1, k)];
+      if (b->hi[1] == ny) a[at(b, i, ny, k)] = -a[at(b, i, ny - 1, k)];
     }
   for (int j = b->lo[1] - 1; j <= b->hi[1]; ++j)
     for (int i = b->lo[0] - 1; i <= b->hi[0]; ++i) {
       if (b->lo[2] == 0) a[at(b, i, j, -1)] = -a[at(b, i, j, 0)];
-      if (b->hi[2] == n) a[at(b, i, j, n)] = -a[at(b, i, j, n - 1)];
+      if (b->hi[2] == nz) a[at(b, i, j, nz)] = -a[at(b, i, j, nz - 1)];
     }
+}
+
+/* out = A u on the cells [rlo, rhi), 27-point operator; u must have valid
+ * ghosts, edges and corners included */
+static void apply_A27(const Box* b, const double* u, double* out, const int rlo[3],
+                      const int rhi[3]) {
+  const Op* o = &b->geo->op;
+  const double ih2 = (double)b->n * (double)b->n;
+  for (int k = rlo[2]; k < rhi[2]; ++k)
+    for (int j = rlo[1]; j < rhi[1]; ++j)
+      for (int i = rlo[0]; i < rhi[0]; ++i) {
+        double sf = 0.0, se = 0.0, sc = 0.0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int far = (dx != 0) + (dy != 0) + (dz != 0);
+              const double v = u[at(b, i + dx, j + dy, k + dz)];
+              if (far == 1) sf += v;
+              else if (far == 2) se += v;
+              else if (far == 3) sc += v;
+            }
+        out[at(b, i, j, k)] =
+            (o->w0 * u[at(b, i, j, k)] - o->w1 * sf - o->w2 * se - o->w3 * sc) * ih2;
+      }
 }
 
 /* out = A u on the cells [rlo, rhi); u must have valid ghosts.  Eq. (eq:deq) */
 static void apply_A(const Box* b, const double* u, double* out, const int rlo[3],
                     const int rhi[3]) {
+  if (b->geo->op.pts == 27) {
+    apply_A27(b, u, out, rlo, rhi);
+    return;
+  }
   const double ih2 = (double)b->n * (double)b->n; /* 1/h^2, h = 1/n */
   for (int k = rlo[2]; k < rhi[2]; ++k)
     for (int j = rlo[1]; j < rhi[1]; ++j)
@@ -168,10 +265,11 @@ static void residual(const Box* b, double* u, const double* f, double* r) {
 static void smooth(const Box* b, int nu, double cheb_lo, double cheb_hi, double* u,
                    const double* f, double* r, double* d) {
   if (nu <= 0) return;
-  const double lmax = 2.0;
+  const Op* o = &b->geo->op;
+  const double lmax = o->lmax; /* 2 for the 7-point operator */
   const double lo = cheb_lo * lmax, hi = cheb_hi * lmax;
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
-  const double dinv = 1.0 / (6.0 * (double)b->n * (double)b->n); /* D^-1 = h^2/6 */
+  const double dinv = 1.0 / (o->w0 * (double)b->n * (double)b->n); /* D^-1 = h^2/w0 */
   double rho_old = delta / theta;
   residual(b, u, f, r);
   for (int k = b->lo[2]; k < b->hi[2]; ++k)
@@ -254,7 +352,7 @@ static void prolong(const Box* cb, const double* ac, const Box* fb, double* af,
 static void grown_region(const Box* b, int rlo[3], int rhi[3]) {
   for (int d = 0; d < 3; ++d) {
     rlo[d] = b->lo[d] > 0 ? b->lo[d] - 1 : 0;
-    rhi[d] = b->hi[d] < b->n ? b->hi[d] + 1 : b->n;
+    rhi[d] = b->hi[d] < b->nd[d] ? b->hi[d] + 1 : b->nd[d];
   }
 }
 
@@ -262,22 +360,25 @@ static void grown_region(const Box* b, int rlo[3], int rhi[3]) {
 /* coarsest-grid solve u = L_0^-1 f (Fig. "FAS multigrid V-cycle", else       */
 /* branch).  The matrix is assembled column by column by applying the         */
 /* operator to unit vectors; it is symmetric positive definite with nonzeros  */
-/* only within |row - col| <= n^2, so it is factored once by a Cholesky       */
-/* factorisation restricted to that band and solved by two triangular solves. */
+/* only within |row - col| <= nx ny (7-point) or nx ny + nx + 1 (27-point),   */
+/* so it is factored once by a Cholesky factorisation restricted to that band */
+/* and solved by two triangular solves.                                       */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  int n, m, bw;   /* grid edge, unknowns n^3, half bandwidth n^2 */
+  int m, bw;      /* unknowns nx ny nz, half bandwidth */
   double* L;      /* m x m lower factor, entries within the band */
 } Coarse;
 
 static long cell_of(const Box* b, int q) {
-  const int n = b->n;
-  return at(b, q % n, (q / n) % n, q / (n * n));
+  const int nx = b->nd[0], ny = b->nd[1];
+  return at(b, q % nx, (q / nx) % ny, q / (nx * ny));
 }
 
 static int coarse_factor(Coarse* C, const Box* b) {
-  const int n = b->n, m = n * n * n, bw = n * n;
-  C->n = n; C->m = m; C->bw = bw;
+  const int nx = b->nd[0], ny = b->nd[1], nz = b->nd[2];
+  const int m = nx * ny * nz;
+  const int bw = (b->geo->op.pts == 27) ? nx * ny + nx + 1 : nx * ny;
+  C->m = m; C->bw = bw;
   C->L = zalloc((long)m * m);
   double* e = zalloc(b->nstore);
   double* col = zalloc(b->nstore);
@@ -337,14 +438,15 @@ typedef struct {
 
 typedef struct {
   or_config cfg;
+  Geo geo;            /* domain and operator; every box points here */
   int G;              /* number of global levels; gl[G-1] is level 0 (transition / finest) */
   GLevel gl[OR_MAXG];
   Coarse coarse;      /* factor of the coarsest operator */
   int status;
 } Solver;
 
-static int glevel_alloc(GLevel* L, int n) {
-  box_whole(&L->box, n);
+static int glevel_alloc(GLevel* L, const Geo* g, int n) {
+  box_whole(&L->box, g, n);
   long s = L->box.nstore;
   L->u = zalloc(s); L->f = zalloc(s); L->rhs = zalloc(s); L->t = zalloc(s);
   L->r = zalloc(s); L->d = zalloc(s); L->rho = zalloc(s); L->e = zalloc(s);
@@ -422,7 +524,7 @@ typedef struct {
 } Scratch;
 
 typedef struct {
-  int K, nseg1, nseg;                   /* segments per dimension, total */
+  int K, nsd[3], nseg;                  /* segments per dimension, total */
   int nk[OR_MAXK + 1];                  /* level sizes N_k, k = 0..K */
   double* fk[OR_MAXK + 1];              /* f_k on SR levels (global arrays of the level grid) */
   Box fbox[OR_MAXK + 1];
@@ -431,17 +533,26 @@ typedef struct {
 
 /* segment p's compute region on SR level k: genuine region grown by J_k and
  * clipped by the domain, Omega^C_k = Omega^{V+J_k} cap Omega_k (Sec. 4) */
-static void seg_box(const or_config* c, const SR* R, int p, int k, Box* b) {
+static void seg_coords(const SR* R, int p, int q[3]) {
+  q[0] = p % R->nsd[0];
+  q[1] = (p / R->nsd[0]) % R->nsd[1];
+  q[2] = p / (R->nsd[0] * R->nsd[1]);
+}
+
+static void seg_box(const Solver* S, const SR* R, int p, int k, Box* b) {
+  const or_config* c = &S->cfg;
   const int sk = c->seg >> (R->K - k); /* genuine edge on level k */
-  const int q[3] = {p % R->nseg1, (p / R->nseg1) % R->nseg1, p / (R->nseg1 * R->nseg1)};
+  int q[3];
+  seg_coords(R, p, q);
   int lo[3], hi[3];
   for (int d = 0; d < 3; ++d) {
+    const int nd = R->nk[k] * S->geo.len[d];
     lo[d] = q[d] * sk - c->J[k - 1];
     hi[d] = (q[d] + 1) * sk + c->J[k - 1];
     if (lo[d] < 0) lo[d] = 0;
-    if (hi[d] > R->nk[k]) hi[d] = R->nk[k];
+    if (hi[d] > nd) hi[d] = nd;
   }
-  box_init(b, R->nk[k], lo, hi);
+  box_init(b, &S->geo, R->nk[k], lo, hi);
 }
 
 /* one FMG stage k for segment P, up to and including the level-1 restriction:
@@ -545,28 +656,30 @@ static int levels_below(int n, int nc) {
 }
 
 static void load_grid(const Box* b, double* a, const double* src) {
-  const int n = b->n;
-  for (int k = 0; k < n; ++k)
-    for (int j = 0; j < n; ++j)
-      for (int i = 0; i < n; ++i) a[at(b, i, j, k)] = src[((long)k * n + j) * n + i];
+  const int nx = b->nd[0], ny = b->nd[1], nz = b->nd[2];
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) a[at(b, i, j, k)] = src[((long)k * ny + j) * nx + i];
 }
 
 static void store_grid(const Box* b, const double* a, double* dst) {
-  const int n = b->n;
-  for (int k = 0; k < n; ++k)
-    for (int j = 0; j < n; ++j)
-      for (int i = 0; i < n; ++i) dst[((long)k * n + j) * n + i] = a[at(b, i, j, k)];
+  const int nx = b->nd[0], ny = b->nd[1], nz = b->nd[2];
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) dst[((long)k * ny + j) * nx + i] = a[at(b, i, j, k)];
 }
 
 /* validation shared by the solvers; returns 0 if the configuration is usable */
 int or_check_config(const or_config* c) {
+  Geo g;
+  if (geo_init(&g, c)) return -2;
   if (c->n_coarse < 0 || c->n_coarse > 16) return -2;
-  if (c->n < 2 || levels_below(c->n, c->n_coarse) < 0) return -2;
+  if (c->n < 1 || levels_below(c->n, c->n_coarse) < 0) return -2;
   if (c->alpha < 0 || c->nu1 < 0 || c->nu2 < 0) return -2;
   if (!(c->cheb_lo > 0.0 && c->cheb_hi > c->cheb_lo)) return -2;
   if (c->seg == 0 || c->K == 0) return 0;
   if (c->K < 0 || c->K > OR_MAXK || c->seg < 0) return -2;
-  if (c->n % c->seg) return -2;
+  if (c->n % c->seg) return -2; /* whole segments per unit length */
   if (c->seg % (1 << c->K)) return -2;
   const int n0 = c->n >> c->K;
   if (levels_below(n0, c->n_coarse) < 0) return -2;
@@ -588,11 +701,12 @@ void or_buffer_schedule(int A, int B, int K, int* J) {
 static int solver_init(Solver* S, const or_config* c, int n_global_top) {
   memset(S, 0, sizeof(*S));
   S->cfg = *c;
+  if (geo_init(&S->geo, c)) return -2;
   int m = levels_below(n_global_top, c->n_coarse);
   S->G = m + 1;
-  if (S->G > OR_MAXG) return -2;
+  if (m < 0 || S->G > OR_MAXG) return -2;
   for (int g = 0; g < S->G; ++g)
-    if (glevel_alloc(&S->gl[g], n_global_top >> (S->G - 1 - g))) return -3;
+    if (glevel_alloc(&S->gl[g], &S->geo, n_global_top >> (S->G - 1 - g))) return -3;
   return coarse_factor(&S->coarse, &S->gl[0].box);
 }
 
@@ -626,15 +740,18 @@ static int solve_sr(const or_config* c, const double* f, double* u) {
   SR R;
   memset(&R, 0, sizeof(R));
   R.K = K;
-  R.nseg1 = c->n / c->seg;
-  R.nseg = R.nseg1 * R.nseg1 * R.nseg1;
   for (int k = 0; k <= K; ++k) R.nk[k] = c->n >> (K - k);
   Solver S;
   int st = solver_init(&S, c, R.nk[0]);
   if (st) { solver_free(&S); return st; }
+  R.nseg = 1;
+  for (int d = 0; d < 3; ++d) {
+    R.nsd[d] = c->n * S.geo.len[d] / c->seg;
+    R.nseg *= R.nsd[d];
+  }
   /* f_k on all SR levels, restricted down from f_K, then down the global levels */
   for (int k = 1; k <= K; ++k) {
-    box_whole(&R.fbox[k], R.nk[k]);
+    box_whole(&R.fbox[k], &S.geo, R.nk[k]);
     R.fk[k] = zalloc(R.fbox[k].nstore);
     if (!R.fk[k]) st = -3;
   }
@@ -654,10 +771,11 @@ static int solve_sr(const or_config* c, const double* f, double* u) {
   for (int p = 0; p < R.nseg; ++p) {
     Segment* P = &R.seg[p];
     const int s0 = c->seg >> K;
-    const int q[3] = {p % R.nseg1, (p / R.nseg1) % R.nseg1, p / (R.nseg1 * R.nseg1)};
+    int q[3];
+    seg_coords(&R, p, q);
     for (int d = 0; d < 3; ++d) { P->g0lo[d] = q[d] * s0; P->g0hi[d] = (q[d] + 1) * s0; }
     for (int k = 1; k <= K; ++k) {
-      seg_box(c, &R, p, k, &P->box[k]);
+      seg_box(&S, &R, p, k, &P->box[k]);
       long s = P->box[k].nstore;
       if (s > maxstore) maxstore = s;
       P->u[k] = zalloc(s);
@@ -719,16 +837,17 @@ static int solve_sr(const or_config* c, const double* f, double* u) {
         }
       }
       /* return u_K: the genuine cells of every segment */
-      const int n = c->n;
+      const int nx = R.fbox[K].nd[0], ny = R.fbox[K].nd[1];
       for (int p = 0; p < R.nseg; ++p) {
         Segment* P = &R.seg[p];
         const Box* b = &P->box[K];
         const int sK = c->seg;
-        const int q[3] = {p % R.nseg1, (p / R.nseg1) % R.nseg1, p / (R.nseg1 * R.nseg1)};
+        int q[3];
+        seg_coords(&R, p, q);
         for (int z = q[2] * sK; z < (q[2] + 1) * sK; ++z)
           for (int y = q[1] * sK; y < (q[1] + 1) * sK; ++y)
             for (int x = q[0] * sK; x < (q[0] + 1) * sK; ++x)
-              u[((long)z * n + y) * n + x] = P->u[K][at(b, x, y, z)];
+              u[((long)z * ny + y) * nx + x] = P->u[K][at(b, x, y, z)];
       }
       st = S.status;
     }
@@ -779,9 +898,9 @@ static double residual_max(GLevel* L, const double* f) {
   const Box* b = &L->box;
   residual(b, L->u, f, L->r);
   double m = 0.0;
-  for (int k = 0; k < b->n; ++k)
-    for (int j = 0; j < b->n; ++j)
-      for (int i = 0; i < b->n; ++i) {
+  for (int k = 0; k < b->nd[2]; ++k)
+    for (int j = 0; j < b->nd[1]; ++j)
+      for (int i = 0; i < b->nd[0]; ++i) {
         const double v = fabs(L->r[at(b, i, j, k)]);
         if (!(v <= m)) m = v; /* a NaN sticks */
       }
@@ -805,7 +924,7 @@ int or_vsolve(const or_config* c, const double* f, double* u, double rtol, int m
   st = solver_init(&S, &pc, c->n);
   if (!st) {
     GLevel* L = &S.gl[S.G - 1];
-    const long cells = (long)c->n * c->n * c->n;
+    const long cells = (long)L->box.nd[0] * L->box.nd[1] * L->box.nd[2];
     double fnorm = 0.0;
     for (long q = 0; q < cells; ++q)
       if (!(fabs(f[q]) <= fnorm)) fnorm = fabs(f[q]);
@@ -830,11 +949,23 @@ int or_vsolve(const or_config* c, const double* f, double* u, double rtol, int m
   return st;
 }
 
-/* ---- single components on a whole n^3 grid (unpadded C-order arrays) ---- */
+/* ---- single components on a whole grid (unpadded C-order arrays) --------
+ * The *_g entry points take the grid (n cells per unit length, the domain
+ * lengths len) and the operator (stencil, w) from a configuration; the plain
+ * ones are the unit cube with the 7-point operator. */
 
-int or_apply(int n, const double* u, double* out) {
+static or_config cube7(int n) {
+  or_config c;
+  memset(&c, 0, sizeof(c));
+  c.n = n;
+  return c;
+}
+
+int or_apply_g(const or_config* c, const double* u, double* out) {
+  Geo g;
+  if (c->n < 1 || geo_init(&g, c)) return -2;
   Box b;
-  box_whole(&b, n);
+  box_whole(&b, &g, c->n);
   double* a = zalloc(b.nstore);
   double* o = zalloc(b.nstore);
   if (!a || !o) { free(a); free(o); return -3; }
@@ -846,22 +977,26 @@ int or_apply(int n, const double* u, double* out) {
   return 0;
 }
 
-int or_smooth(int n, int nu, double cheb_lo, double cheb_hi, const double* f, double* u) {
+int or_smooth_g(const or_config* c, int nu, const double* f, double* u) {
+  Geo g;
+  if (c->n < 1 || geo_init(&g, c)) return -2;
   Box b;
-  box_whole(&b, n);
+  box_whole(&b, &g, c->n);
   double *a = zalloc(b.nstore), *ff = zalloc(b.nstore), *r = zalloc(b.nstore), *d = zalloc(b.nstore);
   if (!a || !ff || !r || !d) { free(a); free(ff); free(r); free(d); return -3; }
   load_grid(&b, a, u);
   load_grid(&b, ff, f);
-  smooth(&b, nu, cheb_lo, cheb_hi, a, ff, r, d);
+  smooth(&b, nu, c->cheb_lo, c->cheb_hi, a, ff, r, d);
   store_grid(&b, a, u);
   free(a); free(ff); free(r); free(d);
   return 0;
 }
 
-int or_residual(int n, const double* f, const double* u, double* r) {
+int or_residual_g(const or_config* c, const double* f, const double* u, double* r) {
+  Geo g;
+  if (c->n < 1 || geo_init(&g, c)) return -2;
   Box b;
-  box_whole(&b, n);
+  box_whole(&b, &g, c->n);
   double *a = zalloc(b.nstore), *ff = zalloc(b.nstore), *rr = zalloc(b.nstore);
   if (!a || !ff || !rr) { free(a); free(ff); free(rr); return -3; }
   load_grid(&b, a, u);
@@ -872,11 +1007,13 @@ int or_residual(int n, const double* f, const double* u, double* r) {
   return 0;
 }
 
-int or_restrict(int n, const double* a, double* ac) {
-  if (n % 2) return -2;
+/* c describes the fine grid (c->n even) */
+int or_restrict_g(const or_config* c, const double* a, double* ac) {
+  Geo g;
+  if (c->n < 2 || c->n % 2 || geo_init(&g, c)) return -2;
   Box fb, cb;
-  box_whole(&fb, n);
-  box_whole(&cb, n / 2);
+  box_whole(&fb, &g, c->n);
+  box_whole(&cb, &g, c->n / 2);
   double *x = zalloc(fb.nstore), *y = zalloc(cb.nstore);
   if (!x || !y) { free(x); free(y); return -3; }
   load_grid(&fb, x, a);
@@ -886,11 +1023,14 @@ int or_restrict(int n, const double* a, double* ac) {
   return 0;
 }
 
-/* fine (2 nc)^3 = trilinear prolongation of the coarse nc^3 grid (boundary ghosts by Sec. 3.3) */
-int or_prolong(int nc, const double* ac, double* af) {
+/* fine grid (2 n per unit length) = trilinear prolongation of the coarse grid
+ * c describes (boundary ghosts by Sec. 3.3) */
+int or_prolong_g(const or_config* c, const double* ac, double* af) {
+  Geo g;
+  if (c->n < 1 || geo_init(&g, c)) return -2;
   Box fb, cb;
-  box_whole(&cb, nc);
-  box_whole(&fb, 2 * nc);
+  box_whole(&cb, &g, c->n);
+  box_whole(&fb, &g, 2 * c->n);
   double *x = zalloc(cb.nstore), *y = zalloc(fb.nstore);
   if (!x || !y) { free(x); free(y); return -3; }
   load_grid(&cb, x, ac);
@@ -901,9 +1041,11 @@ int or_prolong(int nc, const double* ac, double* af) {
   return 0;
 }
 
-int or_coarse_solve(int n, const double* f, double* u) {
+int or_coarse_solve_g(const or_config* c, const double* f, double* u) {
+  Geo g;
+  if (c->n < 1 || geo_init(&g, c)) return -2;
   Box b;
-  box_whole(&b, n);
+  box_whole(&b, &g, c->n);
   double *ff = zalloc(b.nstore), *uu = zalloc(b.nstore);
   Coarse C;
   memset(&C, 0, sizeof(C));
@@ -916,6 +1058,38 @@ int or_coarse_solve(int n, const double* f, double* u) {
   coarse_free(&C);
   free(ff); free(uu);
   return st;
+}
+
+int or_apply(int n, const double* u, double* out) {
+  const or_config c = cube7(n);
+  return or_apply_g(&c, u, out);
+}
+
+int or_smooth(int n, int nu, double cheb_lo, double cheb_hi, const double* f, double* u) {
+  or_config c = cube7(n);
+  c.cheb_lo = cheb_lo;
+  c.cheb_hi = cheb_hi;
+  return or_smooth_g(&c, nu, f, u);
+}
+
+int or_residual(int n, const double* f, const double* u, double* r) {
+  const or_config c = cube7(n);
+  return or_residual_g(&c, f, u, r);
+}
+
+int or_restrict(int n, const double* a, double* ac) {
+  const or_config c = cube7(n);
+  return or_restrict_g(&c, a, ac);
+}
+
+int or_prolong(int nc, const double* ac, double* af) {
+  const or_config c = cube7(nc);
+  return or_prolong_g(&c, ac, af);
+}
+
+int or_coarse_solve(int n, const double* f, double* u) {
+  const or_config c = cube7(n);
+  return or_coarse_solve_g(&c, f, u);
 }
 
 int or_max_threads(void) {

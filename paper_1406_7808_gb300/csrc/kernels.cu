@@ -100,8 +100,8 @@ __device__ __forceinline__ void region_of(const BoxDesc& b, int which, int lo[3]
 }
 
 // The six neighbours of stored cell c at (x, y, z), converted to A; a
-// neighbour outside [0, n) is minus the centre value (mirror through u = 0
-// on the face).
+// neighbour outside the level grid [0, nx) x [0, ny) x [0, nz) is minus the
+// centre value (mirror through u = 0 on the face).
 template <typename A, typename T>
 __device__ __forceinline__ A acc_of(T x) {
   return (A)x;
@@ -113,14 +113,15 @@ __device__ __forceinline__ double acc_of<double, float>(float x) {
 
 template <typename A, typename T>
 __device__ __forceinline__ void neighbours(const T* __restrict__ a, long long c, const BoxDesc& b,
-                                           int n, int x, int y, int z, T centre, A v[6]) {
+                                           const LevelView& L, int x, int y, int z, T centre,
+                                           A v[6]) {
   const T m = negx(centre);
   v[0] = acc_of<A>((x > 0) ? a[c - 1] : m);
-  v[1] = acc_of<A>((x < n - 1) ? a[c + 1] : m);
+  v[1] = acc_of<A>((x < L.nx - 1) ? a[c + 1] : m);
   v[2] = acc_of<A>((y > 0) ? a[c - b.sy] : m);
-  v[3] = acc_of<A>((y < n - 1) ? a[c + b.sy] : m);
+  v[3] = acc_of<A>((y < L.ny - 1) ? a[c + b.sy] : m);
   v[4] = acc_of<A>((z > 0) ? a[c - b.sz] : m);
-  v[5] = acc_of<A>((z < n - 1) ? a[c + b.sz] : m);
+  v[5] = acc_of<A>((z < L.nz - 1) ? a[c + b.sz] : m);
 }
 
 // acc + w * (v0 + ... + v5) as six fused multiply-adds
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kZThreads) k_cheb_residual_zm(LevelView L,
   __syncthreads();
   int x, y, z0, z1;
   if (!ztile(B, tiles, x, y, z0, z1)) return;
-  const int n = L.n;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
   const long long sy = B.sy, sz = B.sz, fsz = FB.sz;
   long long c = at(B, x, y, z0);
   long long fc = at(FB, x, y, z0);
@@ -192,12 +193,12 @@ __global__ void __launch_bounds__(kZThreads) k_cheb_residual_zm(LevelView L,
   T um = (z0 > 0) ? u[c - sz] : negx(uc);
   for (int z = z0; z < z1; ++z) {
     const T m = negx(uc);
-    const T up = (z < n - 1) ? u[c + sz] : m;
+    const T up = (z < nz - 1) ? u[c + sz] : m;
     T v[6];
     v[0] = (x > 0) ? u[c - 1] : m;
-    v[1] = (x < n - 1) ? u[c + 1] : m;
+    v[1] = (x < nx - 1) ? u[c + 1] : m;
     v[2] = (y > 0) ? u[c - sy] : m;
-    v[3] = (y < n - 1) ? u[c + sy] : m;
+    v[3] = (y < ny - 1) ? u[c + sy] : m;
     v[4] = um;
     v[5] = up;
     const T fv = f.p[fc];
@@ -218,19 +219,19 @@ __global__ void __launch_bounds__(kZThreads) k_cheb2_update_zm(LevelView L, T* _
   __syncthreads();
   int x, y, z0, z1;
   if (!ztile(B, tiles, x, y, z0, z1)) return;
-  const int n = L.n;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
   const long long sy = B.sy, sz = B.sz;
   long long c = at(B, x, y, z0);
   T rc = r[c];
   T rm = (z0 > 0) ? r[c - sz] : negx(rc);
   for (int z = z0; z < z1; ++z) {
     const T m = negx(rc);
-    const T rp = (z < n - 1) ? r[c + sz] : m;
+    const T rp = (z < nz - 1) ? r[c + sz] : m;
     T v[6];
     v[0] = (x > 0) ? r[c - 1] : m;
-    v[1] = (x < n - 1) ? r[c + 1] : m;
+    v[1] = (x < nx - 1) ? r[c + 1] : m;
     v[2] = (y > 0) ? r[c - sy] : m;
-    v[3] = (y < n - 1) ? r[c + sy] : m;
+    v[3] = (y < ny - 1) ? r[c + sy] : m;
     v[4] = rm;
     v[5] = rp;
     u[c] = fma6(b, v, fma(a, rc, u[c]));
@@ -257,13 +258,13 @@ __global__ void __launch_bounds__(kThreads) k_cheb_residual(LevelView L, const T
   __syncthreads();
   const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
   const int ncell = ex * ey * ez;
-  const int n = L.n;
+
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
     const T uc = u[c];
     T v[6];
-    neighbours<T>(u, c, B, n, q.x, q.y, q.z, uc, v);
+    neighbours<T>(u, c, B, L, q.x, q.y, q.z, uc, v);
     const T fv = f.p[at(FB, q.x, q.y, q.z)];
     r[c] = fma6(sixth, v, fma(fv, cf, negx(uc)));
   }
@@ -278,13 +279,13 @@ __global__ void __launch_bounds__(kThreads) k_cheb2_update(LevelView L, T* __res
   __syncthreads();
   const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
   const int ncell = ex * ey * ez;
-  const int n = L.n;
+
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
     const T rc = r[c];
     T v[6];
-    neighbours<T>(r, c, B, n, q.x, q.y, q.z, rc, v);
+    neighbours<T>(r, c, B, L, q.x, q.y, q.z, rc, v);
     u[c] = fma6(b, v, fma(a, rc, u[c]));
   }
 }
@@ -324,13 +325,13 @@ __global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const T* __rest
   __syncthreads();
   const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
   const int ncell = ex * ey * ez;
-  const int n = L.n;
+
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
     const T uc = u[c];
     T v[6];
-    neighbours<T>(u, c, B, n, q.x, q.y, q.z, uc, v);
+    neighbours<T>(u, c, B, L, q.x, q.y, q.z, uc, v);
     // apply: c6 = 6 n^2, cn = -n^2; residual: c6 = -6 n^2, cn = n^2
     const T base = residual ? f.p[at(FB, q.x, q.y, q.z)] : k.zero;
     out[c] = fma6(cn, v, fma(c6, uc, base));
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F, const 
   region_of(B, kRestrict, lo, hi);
   const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
   const int ncell = ex * ey * ez;
-  const int n = F.n;
+
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, lo, ex, ey);
     const int x0 = 2 * q.x, y0 = 2 * q.y, z0 = 2 * q.z;
@@ -392,8 +393,8 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F, const 
     S = fma(v[1][1][0], k.one, S);
     S = fma(v[1][1][1], k.one, S);
     // the 24 outer neighbours, mirrored with a sign flip outside the domain
-    const bool xl = x0 > 0, xr = x0 + 2 < n, yl = y0 > 0, yr = y0 + 2 < n, zl = z0 > 0,
-               zr = z0 + 2 < n;
+    const bool xl = x0 > 0, xr = x0 + 2 < F.nx, yl = y0 > 0, yr = y0 + 2 < F.ny, zl = z0 > 0,
+               zr = z0 + 2 < F.nz;
     T O = k.zero;
 #pragma unroll
     for (int cz = 0; cz < 2; ++cz)
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView 
     FBx = (F.nbox == 1) ? F.boxes[0] : F.boxes[blockIdx.y];
   }
   __syncthreads();
-  const int n = C.n;
+
   const bool shell = B.ox < B.lo[0];
   int lo[3], hi[3];
 #pragma unroll
@@ -452,7 +453,8 @@ __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView 
   const int ncell = ex * ey * ez;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, lo, ex, ey);
-    const bool inside_domain = q.x >= 0 && q.x < n && q.y >= 0 && q.y < n && q.z >= 0 && q.z < n;
+    const bool inside_domain =
+        q.x >= 0 && q.x < C.nx && q.y >= 0 && q.y < C.ny && q.z >= 0 && q.z < C.nz;
     if (!inside_domain) continue;
     const long long c = at(B, q.x, q.y, q.z);
     const T uc = u[c];
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView 
     const bool inF = q.x >= FBx.rlo[0] && q.x < FBx.rhi[0] && q.y >= FBx.rlo[1] &&
                      q.y < FBx.rhi[1] && q.z >= FBx.rlo[2] && q.z < FBx.rhi[2];
     double v[6];
-    neighbours<double>(u, c, B, n, q.x, q.y, q.z, uc, v);
+    neighbours<double>(u, c, B, C, q.x, q.y, q.z, uc, v);
     rhs[c] = (T)fma6(cn, v, fma(c6, widen(uc), inF ? widen(rho[c]) : k.zero));
   }
 }
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[0];
   __syncthreads();
-  const int n = C.n;
+
   const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
   const int ncell = ex * ey * ez;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
     const long long c = at(B, q.x, q.y, q.z);
     const T tc = t[c];
     double v[6];
-    neighbours<double>(t, c, B, n, q.x, q.y, q.z, tc, v);
+    neighbours<double>(t, c, B, C, q.x, q.y, q.z, tc, v);
     u[c] = tc;
     rhs[c] = (T)fma6(cn, v, fma(c6, widen(tc), widen(rho[c])));
   }
@@ -530,17 +532,17 @@ __global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const T* __re
   const int Z0 = clo[2] + tz * kPZChunk;
   const int Z1 = min(Z0 + kPZChunk, clo[2] + cex[2]);
   if (Z0 >= Z1) return;
-  const int nc = C.n;
+  const int ncx = C.nx, ncy = C.ny, ncz = C.nz;
   // columns of the 3x3 neighbourhood: mirrored index, sign flip, needed?
   int xi[3], yi[3];
   bool fx[3], fy[3], nx[3], ny[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     int x = X + d - 1, y = Y + d - 1;
-    fx[d] = x < 0 || x >= nc;
-    fy[d] = y < 0 || y >= nc;
-    xi[d] = x < 0 ? 0 : (x >= nc ? nc - 1 : x);
-    yi[d] = y < 0 ? 0 : (y >= nc ? nc - 1 : y);
+    fx[d] = x < 0 || x >= ncx;
+    fy[d] = y < 0 || y >= ncy;
+    xi[d] = x < 0 ? 0 : (x >= ncx ? ncx - 1 : x);
+    yi[d] = y < 0 ? 0 : (y >= ncy ? ncy - 1 : y);
   }
   nx[0] = 2 * X >= plo[0];
   nx[1] = true;
@@ -550,8 +552,8 @@ __global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const T* __re
   ny[2] = 2 * Y + 1 < phi[1];
   // 2x2 (x, y)-interpolated values of coarse plane Z (unscaled)
   auto plane = [&](int Z, T q[2][2]) {
-    const bool fz = Z < 0 || Z >= nc;
-    const int zi = Z < 0 ? 0 : (Z >= nc ? nc - 1 : Z);
+    const bool fz = Z < 0 || Z >= ncz;
+    const int zi = Z < 0 ? 0 : (Z >= ncz ? ncz - 1 : Z);
     T px[3][2];
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy) {
@@ -635,13 +637,13 @@ __global__ void __launch_bounds__(kThreads) k_diff(LevelView C, const T* __restr
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[blockIdx.y];
   __syncthreads();
-  const int n = C.n;
+  const int nd[3] = {C.nx, C.ny, C.nz};
   const bool shell = B.ox < B.lo[0];
   int lo[3], hi[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     lo[d] = shell ? max(B.lo[d] - 1, 0) : B.lo[d];
-    hi[d] = shell ? min(B.hi[d] + 1, n) : B.hi[d];
+    hi[d] = shell ? min(B.hi[d] + 1, nd[d]) : B.hi[d];
   }
   const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
   const int ncell = ex * ey * ez;
@@ -658,19 +660,19 @@ __global__ void k_coarse_solve(LevelView L, const double* __restrict__ minv, Fie
                                T* __restrict__ u, Fk<double> k) {
   const BoxDesc B = L.boxes[0];
   const BoxDesc FB = f.boxes[0];
-  const int n = L.n, m = n * n * n;
+  const int nx = L.nx, ny = L.ny, m = nx * ny * L.nz;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= m) return;
   double s = k.zero;
   for (int j = lane; j < m; j += 32) {
-    const int x = j % n, y = (j / n) % n, z = j / (n * n);
+    const int x = j % nx, y = (j / nx) % ny, z = j / (nx * ny);
     s = fma(minv[(long long)warp * m + j], widen(f.p[at(FB, x, y, z)]), s);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s = fma(__shfl_xor_sync(0xffffffffu, s, o), k.one, s);
   if (lane == 0) {
-    const int x = warp % n, y = (warp / n) % n, z = warp / (n * n);
+    const int x = warp % nx, y = (warp / nx) % ny, z = warp / (nx * ny);
     u[at(B, x, y, z)] = (T)s;
   }
 }
@@ -683,20 +685,20 @@ __device__ __forceinline__ bool not_finite(float v) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_restrict_global(int nf, const T* __restrict__ ff,
+__global__ void __launch_bounds__(kThreads) k_restrict_global(Dims fd, const T* __restrict__ ff,
                                                               T* __restrict__ fc, int check,
                                                               unsigned int* status, T eighth,
                                                               Fk<T> k) {
-  const int nc = nf / 2;
-  const long long ncell = (long long)nc * nc * nc;
+  const int cx = fd.x / 2, cy = fd.y / 2, cz = fd.z / 2;
+  const long long ncell = (long long)cx * cy * cz;
   bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
        i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % nc);
-    const long long t = i / nc;
-    const int y = (int)(t % nc), z = (int)(t / nc);
-    const long long f0 = ((long long)(2 * z) * nf + 2 * y) * nf + 2 * x;
-    const long long py = nf, pz = (long long)nf * nf;
+    const int x = (int)(i % cx);
+    const long long t = i / cx;
+    const int y = (int)(t % cy), z = (int)(t / cy);
+    const long long py = fd.x, pz = (long long)fd.x * fd.y;
+    const long long f0 = (2 * z) * pz + (2 * y) * py + 2 * x;
     const T a[8] = {ff[f0], ff[f0 + 1], ff[f0 + py], ff[f0 + py + 1],
                     ff[f0 + pz], ff[f0 + pz + 1], ff[f0 + pz + py], ff[f0 + pz + py + 1]};
     T s = k.zero;
@@ -721,22 +723,22 @@ __global__ void __launch_bounds__(kThreads) k_gather_genuine(LevelView L, const 
   region_of(B, kGenuine, lo, hi);
   const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
   const int ncell = ex * ey * ez;
-  const long long n = L.n;
+  const long long nx = L.nx, ny = L.ny;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const Cell q = cell_of(i, lo, ex, ey);
-    const long long o = (q.z * n + q.y) * n + q.x;
+    const long long o = (q.z * ny + q.y) * nx + q.x;
     const double v = widen(u[at(B, q.x, q.y, q.z)]);
     out[o] = add ? fma(v, k.one, out[o]) : v;
   }
 }
 
 // d = float(f - A u) with float64 arithmetic, or d = float(f) without u
-__global__ void __launch_bounds__(kThreads) k_defect(int n, const double* __restrict__ f,
+__global__ void __launch_bounds__(kThreads) k_defect(Dims g, const double* __restrict__ f,
                                                      const double* __restrict__ u,
                                                      float* __restrict__ d, unsigned int* status,
                                                      double c6, double cn) {
-  const long long ncell = (long long)n * n * n;
-  const long long sy = n, sz = (long long)n * n;
+  const long long ncell = (long long)g.x * g.y * g.z;
+  const long long sy = g.x, sz = (long long)g.x * g.y;
   bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
        i += (long long)gridDim.x * blockDim.x) {
@@ -746,52 +748,52 @@ __global__ void __launch_bounds__(kThreads) k_defect(int n, const double* __rest
       d[i] = (float)fv;
       continue;
     }
-    const int x = (int)(i % n);
-    const long long t = i / n;
-    const int y = (int)(t % n), z = (int)(t / n);
+    const int x = (int)(i % g.x);
+    const long long t = i / g.x;
+    const int y = (int)(t % g.y), z = (int)(t / g.y);
     const double uc = u[i];
     const double m = negx(uc);
     double v[6];
     v[0] = (x > 0) ? u[i - 1] : m;
-    v[1] = (x < n - 1) ? u[i + 1] : m;
+    v[1] = (x < g.x - 1) ? u[i + 1] : m;
     v[2] = (y > 0) ? u[i - sy] : m;
-    v[3] = (y < n - 1) ? u[i + sy] : m;
+    v[3] = (y < g.y - 1) ? u[i + sy] : m;
     v[4] = (z > 0) ? u[i - sz] : m;
-    v[5] = (z < n - 1) ? u[i + sz] : m;
+    v[5] = (z < g.z - 1) ? u[i + sz] : m;
     d[i] = (float)fma6(cn, v, fma(c6, uc, fv));
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
 }
 
-// *norm = max over the n^3 cells of |f - A u| (float64; |f| without u), as
+// *norm = max over the cells of the grid of |f - A u| (float64; |f| without u), as
 // the bit pattern of a non-negative double (which orders like the unsigned
 // integer); sets *status |= 1 if a value is not finite.  *norm must hold 0
 // on entry.
-__global__ void __launch_bounds__(kThreads) k_resid_norm(int n, const double* __restrict__ f,
+__global__ void __launch_bounds__(kThreads) k_resid_norm(Dims g, const double* __restrict__ f,
                                                          const double* __restrict__ u,
                                                          unsigned long long* norm,
                                                          unsigned int* status, double c6,
                                                          double cn) {
-  const long long ncell = (long long)n * n * n;
-  const long long sy = n, sz = (long long)n * n;
+  const long long ncell = (long long)g.x * g.y * g.z;
+  const long long sy = g.x, sz = (long long)g.x * g.y;
   unsigned long long m = 0;
   bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
        i += (long long)gridDim.x * blockDim.x) {
     double r = f[i];
     if (u) {
-      const int x = (int)(i % n);
-      const long long t = i / n;
-      const int y = (int)(t % n), z = (int)(t / n);
+      const int x = (int)(i % g.x);
+      const long long t = i / g.x;
+      const int y = (int)(t % g.y), z = (int)(t / g.y);
       const double uc = u[i];
       const double mu = negx(uc);
       double v[6];
       v[0] = (x > 0) ? u[i - 1] : mu;
-      v[1] = (x < n - 1) ? u[i + 1] : mu;
+      v[1] = (x < g.x - 1) ? u[i + 1] : mu;
       v[2] = (y > 0) ? u[i - sy] : mu;
-      v[3] = (y < n - 1) ? u[i + sy] : mu;
+      v[3] = (y < g.y - 1) ? u[i + sy] : mu;
       v[4] = (z > 0) ? u[i - sz] : mu;
-      v[5] = (z < n - 1) ? u[i + sz] : mu;
+      v[5] = (z < g.z - 1) ? u[i + sz] : mu;
       r = fma6(cn, v, fma(c6, uc, r));
     }
     bad |= not_finite(r);
@@ -944,7 +946,7 @@ cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaSt
 template <typename T>
 cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldT<T> f, T* u,
                                 cudaStream_t s) {
-  const int m = L.n * L.n * L.n;
+  const int m = L.nx * L.ny * L.nz;
   const int warps_per_block = 8;
   const int blocks = (m + warps_per_block - 1) / warps_per_block;
   k_coarse_solve<T><<<blocks, warps_per_block * 32, 0, s>>>(L, minv, f, u, fk<double>());
@@ -952,11 +954,11 @@ cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldT<T
 }
 
 template <typename T>
-cudaError_t launch_restrict_global(int nf, const T* ff, T* fc, int check, unsigned int* status,
+cudaError_t launch_restrict_global(Dims fd, const T* ff, T* fc, int check, unsigned int* status,
                                    cudaStream_t s) {
-  const long long nc = nf / 2;
-  k_restrict_global<T><<<flat_blocks(nc * nc * nc), kThreads, 0, s>>>(nf, ff, fc, check, status,
-                                                                      T(0.125), fk<T>());
+  const long long cells = (long long)(fd.x / 2) * (fd.y / 2) * (fd.z / 2);
+  k_restrict_global<T><<<flat_blocks(cells), kThreads, 0, s>>>(fd, ff, fc, check, status,
+                                                               T(0.125), fk<T>());
   return cudaGetLastError();
 }
 
@@ -968,17 +970,17 @@ cudaError_t launch_gather_genuine(const LevelView& L, const T* u, double* out, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_defect(int n, const double* f, const double* u, float* d,
+cudaError_t launch_defect(Dims g, int n, const double* f, const double* u, float* d,
                           unsigned int* status, cudaStream_t s) {
-  const long long cells = (long long)n * n * n;
-  k_defect<<<flat_blocks(cells), kThreads, 0, s>>>(n, f, u, d, status, -6.0 * sq(n), sq(n));
+  const long long cells = (long long)g.x * g.y * g.z;
+  k_defect<<<flat_blocks(cells), kThreads, 0, s>>>(g, f, u, d, status, -6.0 * sq(n), sq(n));
   return cudaGetLastError();
 }
 
-cudaError_t launch_resid_norm(int n, const double* f, const double* u, unsigned long long* norm,
-                              unsigned int* status, cudaStream_t s) {
-  const long long cells = (long long)n * n * n;
-  k_resid_norm<<<flat_blocks(cells), kThreads, 0, s>>>(n, f, u, norm, status, -6.0 * sq(n),
+cudaError_t launch_resid_norm(Dims g, int n, const double* f, const double* u,
+                              unsigned long long* norm, unsigned int* status, cudaStream_t s) {
+  const long long cells = (long long)g.x * g.y * g.z;
+  k_resid_norm<<<flat_blocks(cells), kThreads, 0, s>>>(g, f, u, norm, status, -6.0 * sq(n),
                                                        sq(n));
   return cudaGetLastError();
 }
@@ -1010,7 +1012,7 @@ cudaError_t launch_accumulate(long long cells, const float* e, double* u, int ad
   template cudaError_t launch_diff<T>(const LevelView&, const T*, const T*, T*, cudaStream_t);  \
   template cudaError_t launch_coarse_solve<T>(const LevelView&, const double*, FieldT<T>, T*,  \
                                               cudaStream_t);                                   \
-  template cudaError_t launch_restrict_global<T>(int, const T*, T*, int, unsigned int*,        \
+  template cudaError_t launch_restrict_global<T>(Dims, const T*, T*, int, unsigned int*,       \
                                                  cudaStream_t);                                \
   template cudaError_t launch_gather_genuine<T>(const LevelView&, const T*, double*, int,      \
                                                 cudaStream_t);

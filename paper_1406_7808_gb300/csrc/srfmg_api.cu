@@ -38,7 +38,8 @@ namespace {
 
 // geometry of one level: its boxes on the host and the device
 struct Geom {
-  int n = 0;
+  int n = 0;                     // cells per unit length
+  int nd[3] = {0, 0, 0};         // cells per dimension of the whole level grid
   int nbox = 0;
   long long slot = 0;            // elements per box (SR levels)
   std::vector<BoxDesc> hboxes;
@@ -64,7 +65,7 @@ struct Hier {
 
 struct Cheb {
   int nu = 0;
-  double a = 0, b = 0;              // degree-2 polynomial form
+  double a = 0, b = 0, c2 = 0;      // degree-2 polynomial form
   std::vector<double> alpha, beta;  // recurrence steps
 };
 
@@ -123,6 +124,10 @@ struct sr_fmg_s {
   double* minv = nullptr;          // inverse of the coarsest operator
   unsigned int* status = nullptr;  // device status bits
   Cheb pre, post, fmg;
+  int len[3] = {1, 1, 1};          // domain lengths
+  bool op27 = false;               // 27-point operator (float64 only)
+  W27 w27{6.0, 1.0, 0.0, 0.0};     // operator weights (7-point: w0 = 6, w1 = 1)
+  double lmax = 2.0;               // lambda_max(D^-1 A)
   size_t bytes = 0;
   std::vector<void*> allocs;
   double* hbuf_f = nullptr;        // device staging for sr_fmg_solve_host
@@ -205,9 +210,55 @@ void schedule(const sr_fmg_config& c, int* J) {
   }
 }
 
+// weights of the configured operator; SR_ERR_INVALID if the stencil is not
+// 7, or a 27-point one consistent with -Delta and positive definite.  The
+// operator's symbol on the sine mode with c_d = cos(theta_d) is
+// w0 - 2 w1 sum c_d - 4 w2 sum c_d c_e - 8 w3 c_0 c_1 c_2, multilinear in c,
+// so its extremes over [-1, 1]^3 lie at the corners.
+int op_weights(const sr_fmg_config* c, W27* w, double* lmax) {
+  if (c->stencil == 0 || c->stencil == 7) {
+    *w = W27{6.0, 1.0, 0.0, 0.0};
+    *lmax = 2.0;
+    return SR_OK;
+  }
+  if (c->stencil != 27) return SR_ERR_INVALID;
+  const double w1 = c->w[0], w2 = c->w[1], w3 = c->w[2];
+  if (!(std::fabs(w1 + 4.0 * w2 + 4.0 * w3 - 1.0) <= 1e-12)) return SR_ERR_INVALID;
+  const double w0 = 6.0 * w1 + 12.0 * w2 + 8.0 * w3;
+  if (!(w0 > 0.0)) return SR_ERR_INVALID;
+  double top = 0.0;
+  for (int v = 0; v < 8; ++v) {
+    const double x = (v & 1) ? 1.0 : -1.0, y = (v & 2) ? 1.0 : -1.0, z = (v & 4) ? 1.0 : -1.0;
+    const double sym = w0 - 2.0 * w1 * (x + y + z) - 4.0 * w2 * (x * y + x * z + y * z) -
+                       8.0 * w3 * x * y * z;
+    if (v != 7 && !(sym > 0.0)) return SR_ERR_INVALID;
+    if (sym > top) top = sym;
+  }
+  *w = W27{w0, w1, w2, w3};
+  *lmax = top / w0;
+  return SR_OK;
+}
+
+int lengths_of(const sr_fmg_config* c, int len[3]) {
+  for (int d = 0; d < 3; ++d) {
+    len[d] = c->len[d] ? c->len[d] : 1;
+    if (len[d] < 1 || len[d] > 64) return SR_ERR_INVALID;
+  }
+  return SR_OK;
+}
+
 int check_config(const sr_fmg_config* c) {
   if (!c) return SR_ERR_INVALID;
   if (c->precision != SR_FP64 && c->precision != SR_MIXED) return SR_ERR_INVALID;
+  int len[3];
+  W27 w;
+  double lmax;
+  if (lengths_of(c, len) || op_weights(c, &w, &lmax)) return SR_ERR_INVALID;
+  if (c->stencil == 27 && c->precision != SR_FP64) return SR_ERR_INVALID;
+  {
+    const long long cells = (long long)c->n * c->n * c->n * len[0] * len[1] * len[2];
+    if (c->n > 0 && cells > (1LL << 34)) return SR_ERR_UNSUPPORTED_SIZE;
+  }
   if (c->precision == SR_MIXED && (c->n_outer < 0 || c->n_outer > 16)) return SR_ERR_INVALID;
   if (c->alpha < 0 || c->nu1 < 0 || c->nu2 < 0 || c->alpha > 16 || c->nu1 > 16 || c->nu2 > 16)
     return SR_ERR_INVALID;
@@ -222,7 +273,7 @@ int check_config(const sr_fmg_config* c) {
   if (c->seg % (1 << c->K)) return SR_ERR_INVALID;
   if (halvings_to_coarsest(c->n >> c->K, c->n_coarse) < 0) return SR_ERR_UNSUPPORTED_SIZE;
   const long long nseg1 = c->n / c->seg;
-  if (nseg1 * nseg1 * nseg1 > 65535) return SR_ERR_UNSUPPORTED_SIZE;
+  if (nseg1 * nseg1 * nseg1 * len[0] * len[1] * len[2] > 65535) return SR_ERR_UNSUPPORTED_SIZE;
   int J[SR_FMG_MAXK];
   schedule(*c, J);
   for (int k = 1; k <= c->K; ++k) {
@@ -232,10 +283,10 @@ int check_config(const sr_fmg_config* c) {
   return SR_OK;
 }
 
-Cheb chebyshev(int nu, double lo_frac, double hi_frac) {
+Cheb chebyshev(int nu, double lo_frac, double hi_frac, double lmax) {
   Cheb c;
   c.nu = nu;
-  const double lo = 2.0 * lo_frac, hi = 2.0 * hi_frac;
+  const double lo = lmax * lo_frac, hi = lmax * hi_frac;
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
   // three-term recurrence: d_0 = r_0/theta, d_m = rho_m rho_{m-1} d_{m-1} + (2 rho_m/delta) r_m
   double rho_old = delta / theta;
@@ -251,13 +302,15 @@ Cheb chebyshev(int nu, double lo_frac, double hi_frac) {
     }
   }
   if (nu == 2) {
-    // x2 = x0 + c1 r0 + c2 B r0 with B r0 = r0 - (sum of neighbours of r0)/6
+    // x2 = x0 + c1 r0 + c2 B r0 with B r0 = D^-1 A r0 = r0 - W r0, W the
+    // neighbour part (7-point: the sum of the 6 neighbours of r0 over 6)
     const double r0 = delta / theta;
     const double r1 = 1.0 / (2.0 * theta / delta - r0);
     const double c1 = (1.0 + r1 * r0) / theta + 2.0 * r1 / delta;
     const double c2 = -2.0 * r1 / (delta * theta);
     c.a = c1 + c2;
     c.b = -c2 / 6.0;
+    c.c2 = c2;
   }
   return c;
 }
@@ -278,21 +331,29 @@ int dalloc(sr_fmg_s* h, T** p, size_t count) {
   return SR_OK;
 }
 
-BoxDesc whole_box(int n) {
+BoxDesc whole_box(const int nd[3]) {
   BoxDesc b;
   std::memset(&b, 0, sizeof(b));
   for (int d = 0; d < 3; ++d) {
-    b.lo[d] = 0; b.hi[d] = n;
-    b.plo[d] = 0; b.phi[d] = n;
-    b.rlo[d] = 0; b.rhi[d] = n / 2;
-    b.glo[d] = 0; b.ghi[d] = n;
+    b.lo[d] = 0; b.hi[d] = nd[d];
+    b.plo[d] = 0; b.phi[d] = nd[d];
+    b.rlo[d] = 0; b.rhi[d] = nd[d] / 2;
+    b.glo[d] = 0; b.ghi[d] = nd[d];
   }
   b.ox = b.oy = b.oz = 0;
-  b.sy = n;
-  b.sz = (long long)n * n;
+  b.sy = nd[0];
+  b.sz = (long long)nd[0] * nd[1];
   b.base = 0;
   return b;
 }
+
+void set_dims(Geom& L, int n, const int len[3]) {
+  L.n = n;
+  for (int d = 0; d < 3; ++d) L.nd[d] = n * len[d];
+}
+
+long long cells_of(const Geom& L) { return (long long)L.nd[0] * L.nd[1] * L.nd[2]; }
+Dims dims_of(const Geom& L) { return Dims{L.nd[0], L.nd[1], L.nd[2]}; }
 
 long long prod(const int lo[3], const int hi[3]) {
   return (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
@@ -304,7 +365,7 @@ int finish_level(sr_fmg_s* h, Geom& L) {
   if (rc) return rc;
   CK(cudaMemcpy(L.dboxes, L.hboxes.data(), sizeof(BoxDesc) * L.hboxes.size(),
                 cudaMemcpyHostToDevice));
-  BoxDesc g = whole_box(L.n);
+  BoxDesc g = whole_box(L.nd);
   rc = dalloc(h, &L.dglobal, 1);
   if (rc) return rc;
   CK(cudaMemcpy(L.dglobal, &g, sizeof(BoxDesc), cudaMemcpyHostToDevice));
@@ -312,6 +373,9 @@ int finish_level(sr_fmg_s* h, Geom& L) {
   v.boxes = L.dboxes;
   v.nbox = L.nbox;
   v.n = L.n;
+  v.nx = L.nd[0];
+  v.ny = L.nd[1];
+  v.nz = L.nd[2];
   for (const BoxDesc& b : L.hboxes) {
     const int slo[3] = {b.ox, b.oy, b.oz};
     int shi[3];
@@ -335,34 +399,45 @@ int finish_level(sr_fmg_s* h, Geom& L) {
   return SR_OK;
 }
 
-// dense inverse of the coarsest operator from its eigen-decomposition: the
-// 1D factors sin(k pi (i + 1/2) / n), k = 1..n, are orthogonal with squared
-// norms n/2 (k < n) and n (k = n), eigenvalues 4 n^2 sin^2(k pi / 2n).
-std::vector<double> coarsest_inverse(int n) {
-  const int m = n * n * n;
-  std::vector<double> phi((size_t)n * n), lam(n);
+// dense inverse of the coarsest operator from its eigen-decomposition: on
+// each axis of N cells the factors sin(k pi (i + 1/2) / N), k = 1..N, are
+// orthogonal with squared norms N/2 (k < N) and N (k = N); the operator's
+// eigenvalue on their product is n^2 (w0 - 2 w1 sum c_d - 4 w2 sum c_d c_e
+// - 8 w3 c_0 c_1 c_2), c_d = cos(k_d pi / N_d) (7-point: w = (6, 1, 0, 0)).
+std::vector<double> coarsest_inverse(const int nd[3], int n, const W27& w) {
+  const int m = nd[0] * nd[1] * nd[2];
   const double pi = 3.14159265358979323846;
-  for (int k = 1; k <= n; ++k) {
-    const double norm = std::sqrt((k < n) ? 2.0 / n : 1.0 / n);
-    for (int i = 0; i < n; ++i) phi[(size_t)(k - 1) * n + i] = norm * std::sin(pi * k * (i + 0.5) / n);
-    const double s = std::sin(pi * k / (2.0 * n));
-    lam[k - 1] = 4.0 * n * n * s * s;
+  std::vector<double> phi[3], cs[3];
+  for (int d = 0; d < 3; ++d) {
+    const int N = nd[d];
+    phi[d].assign((size_t)N * N, 0.0);
+    cs[d].assign(N, 0.0);
+    for (int k = 1; k <= N; ++k) {
+      const double norm = std::sqrt((k < N) ? 2.0 / N : 1.0 / N);
+      for (int i = 0; i < N; ++i)
+        phi[d][(size_t)(k - 1) * N + i] = norm * std::sin(pi * k * (i + 0.5) / N);
+      cs[d][k - 1] = std::cos(pi * k / N);
+    }
   }
-  std::vector<double> minv((size_t)m * m, 0.0);
-  for (int k3 = 0; k3 < n; ++k3)
-    for (int k2 = 0; k2 < n; ++k2)
-      for (int k1 = 0; k1 < n; ++k1) {
-        const double il = 1.0 / (lam[k1] + lam[k2] + lam[k3]);
-        std::vector<double> v(m);
-        for (int z = 0; z < n; ++z)
-          for (int y = 0; y < n; ++y)
-            for (int x = 0; x < n; ++x)
-              v[(z * n + y) * n + x] = phi[(size_t)k1 * n + x] * phi[(size_t)k2 * n + y] *
-                                       phi[(size_t)k3 * n + z];
+  const double n2 = (double)n * n;
+  std::vector<double> minv((size_t)m * m, 0.0), v(m);
+  for (int k3 = 0; k3 < nd[2]; ++k3)
+    for (int k2 = 0; k2 < nd[1]; ++k2)
+      for (int k1 = 0; k1 < nd[0]; ++k1) {
+        const double x = cs[0][k1], y = cs[1][k2], z = cs[2][k3];
+        const double lam = n2 * (w.w0 - 2.0 * w.w1 * (x + y + z) -
+                                 4.0 * w.w2 * (x * y + x * z + y * z) - 8.0 * w.w3 * x * y * z);
+        const double il = 1.0 / lam;
+        for (int zz = 0; zz < nd[2]; ++zz)
+          for (int yy = 0; yy < nd[1]; ++yy)
+            for (int xx = 0; xx < nd[0]; ++xx)
+              v[((size_t)zz * nd[1] + yy) * nd[0] + xx] =
+                  phi[0][(size_t)k1 * nd[0] + xx] * phi[1][(size_t)k2 * nd[1] + yy] *
+                  phi[2][(size_t)k3 * nd[2] + zz];
         for (int p = 0; p < m; ++p) {
-          const double w = il * v[p];
+          const double wv = il * v[p];
           double* row = &minv[(size_t)p * m];
-          for (int q = 0; q < m; ++q) row[q] += w * v[q];
+          for (int q = 0; q < m; ++q) row[q] += wv * v[q];
         }
       }
   return minv;
@@ -380,12 +455,12 @@ int build_global_levels(sr_fmg_s* h, Hier<T>& H, int ntop, bool top_user) {
   const bool sr = h->K > 0;
   for (int g = 0; g < h->G; ++g) {
     Level<T>& L = H.glev[g];
-    L.n = ntop >> (h->G - 1 - g);
-    L.hboxes.assign(1, whole_box(L.n));
+    set_dims(L, ntop >> (h->G - 1 - g), h->len);
+    L.hboxes.assign(1, whole_box(L.nd));
     if (g == 0) for (int d = 0; d < 3; ++d) { L.hboxes[0].rlo[d] = 0; L.hboxes[0].rhi[d] = 0; }
     int rc = finish_level(h, L);
     if (rc) return rc;
-    const size_t cells = (size_t)L.n * L.n * L.n;
+    const size_t cells = (size_t)cells_of(L);
     const bool finest = (g == h->G - 1) && !sr;
     if ((rc = dalloc(h, &L.r, cells))) return rc;
     if (need_d && (rc = dalloc(h, &L.d, cells))) return rc;
@@ -397,8 +472,7 @@ int build_global_levels(sr_fmg_s* h, Hier<T>& H, int ntop, bool top_user) {
     if ((rc = dalloc(h, &L.f, cells))) return rc;
   }
   if (!h->minv) {
-    const int nc = H.glev[0].n;
-    std::vector<double> minv = coarsest_inverse(nc);
+    std::vector<double> minv = coarsest_inverse(H.glev[0].nd, H.glev[0].n, h->w27);
     int rc = dalloc(h, &h->minv, minv.size());
     if (rc) return rc;
     CK(cudaMemcpy(h->minv, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -412,29 +486,31 @@ int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
   const int K = h->K;
   int J[SR_FMG_MAXK];
   schedule(c, J);
-  const int nseg1 = c.n / c.seg;
+  int nsd[3];
+  for (int d = 0; d < 3; ++d) nsd[d] = c.n * h->len[d] / c.seg;  // segments per dimension
   const bool need_d = c.alpha > 2 || c.nu1 > 2 || c.nu2 > 2;
   H.slev.resize(K + 1);
   for (int k = 1; k <= K; ++k) {
     Level<T>& L = H.slev[k];
-    L.n = c.n >> (K - k);
+    set_dims(L, c.n >> (K - k), h->len);
     const int sk = c.seg >> (K - k);
     const int s0 = c.seg >> K;
     std::vector<BoxDesc> boxes;
     long long slot = 0;
-    for (int pz = 0; pz < nseg1; ++pz)
-      for (int py = 0; py < nseg1; ++py)
-        for (int px = 0; px < nseg1; ++px) {
+    for (int pz = 0; pz < nsd[2]; ++pz)
+      for (int py = 0; py < nsd[1]; ++py)
+        for (int px = 0; px < nsd[0]; ++px) {
           const int q[3] = {px, py, pz};
           BoxDesc b;
           std::memset(&b, 0, sizeof(b));
           for (int d = 0; d < 3; ++d) {
             b.glo[d] = q[d] * sk;
             b.ghi[d] = (q[d] + 1) * sk;
+            const int nd = L.nd[d];
             b.lo[d] = b.glo[d] - J[k - 1] < 0 ? 0 : b.glo[d] - J[k - 1];
-            b.hi[d] = b.ghi[d] + J[k - 1] > L.n ? L.n : b.ghi[d] + J[k - 1];
+            b.hi[d] = b.ghi[d] + J[k - 1] > nd ? nd : b.ghi[d] + J[k - 1];
             b.plo[d] = b.lo[d] > 0 ? b.lo[d] - 1 : 0;
-            b.phi[d] = b.hi[d] < L.n ? b.hi[d] + 1 : L.n;
+            b.phi[d] = b.hi[d] < nd ? b.hi[d] + 1 : nd;
             if (k > 1) {  // Omega^F on level k-1: the cells under the compute region
               b.rlo[d] = b.lo[d] / 2;
               b.rhi[d] = b.hi[d] / 2;
@@ -467,7 +543,7 @@ int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
       if ((rc = dalloc(h, &L.t, elems))) return rc;
       if ((rc = dalloc(h, &L.rhs, elems))) return rc;
       if ((rc = dalloc(h, &L.rho, elems))) return rc;
-      if ((rc = dalloc(h, &L.f, (size_t)L.n * L.n * L.n))) return rc;
+      if ((rc = dalloc(h, &L.f, (size_t)cells_of(L)))) return rc;
     }
   }
   return SR_OK;
@@ -483,21 +559,71 @@ FieldT<T> view_boxes(const Geom& L, const T* p) { return FieldT<T>{p, L.dboxes, 
 
 // algorithmic per-cell counts (floating-point operations; bytes with each
 // array element read or written once) of each kernel
+// The operator-dependent launches: the 7-point kernels, or the 27-point ones
+// (float64 only) when the handle's stencil is 27.
+template <typename T>
+cudaError_t op_cheb_residual(const sr_fmg_s* h, const LevelView& L, const T* u, T* r,
+                             FieldT<T> f, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->op27) return launch27_cheb_residual(L, u, r, f, h->w27, s);
+  }
+  return launch_cheb_residual<T>(L, u, r, f, s);
+}
+template <typename T>
+cudaError_t op_cheb2_update(const sr_fmg_s* h, const LevelView& L, T* u, const T* r,
+                            const Cheb& c, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->op27) return launch27_cheb2_update(L, u, r, c.a, c.c2, h->w27, s);
+  }
+  return launch_cheb2_update<T>(L, u, r, c.a, c.b, s);
+}
+template <typename T>
+cudaError_t op_resid_restrict(const sr_fmg_s* h, const LevelView& F, const T* u, FieldT<T> f,
+                              const LevelView& C, T* uhat, T* rho, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->op27) return launch27_resid_restrict(F, u, f, C, uhat, rho, h->w27, s);
+  }
+  return launch_resid_restrict<T>(F, u, f, C, uhat, rho, s);
+}
+template <typename T>
+cudaError_t op_coarse_rhs(const sr_fmg_s* h, const LevelView& C, const LevelView& F, const T* u,
+                          const T* rho, T* rhs, T* t, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->op27) return launch27_coarse_rhs(C, F, u, rho, rhs, t, h->w27, s);
+  }
+  return launch_coarse_rhs<T>(C, F, u, rho, rhs, t, s);
+}
+template <typename T>
+cudaError_t op_transition_rhs(const sr_fmg_s* h, const LevelView& C, const T* t, const T* rho,
+                              T* u, T* rhs, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->op27) return launch27_transition_rhs(C, t, rho, u, rhs, h->w27, s);
+  }
+  return launch_transition_rhs<T>(C, t, rho, u, rhs, s);
+}
+
+// algorithmic floating-point operations per unit of the operator kernels
+// (7-point / 27-point): smoother passes per cell, residual + restriction per
+// coarse cell, coarse right-hand side per cell
+double ops_smooth(const sr_fmg_s* h) { return h->op27 ? 30 : 7; }
+double ops_restrict(const sr_fmg_s* h) { return h->op27 ? 258 : 42; }
+double ops_rhs(const sr_fmg_s* h) { return h->op27 ? 31 : 7; }
+
 template <typename T>
 int smooth(sr_fmg_s* h, const Level<T>& L, const Cheb& c, T* u, FieldT<T> f, cudaStream_t s) {
   if (c.nu == 0) return SR_OK;
   const double cells = L.tot_cells;
   const double w = sizeof(T);
   if (c.nu == 2) {
-    LAUNCH(h, kind_of<T>(kChebResidual), cells, 7, 3 * w, s,
-           launch_cheb_residual<T>(L.view, u, L.r, f, s));
-    LAUNCH(h, kind_of<T>(kCheb2Update), cells, 7, 3 * w, s,
-           launch_cheb2_update<T>(L.view, u, L.r, c.a, c.b, s));
+    LAUNCH(h, kind_of<T>(kChebResidual), cells, ops_smooth(h), 3 * w, s,
+           op_cheb_residual<T>(h, L.view, u, L.r, f, s));
+    LAUNCH(h, kind_of<T>(kCheb2Update), cells, ops_smooth(h), 3 * w, s,
+           op_cheb2_update<T>(h, L.view, u, L.r, c, s));
     return SR_OK;
   }
   for (int m = 0; m < c.nu; ++m) {
-    LAUNCH(h, kind_of<T>(kChebResidual), cells, 7, 3 * w, s,
-           launch_cheb_residual<T>(L.view, u, L.r, f, s));
+    LAUNCH(h, kind_of<T>(kChebResidual), cells, ops_smooth(h), 3 * w, s,
+           op_cheb_residual<T>(h, L.view, u, L.r, f, s));
     const int write_d = (c.nu > 1 && m < c.nu - 1) ? 1 : 0;
     const bool with_d = write_d || c.alpha[m] != 0.0;
     LAUNCH(h, kind_of<T>(kChebStep), cells, with_d ? 3 : 2, (with_d ? 5 : 3) * w, s,
@@ -521,10 +647,10 @@ int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStrea
   Level<T>& C = H.glev[g - 1];
   int rc = smooth(h, L, h->pre, u, rhs, s);
   if (rc) return rc;
-  LAUNCH(h, kind_of<T>(kResidRestrict), L.tot_restrict, 42, 18 * w, s,
-         launch_resid_restrict<T>(L.view, u, rhs, C.view, C.u, C.rho, s));
-  LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, 7, 4 * w, s,
-         launch_coarse_rhs<T>(C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
+  LAUNCH(h, kind_of<T>(kResidRestrict), L.tot_restrict, ops_restrict(h), 18 * w, s,
+         op_resid_restrict<T>(h, L.view, u, rhs, C.view, C.u, C.rho, s));
+  LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h), 4 * w, s,
+         op_coarse_rhs<T>(h, C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
   rc = vcycle_global(h, H, g - 1, C.u, view_global<T>(C, C.rhs), s);
   if (rc) return rc;
   LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
@@ -566,23 +692,23 @@ int run_fmg_global(sr_fmg_s* h, Hier<T>& H, const T* ftop, T* utop, cudaStream_t
 template <typename T>
 int f_hierarchy(sr_fmg_s* h, Hier<T>& H, const T* f, int check, cudaStream_t s) {
   const T* src = f;
-  int nsrc = h->cfg.n;
+  Dims dsrc{h->cfg.n * h->len[0], h->cfg.n * h->len[1], h->cfg.n * h->len[2]};
   const double w = sizeof(T);
   for (int k = h->K - 1; k >= 1; --k) {
-    const double nc = H.slev[k].n;
-    LAUNCH(h, kind_of<T>(kRestrictF), nc * nc * nc, 8, 9 * w, s,
-           launch_restrict_global<T>(nsrc, src, H.slev[k].f, check, h->status, s));
+    const double cells = (double)cells_of(H.slev[k]);
+    LAUNCH(h, kind_of<T>(kRestrictF), cells, 8, 9 * w, s,
+           launch_restrict_global<T>(dsrc, src, H.slev[k].f, check, h->status, s));
     check = 0;
     src = H.slev[k].f;
-    nsrc = H.slev[k].n;
+    dsrc = dims_of(H.slev[k]);
   }
   for (int g = h->G - (h->K ? 1 : 2); g >= 0; --g) {
-    const double nc = H.glev[g].n;
-    LAUNCH(h, kind_of<T>(kRestrictF), nc * nc * nc, 8, 9 * w, s,
-           launch_restrict_global<T>(nsrc, src, H.glev[g].f, check, h->status, s));
+    const double cells = (double)cells_of(H.glev[g]);
+    LAUNCH(h, kind_of<T>(kRestrictF), cells, 8, 9 * w, s,
+           launch_restrict_global<T>(dsrc, src, H.glev[g].f, check, h->status, s));
     check = 0;
     src = H.glev[g].f;
-    nsrc = H.glev[g].n;
+    dsrc = dims_of(H.glev[g]);
   }
   return SR_OK;
 }
@@ -615,18 +741,18 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
       if (rc) return rc;
       if (j > 1) {
         Level<T>& C = H.slev[j - 1];
-        LAUNCH(h, kind_of<T>(kResidRestrict), Lj.tot_restrict, 42, 18 * w, s,
-               launch_resid_restrict<T>(Lj.view, Lj.u, rhs, C.view, C.u, C.rho, s));
-        LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, 7, 4 * w, s,
-               launch_coarse_rhs<T>(C.view, Lj.view, C.u, C.rho, C.rhs, C.t, s));
+        LAUNCH(h, kind_of<T>(kResidRestrict), Lj.tot_restrict, ops_restrict(h), 18 * w, s,
+               op_resid_restrict<T>(h, Lj.view, Lj.u, rhs, C.view, C.u, C.rho, s));
+        LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h), 4 * w, s,
+               op_coarse_rhs<T>(h, C.view, Lj.view, C.u, C.rho, C.rhs, C.t, s));
       } else {
-        LAUNCH(h, kind_of<T>(kResidRestrict), Lj.tot_restrict, 42, 18 * w, s,
-               launch_resid_restrict<T>(Lj.view, Lj.u, rhs, L0.view, L0.t, L0.rho, s));
+        LAUNCH(h, kind_of<T>(kResidRestrict), Lj.tot_restrict, ops_restrict(h), 18 * w, s,
+               op_resid_restrict<T>(h, Lj.view, Lj.u, rhs, L0.view, L0.t, L0.rho, s));
       }
     }
     // transition level: u_0 <- \hat I u_1, t_0 = u_0, r_0 = rho_0 + L_0 u_0, FASMGV
-    LAUNCH(h, kind_of<T>(kTransitionRhs), L0.tot_cells, 7, 4 * w, s,
-           launch_transition_rhs<T>(L0.view, L0.t, L0.rho, L0.u, L0.rhs, s));
+    LAUNCH(h, kind_of<T>(kTransitionRhs), L0.tot_cells, ops_rhs(h), 4 * w, s,
+           op_transition_rhs<T>(h, L0.view, L0.t, L0.rho, L0.u, L0.rhs, s));
     int rc = vcycle_global(h, H, h->G - 1, L0.u, view_global<T>(L0, L0.rhs), s);
     if (rc) return rc;
     // up-leg
@@ -661,7 +787,7 @@ int solve_once(sr_fmg_s* h, const T* f, double* out, int add, int check, cudaStr
   if (rc) return rc;
   if (h->K) return run_sr<T>(h, H, f, out, add, s);
   if (!user_top) {
-    const long long cells = (long long)h->cfg.n * h->cfg.n * h->cfg.n;
+    const long long cells = cells_of(H.glev[h->G - 1]);
     LAUNCH(h, kAccumulate, (double)cells, add ? 1 : 0, add ? 20 : 12, s,
            launch_accumulate(cells, reinterpret_cast<const float*>(utop), out, add, s));
   }
@@ -674,11 +800,12 @@ int enqueue_solve(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
   if (!h->mixed) return solve_once<double>(h, f, u, 0, 1, s);
   // float64 defect correction around the float32 solve
   const int n = h->cfg.n;
-  const double cells = (double)n * n * n;
+  const Dims g{n * h->len[0], n * h->len[1], n * h->len[2]};
+  const double cells = (double)g.x * g.y * g.z;
   const int passes = h->cfg.n_outer > 0 ? h->cfg.n_outer : 2;
   for (int p = 1; p <= passes; ++p) {
     LAUNCH(h, kDefect, cells, p == 1 ? 0 : 7, p == 1 ? 12 : 20, s,
-           launch_defect(n, f, p == 1 ? nullptr : u, h->defect, h->status, s));
+           launch_defect(g, n, f, p == 1 ? nullptr : u, h->defect, h->status, s));
     int rc = solve_once<float>(h, h->defect, u, p > 1 ? 1 : 0, 0, s);
     if (rc) return rc;
   }
@@ -741,7 +868,9 @@ int srfmg::enqueue_solve_unchecked(sr_fmg_s* h, const double* f, double* u, cuda
   return enqueue_solve(h, f, u, s);
 }
 
-int srfmg::handle_n(const sr_fmg_s* h) { return h->cfg.n; }
+long long srfmg::handle_cells(const sr_fmg_s* h) {
+  return (long long)h->cfg.n * h->cfg.n * h->cfg.n * h->len[0] * h->len[1] * h->len[2];
+}
 
 extern "C" {
 
@@ -783,15 +912,18 @@ int sr_fmg_create(sr_fmg_t* out, const sr_fmg_config* cfg) {
   }
   h->mixed = cfg->precision == SR_MIXED;
   h->K = (cfg->seg > 0) ? cfg->K : 0;
-  h->pre = chebyshev(cfg->nu1, cfg->cheb_lo, cfg->cheb_hi);
-  h->post = chebyshev(cfg->nu2, cfg->cheb_lo, cfg->cheb_hi);
-  h->fmg = chebyshev(cfg->alpha, cfg->cheb_lo, cfg->cheb_hi);
+  lengths_of(cfg, h->len);
+  op_weights(cfg, &h->w27, &h->lmax);
+  h->op27 = cfg->stencil == 27;
+  h->pre = chebyshev(cfg->nu1, cfg->cheb_lo, cfg->cheb_hi, h->lmax);
+  h->post = chebyshev(cfg->nu2, cfg->cheb_lo, cfg->cheb_hi, h->lmax);
+  h->fmg = chebyshev(cfg->alpha, cfg->cheb_lo, cfg->cheb_hi, h->lmax);
   rc = dalloc(h, &h->status, 1);
   if (!h->mixed) {
     if (!rc) rc = build_global_levels<double>(h, h->h64, cfg->n >> h->K, h->K == 0);
     if (!rc && h->K) rc = build_sr_levels<double>(h, h->h64);
   } else {
-    const size_t cells = (size_t)cfg->n * cfg->n * cfg->n;
+    const size_t cells = (size_t)srfmg::handle_cells(h);
     if (!rc) rc = dalloc(h, &h->defect, cells);
     if (!rc) rc = build_global_levels<float>(h, h->h32, cfg->n >> h->K, false);
     if (!rc && h->K) rc = build_sr_levels<float>(h, h->h32);
@@ -821,10 +953,9 @@ int sr_fmg_workspace_bytes(sr_fmg_t h, size_t* bytes) {
 
 int sr_fmg_solve_async(sr_fmg_t h, const double* f_dev, double* u_dev, void* stream) {
   if (!h || !f_dev || !u_dev) return SR_ERR_INVALID;
-  const size_t n = (size_t)h->cfg.n;
   const char* fa = (const char*)f_dev;
   const char* ua = (const char*)u_dev;
-  const size_t bytes = n * n * n * sizeof(double);
+  const size_t bytes = (size_t)srfmg::handle_cells(h) * sizeof(double);
   if (fa < ua + bytes && ua < fa + bytes) return SR_ERR_INVALID;
   if (!is_device_ptr(f_dev) || !is_device_ptr(u_dev)) return SR_ERR_INVALID;
   DeviceGuard g(h->device);
@@ -851,11 +982,11 @@ int sr_fmg_solve(sr_fmg_t h, const double* f_dev, double* u_dev, void* stream) {
 int sr_fmg_solve_host(sr_fmg_t h, const double* f_host, double* u_host, void* stream) {
   if (!h || !f_host || !u_host) return SR_ERR_INVALID;
   DeviceGuard g(h->device);
-  const size_t n = (size_t)h->cfg.n;
-  const size_t bytes = n * n * n * sizeof(double);
+  const size_t cells = (size_t)srfmg::handle_cells(h);
+  const size_t bytes = cells * sizeof(double);
   if (!h->hbuf_f) {
-    int rc = dalloc(h, &h->hbuf_f, n * n * n);
-    if (!rc) rc = dalloc(h, &h->hbuf_u, n * n * n);
+    int rc = dalloc(h, &h->hbuf_f, cells);
+    if (!rc) rc = dalloc(h, &h->hbuf_u, cells);
     if (rc) return rc;
   }
   cudaStream_t s = (cudaStream_t)stream;
@@ -871,7 +1002,7 @@ int sr_fmg_vsolve(sr_fmg_t h, const double* f_dev, double* u_dev, double rtol, i
   if (!h || !f_dev || !u_dev || !cycles || !rel_resid) return SR_ERR_INVALID;
   if (h->K || h->mixed || !(rtol >= 0.0) || max_cycles < 0) return SR_ERR_INVALID;
   const int n = h->cfg.n;
-  const size_t bytes = (size_t)n * n * n * sizeof(double);
+  const size_t bytes = (size_t)srfmg::handle_cells(h) * sizeof(double);
   const char* fa = (const char*)f_dev;
   const char* ua = (const char*)u_dev;
   if (fa < ua + bytes && ua < fa + bytes) return SR_ERR_INVALID;
@@ -882,17 +1013,23 @@ int sr_fmg_vsolve(sr_fmg_t h, const double* f_dev, double* u_dev, double rtol, i
     if (rc) return rc;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const double cells = (double)n * n * n;
   const int top = h->G - 1;
   Hier<double>& H = h->h64;
+  const double cells = (double)cells_of(H.glev[top]);
   *cycles = 0;
   h->launches = 0;
   // one norm into slot k (u == nullptr: ||f||), read back on the host
   auto norm = [&](const double* u, int k, double* out) -> int {
     CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned int), s));
     CK(cudaMemsetAsync(h->norms + k, 0, sizeof(unsigned long long), s));
-    LAUNCH(h, kResidNorm, cells, u ? 7 : 0, u ? 16 : 8, s,
-           launch_resid_norm(n, f_dev, u, h->norms + k, h->status, s));
+    if (h->op27) {
+      LAUNCH(h, kResidNorm, cells, u ? ops_rhs(h) : 0, u ? 16 : 8, s,
+             launch27_resid_norm(H.glev[top].view, f_dev, u, h->norms + k, h->status, h->w27,
+                                 s));
+    } else {
+      LAUNCH(h, kResidNorm, cells, u ? 7 : 0, u ? 16 : 8, s,
+             launch_resid_norm(dims_of(H.glev[top]), n, f_dev, u, h->norms + k, h->status, s));
+    }
     unsigned long long bits = 0;
     unsigned int st = 0;
     CK(cudaMemcpyAsync(&bits, h->norms + k, sizeof(bits), cudaMemcpyDeviceToHost, s));
@@ -981,81 +1118,97 @@ struct TmpLevel {
   ~TmpLevel() { free_all(&h); }
 };
 
-int tmp_level(TmpLevel& T, int n) {
-  T.L.n = n;
-  T.L.hboxes.assign(1, whole_box(n));
+// a handle shell carrying cfg's domain and operator, and one whole level of
+// n cells per unit length
+int tmp_level(TmpLevel& T, const sr_fmg_config& c, int n) {
+  if (lengths_of(&c, T.h.len) || op_weights(&c, &T.h.w27, &T.h.lmax)) return SR_ERR_INVALID;
+  T.h.op27 = c.stencil == 27;
+  set_dims(T.L, n, T.h.len);
+  T.L.hboxes.assign(1, whole_box(T.L.nd));
   return finish_level(&T.h, T.L);
 }
 
 bool dev_ok(const void* p) { return p && is_device_ptr(p); }
 
+sr_fmg_config cube7(int n) {
+  sr_fmg_config c;
+  sr_fmg_default_config(&c, n);
+  return c;
+}
+
 }  // namespace
 
-int sr_op_apply(int n, const double* u, double* out, void* stream) {
-  if (n < 1 || !dev_ok(u) || !dev_ok(out)) return SR_ERR_INVALID;
+int sr_op_apply_ex(const sr_fmg_config* cfg, const double* u, double* out, void* stream) {
+  if (!cfg || cfg->n < 1 || !dev_ok(u) || !dev_ok(out)) return SR_ERR_INVALID;
   TmpLevel T;
-  int rc = tmp_level(T, n);
+  int rc = tmp_level(T, *cfg, cfg->n);
   if (rc) return rc;
-  CK(launch_apply<double>(T.L.view, u, out, (cudaStream_t)stream));
-  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(T.h.op27 ? launch27_apply(T.L.view, u, out, T.h.w27, s)
+              : launch_apply<double>(T.L.view, u, out, s));
+  CK(cudaStreamSynchronize(s));
   return SR_OK;
 }
 
-int sr_op_residual(int n, const double* f, const double* u, double* r, void* stream) {
-  if (n < 1 || !dev_ok(f) || !dev_ok(u) || !dev_ok(r)) return SR_ERR_INVALID;
+int sr_op_residual_ex(const sr_fmg_config* cfg, const double* f, const double* u, double* r,
+                      void* stream) {
+  if (!cfg || cfg->n < 1 || !dev_ok(f) || !dev_ok(u) || !dev_ok(r)) return SR_ERR_INVALID;
   TmpLevel T;
-  int rc = tmp_level(T, n);
+  int rc = tmp_level(T, *cfg, cfg->n);
   if (rc) return rc;
-  CK(launch_residual<double>(T.L.view, u, view_global<double>(T.L, f), r,
-                             (cudaStream_t)stream));
-  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  const FieldT<double> fv = view_global<double>(T.L, f);
+  CK(T.h.op27 ? launch27_residual(T.L.view, u, fv, r, T.h.w27, s)
+              : launch_residual<double>(T.L.view, u, fv, r, s));
+  CK(cudaStreamSynchronize(s));
   return SR_OK;
 }
 
-int sr_op_smooth(int n, int nu, double cheb_lo, double cheb_hi, const double* f, double* u,
-                 void* stream) {
-  if (n < 1 || nu < 0 || nu > 16 || !dev_ok(f) || !dev_ok(u)) return SR_ERR_INVALID;
-  if (!(cheb_lo > 0.0 && cheb_hi > cheb_lo)) return SR_ERR_INVALID;
+int sr_op_smooth_ex(const sr_fmg_config* cfg, int nu, const double* f, double* u, void* stream) {
+  if (!cfg || cfg->n < 1 || nu < 0 || nu > 16 || !dev_ok(f) || !dev_ok(u)) return SR_ERR_INVALID;
+  if (!(cfg->cheb_lo > 0.0 && cfg->cheb_hi > cfg->cheb_lo)) return SR_ERR_INVALID;
   TmpLevel T;
-  int rc = tmp_level(T, n);
-  const size_t cells = (size_t)n * n * n;
+  int rc = tmp_level(T, *cfg, cfg->n);
+  const size_t cells = (size_t)cells_of(T.L);
   if (!rc) rc = dalloc(&T.h, &T.L.r, cells);
   if (!rc) rc = dalloc(&T.h, &T.L.d, cells);
   if (rc) return rc;
-  Cheb c = chebyshev(nu, cheb_lo, cheb_hi);
+  Cheb c = chebyshev(nu, cfg->cheb_lo, cfg->cheb_hi, T.h.lmax);
   rc = smooth<double>(&T.h, T.L, c, u, view_global<double>(T.L, f), (cudaStream_t)stream);
   if (rc) return rc;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
 }
 
-int sr_op_restrict(int n, const double* a, double* ac, void* stream) {
-  if (n < 2 || n % 2 || !dev_ok(a) || !dev_ok(ac)) return SR_ERR_INVALID;
+int sr_op_restrict_ex(const sr_fmg_config* cfg, const double* a, double* ac, void* stream) {
+  if (!cfg || cfg->n < 2 || cfg->n % 2 || !dev_ok(a) || !dev_ok(ac)) return SR_ERR_INVALID;
   TmpLevel T;
-  int rc = dalloc(&T.h, &T.h.status, 1);
+  int rc = tmp_level(T, *cfg, cfg->n);
+  if (!rc) rc = dalloc(&T.h, &T.h.status, 1);
   if (rc) return rc;
-  CK(launch_restrict_global<double>(n, a, ac, 0, T.h.status, (cudaStream_t)stream));
+  CK(launch_restrict_global<double>(dims_of(T.L), a, ac, 0, T.h.status, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
 }
 
-int sr_op_prolong(int nc, const double* ac, double* af, void* stream) {
-  if (nc < 1 || !dev_ok(ac) || !dev_ok(af)) return SR_ERR_INVALID;
+int sr_op_prolong_ex(const sr_fmg_config* cfg, const double* ac, double* af, void* stream) {
+  if (!cfg || cfg->n < 1 || !dev_ok(ac) || !dev_ok(af)) return SR_ERR_INVALID;
   TmpLevel C, F;
-  int rc = tmp_level(C, nc);
-  if (!rc) rc = tmp_level(F, 2 * nc);
+  int rc = tmp_level(C, *cfg, cfg->n);
+  if (!rc) rc = tmp_level(F, *cfg, 2 * cfg->n);
   if (rc) return rc;
   CK(launch_prolong<double>(C.L.view, ac, F.L.view, af, 0, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
 }
 
-int sr_op_coarse_solve(int n, const double* f, double* u, void* stream) {
-  if (n < 1 || n > 8 || !dev_ok(f) || !dev_ok(u)) return SR_ERR_INVALID;
+int sr_op_coarse_solve_ex(const sr_fmg_config* cfg, const double* f, double* u, void* stream) {
+  if (!cfg || cfg->n < 1 || !dev_ok(f) || !dev_ok(u)) return SR_ERR_INVALID;
   TmpLevel T;
-  int rc = tmp_level(T, n);
+  int rc = tmp_level(T, *cfg, cfg->n);
   if (rc) return rc;
-  std::vector<double> minv = coarsest_inverse(n);
+  if (cells_of(T.L) > 4096) return SR_ERR_UNSUPPORTED_SIZE;
+  std::vector<double> minv = coarsest_inverse(T.L.nd, T.L.n, T.h.w27);
   double* dm = nullptr;
   rc = dalloc(&T.h, &dm, minv.size());
   if (rc) return rc;
@@ -1064,6 +1217,40 @@ int sr_op_coarse_solve(int n, const double* f, double* u, void* stream) {
                                  (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return SR_OK;
+}
+
+int sr_op_apply(int n, const double* u, double* out, void* stream) {
+  const sr_fmg_config c = cube7(n);
+  return sr_op_apply_ex(&c, u, out, stream);
+}
+
+int sr_op_residual(int n, const double* f, const double* u, double* r, void* stream) {
+  const sr_fmg_config c = cube7(n);
+  return sr_op_residual_ex(&c, f, u, r, stream);
+}
+
+int sr_op_smooth(int n, int nu, double cheb_lo, double cheb_hi, const double* f, double* u,
+                 void* stream) {
+  sr_fmg_config c = cube7(n);
+  c.cheb_lo = cheb_lo;
+  c.cheb_hi = cheb_hi;
+  return sr_op_smooth_ex(&c, nu, f, u, stream);
+}
+
+int sr_op_restrict(int n, const double* a, double* ac, void* stream) {
+  const sr_fmg_config c = cube7(n);
+  return sr_op_restrict_ex(&c, a, ac, stream);
+}
+
+int sr_op_prolong(int nc, const double* ac, double* af, void* stream) {
+  const sr_fmg_config c = cube7(nc);
+  return sr_op_prolong_ex(&c, ac, af, stream);
+}
+
+int sr_op_coarse_solve(int n, const double* f, double* u, void* stream) {
+  if (n > 8) return SR_ERR_INVALID;
+  const sr_fmg_config c = cube7(n);
+  return sr_op_coarse_solve_ex(&c, f, u, stream);
 }
 
 int sr_op_vcycle(const sr_fmg_config* cfg, const double* f, double* u, void* stream) {

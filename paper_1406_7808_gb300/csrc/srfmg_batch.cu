@@ -74,8 +74,7 @@ std::vector<std::vector<int>> assign(const sr_fmg_batch_s* b, int streams) {
   std::vector<int> order(b->hs.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
   auto work = [&](int i) {
-    const double n = srfmg::handle_n(b->hs[i]);
-    return n * n * n;
+    return (double)srfmg::handle_cells(b->hs[i]);
   };
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work(a) > work(c); });
   std::vector<std::vector<int>> lanes(streams);
@@ -133,8 +132,7 @@ int validate(const sr_fmg_batch_s* b, const double* const* f, double* const* u) 
   if (!f || !u) return SR_ERR_INVALID;
   for (size_t i = 0; i < b->hs.size(); ++i) {
     if (!device_ptr(f[i]) || !device_ptr(u[i])) return SR_ERR_INVALID;
-    const size_t n = (size_t)srfmg::handle_n(b->hs[i]);
-    const size_t bytes = n * n * n * sizeof(double);
+    const size_t bytes = (size_t)srfmg::handle_cells(b->hs[i]) * sizeof(double);
     const char* fa = (const char*)f[i];
     const char* ua = (const char*)u[i];
     if (fa < ua + bytes && ua < fa + bytes) return SR_ERR_INVALID;

@@ -28,11 +28,19 @@ struct BoxDesc {
   long long base;      // offset of the box's storage in the level arrays
 };
 
-// A level as the kernels see it.
+// Cells per dimension of a whole level grid.
+struct Dims {
+  int x, y, z;
+};
+
+// A level as the kernels see it.  The domain is [0, l0] x [0, l1] x [0, l2]
+// (unit cube by default) with n cells per unit length (h = 1/n); the level
+// grid has nx x ny x nz = n l0 x n l1 x n l2 cells.
 struct LevelView {
   const BoxDesc* boxes;  // device array, nbox entries
   int nbox;
-  int n;                 // cells per dimension of the level grid
+  int n;                 // cells per unit length of the level grid
+  int nx, ny, nz;        // cells per dimension of the level grid
   int max_cells;         // largest compute-region cell count over the boxes
   int max_stored;        // largest stored-region (compute plus shell) cell count
   int max_prolong;       // largest prolongation-range cell count
@@ -105,17 +113,18 @@ cudaError_t launch_prolong(const LevelView& C, const T* uc, const LevelView& F, 
 // coarse-grid correction w - t of the FAS V-cycle).
 template <typename T>
 cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaStream_t s);
-// Coarsest grid: u = Minv f, Minv the dense float64 inverse (m x m, m = n^3);
-// float64 arithmetic.
+// Coarsest grid: u = Minv f, Minv the dense float64 inverse (m x m,
+// m = nx ny nz); float64 arithmetic.
 template <typename T>
 cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldT<T> f, T* u,
                                 cudaStream_t s);
-// f_c = 8-child average of f_f on whole global levels; sets *status |= 1 if
-// an input value is not finite (check != 0).
+// f_c = 8-child average of f_f on whole global levels (fd: the fine grid's
+// cells per dimension); sets *status |= 1 if an input value is not finite
+// (check != 0).
 template <typename T>
-cudaError_t launch_restrict_global(int nf, const T* ff, T* fc, int check, unsigned int* status,
+cudaError_t launch_restrict_global(Dims fd, const T* ff, T* fc, int check, unsigned int* status,
                                    cudaStream_t s);
-// Genuine cells of every box of L into the global n^3 float64 array out:
+// Genuine cells of every box of L into the global float64 array out:
 // out = u (add == 0) or out += u (add == 1).
 template <typename T>
 cudaError_t launch_gather_genuine(const LevelView& L, const T* u, double* out, int add,
@@ -123,24 +132,54 @@ cudaError_t launch_gather_genuine(const LevelView& L, const T* u, double* out, i
 
 // ---- float64 defect correction around the float32 inner solver
 
-// d = float(f - A u) on the whole n^3 grid (float64 arithmetic, unpadded
-// arrays); with u == nullptr, d = float(f).  Sets *status |= 1 if f holds a
-// value that is not finite.
-cudaError_t launch_defect(int n, const double* f, const double* u, float* d,
+// d = float(f - A u) on the whole grid g with n cells per unit length
+// (float64 arithmetic, unpadded arrays); with u == nullptr, d = float(f).
+// Sets *status |= 1 if f holds a value that is not finite.
+cudaError_t launch_defect(Dims g, int n, const double* f, const double* u, float* d,
                           unsigned int* status, cudaStream_t s);
-// *norm = max over the n^3 cells of |f - A u| (float64; |f| when u is null),
-// stored as the bit pattern of the double; *norm must be 0 on entry.  Sets
-// *status |= 1 if a value is not finite.
-cudaError_t launch_resid_norm(int n, const double* f, const double* u, unsigned long long* norm,
-                              unsigned int* status, cudaStream_t s);
-// u = e (add == 0) or u += e (add == 1) on n^3 cells, e float32.
+// *norm = max over the cells of grid g of |f - A u| (float64; |f| when u is
+// null), stored as the bit pattern of the double; *norm must be 0 on entry.
+// Sets *status |= 1 if a value is not finite.
+cudaError_t launch_resid_norm(Dims g, int n, const double* f, const double* u,
+                              unsigned long long* norm, unsigned int* status, cudaStream_t s);
+// u = e (add == 0) or u += e (add == 1) on `cells` cells, e float32.
 cudaError_t launch_accumulate(long long cells, const float* e, double* u, int add,
                               cudaStream_t s);
+
+// ---- the 27-point operator (kernels27.cu; float64 only)
+// A u = n^2 (w0 u - w1 sum_faces - w2 sum_edges - w3 sum_corners)
+struct W27 {
+  double w0, w1, w2, w3;
+};
+
+// r = D^-1 (f - A u), D = w0 n^2, on the compute region.
+cudaError_t launch27_cheb_residual(const LevelView& L, const double* u, double* r,
+                                   FieldT<double> f, W27 w, cudaStream_t s);
+// u += a r - c2 W r with W r = (w1 sf + w2 se + w3 sc)(r) / w0 (the degree-2
+// Chebyshev polynomial; r's shell inside the domain reads as zero).
+cudaError_t launch27_cheb2_update(const LevelView& L, double* u, const double* r, double a,
+                                  double c2, W27 w, cudaStream_t s);
+cudaError_t launch27_apply(const LevelView& L, const double* u, double* out, W27 w,
+                           cudaStream_t s);
+cudaError_t launch27_residual(const LevelView& L, const double* u, FieldT<double> f, double* r,
+                              W27 w, cudaStream_t s);
+cudaError_t launch27_resid_restrict(const LevelView& F, const double* u, FieldT<double> f,
+                                    const LevelView& C, double* uhat_dst, double* rho_dst, W27 w,
+                                    cudaStream_t s);
+cudaError_t launch27_coarse_rhs(const LevelView& C, const LevelView& F, const double* u,
+                                const double* rho, double* rhs, double* t, W27 w,
+                                cudaStream_t s);
+cudaError_t launch27_transition_rhs(const LevelView& C, const double* t, const double* rho,
+                                    double* u, double* rhs, W27 w, cudaStream_t s);
+// max |f - A u| (|f| without u) over the whole unpadded level L (one box)
+cudaError_t launch27_resid_norm(const LevelView& L, const double* f, const double* u,
+                                unsigned long long* norm, unsigned int* status, W27 w,
+                                cudaStream_t s);
 
 // Queue one solve of handle h on stream without validating the pointers
 // (the batch path validates them before stream capture); srfmg_api.cu.
 int enqueue_solve_unchecked(::sr_fmg_s* h, const double* f, double* u, cudaStream_t s);
-// n of the handle's grid
-int handle_n(const ::sr_fmg_s* h);
+// cells of the handle's fine grid
+long long handle_cells(const ::sr_fmg_s* h);
 
 }  // namespace srfmg

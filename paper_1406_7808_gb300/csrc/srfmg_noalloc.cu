@@ -97,6 +97,7 @@ extern "C" int sr_op_smooth_noalloc(int n, int nu, double cheb_lo, double cheb_h
   L.boxes = desc;
   L.nbox = 1;
   L.n = n;
+  L.nx = L.ny = L.nz = n;
   L.max_cells = L.max_stored = L.max_prolong = L.max_genuine = n * n * n;
   L.max_restrict = (n / 2) * (n / 2) * (n / 2);
   L.max_ex = L.max_ey = L.max_ez = n;

@@ -76,3 +76,28 @@ def random_direction(n, rng):
     seed = int(rng.integers(0, 2 ** 31 - 1))
     f, _ = manufactured(n, seed, sigma=1.0, main=False)
     return f
+
+
+# ---------------------------------------------------------------------------
+# The model problem of the paper's experiments (Sec. 5.1): the domain
+# [0, 2] x [0, 1] x [0, 1] with the prescribed solution
+#     u(x) = prod_{i=1..3} (x_i^4 - R_i^2 x_i^2),   R = (2, 1, 1),
+# which vanishes on the whole boundary (x_i = 0 or x_i = R_i).  With
+# g_i(t) = t^4 - R_i^2 t^2 and g_i'' = 12 t^2 - 2 R_i^2, f = -Delta u =
+# -sum_i g_i''(x_i) prod_{j != i} g_j(x_j), evaluated at the cell centres.
+PAPER_LENGTHS = (2, 1, 1)
+PAPER_R = (2.0, 1.0, 1.0)
+
+
+def paper_problem(n, lengths=PAPER_LENGTHS, R=PAPER_R):
+    """(f, u) on the grid with n cells per unit length over [0, l0] x [0, l1] x
+    [0, l2], arrays of shape (n l2, n l1, n l0) indexed [z][y][x]."""
+    xs = [cell_centres(n * int(l)) * int(l) for l in lengths]  # centres in [0, l]
+    g = [t ** 4 - r * r * t ** 2 for t, r in zip(xs, R)]
+    g2 = [12.0 * t ** 2 - 2.0 * r * r for t, r in zip(xs, R)]
+
+    def outer(ax, ay, az):
+        return az[:, None, None] * ay[None, :, None] * ax[None, None, :]
+    u = outer(g[0], g[1], g[2])
+    f = -(outer(g2[0], g[1], g[2]) + outer(g[0], g2[1], g[2]) + outer(g[0], g[1], g2[2]))
+    return f, u

@@ -1,7 +1,8 @@
 """Thin Python binding of the C ABI in include/srfmg.h (ctypes; argument
 marshalling only -- every step of the solve runs in the CUDA library).
 
-Device arrays are torch float64 CUDA tensors of shape (n, n, n), contiguous,
+Device arrays are torch float64 CUDA tensors of shape (n, n, n) -- or
+(n l2, n l1, n l0) on the domain [0, l0] x [0, l1] x [0, l2] -- contiguous,
 index order [z][y][x]; work is queued on torch's current CUDA stream.  The
 library is loaded on first use; a missing or unloadable library raises
 RuntimeError (there is no fallback path).
@@ -53,6 +54,9 @@ class Config(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("n_outer", ctypes.c_int),
         ("mbs", ctypes.c_int),
+        ("len", ctypes.c_int * 3),
+        ("stencil", ctypes.c_int),
+        ("w", ctypes.c_double * 3),
     ]
 
 
@@ -115,6 +119,12 @@ def load():
     lib.sr_op_prolong.argtypes = [ctypes.c_int, _VP, _VP, _VP]
     lib.sr_op_coarse_solve.argtypes = [ctypes.c_int, _VP, _VP, _VP]
     lib.sr_op_vcycle.argtypes = [ctypes.POINTER(Config), _VP, _VP, _VP]
+    PC = ctypes.POINTER(Config)
+    for name in ("sr_op_apply_ex", "sr_op_restrict_ex", "sr_op_prolong_ex",
+                 "sr_op_coarse_solve_ex"):
+        getattr(lib, name).argtypes = [PC, _VP, _VP, _VP]
+    lib.sr_op_residual_ex.argtypes = [PC, _VP, _VP, _VP, _VP]
+    lib.sr_op_smooth_ex.argtypes = [PC, ctypes.c_int, _VP, _VP, _VP]
     _LIB = lib
     return lib
 
@@ -143,9 +153,11 @@ def buffer_schedule(A, B, K):
 
 def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, nu2=2,
                 cheb_lo=1.0 / 6.0, cheb_hi=1.0, precision=SR_FP64, n_outer=2, mixed=False,
-                mbs=False):
-    """sr_fmg_config for an n^3 grid (mixed=True selects SR_MIXED; mbs=True the
-    maximum buffer schedule J_k = 2^(k-1) A)."""
+                mbs=False, lengths=(1, 1, 1), stencil=7, weights=None):
+    """sr_fmg_config with n cells per unit length (mixed=True selects SR_MIXED;
+    mbs=True the maximum buffer schedule J_k = 2^(k-1) A; lengths the domain
+    [0, l0] x [0, l1] x [0, l2]; stencil 7 or 27 with weights (faces, edges,
+    corners))."""
     c = Config()
     load().sr_fmg_default_config(ctypes.byref(c), int(n))
     c.n_coarse, c.seg, c.K, c.A, c.B = n_coarse, seg, K, A, B
@@ -159,7 +171,35 @@ def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, 
     c.cheb_lo, c.cheb_hi = cheb_lo, cheb_hi
     c.precision, c.n_outer = (SR_MIXED if mixed else precision), n_outer
     c.mbs = int(bool(mbs))
+    for d in range(3):
+        c.len[d] = int(lengths[d])
+    c.stencil = int(stencil)
+    if weights is None and int(stencil) == 27:
+        weights = W27_DEFAULT
+    if weights is not None:
+        for d in range(3):
+            c.w[d] = float(weights[d])
     return c
+
+
+# the 27-point reading used when no weights are given: (14, 3, 1)/30 for the
+# face, edge and corner neighbours (centre 128/30)
+W27_DEFAULT = (14.0 / 30.0, 3.0 / 30.0, 1.0 / 30.0)
+
+
+def grid_shape(n, lengths=(1, 1, 1)):
+    """Array shape (z, y, x) of the grid with n cells per unit length."""
+    return (n * int(lengths[2]), n * int(lengths[1]), n * int(lengths[0]))
+
+
+GEO_KEYS = ("lengths", "stencil", "weights")
+
+
+def _per_unit(t, lengths):
+    n = t.shape[2] // int(lengths[0])
+    if n < 1 or tuple(t.shape) != grid_shape(n, lengths):
+        raise ValueError(f"shape {tuple(t.shape)} does not match the domain lengths {lengths}")
+    return n
 
 
 def _stream():
@@ -167,14 +207,19 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _dev(t, n=None, name="array"):
+def _dev(t, shape=None, name="array"):
+    """shape None: any cube; else the exact (z, y, x) shape"""
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
         raise TypeError(f"{name} must be a float64 CUDA tensor")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
-    if t.dim() != 3 or len(set(t.shape)) != 1 or (n is not None and t.shape[0] != n):
+    if t.dim() != 3:
+        raise ValueError(f"{name} must be a 3D tensor")
+    if shape is None and len(set(t.shape)) != 1:
         raise ValueError(f"{name} must have shape (n, n, n)")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -184,6 +229,7 @@ class Solver:
     def __init__(self, n, **kw):
         self.config = make_config(n, **kw)
         self.n = int(n)
+        self.shape = grid_shape(self.n, kw.get("lengths", (1, 1, 1)))
         h = _VP()
         _check(load().sr_fmg_create(ctypes.byref(h), ctypes.byref(self.config)), "sr_fmg_create")
         self._h = h
@@ -244,7 +290,7 @@ class Solver:
         import torch
         if out is None:
             out = torch.empty_like(f)
-        _check(load().sr_fmg_solve(self._h, _dev(f, self.n, "f"), _dev(out, self.n, "u"),
+        _check(load().sr_fmg_solve(self._h, _dev(f, self.shape, "f"), _dev(out, self.shape, "u"),
                                    _stream()), "sr_fmg_solve")
         return out
 
@@ -256,13 +302,13 @@ class Solver:
         if u is None:
             u = torch.zeros_like(f)
         cycles, rel = ctypes.c_int(), ctypes.c_double()
-        _check(load().sr_fmg_vsolve(self._h, _dev(f, self.n, "f"), _dev(u, self.n, "u"),
+        _check(load().sr_fmg_vsolve(self._h, _dev(f, self.shape, "f"), _dev(u, self.shape, "u"),
                                     float(rtol), int(max_cycles), ctypes.byref(cycles),
                                     ctypes.byref(rel), _stream()), "sr_fmg_vsolve")
         return u, cycles.value, rel.value
 
     def solve_async(self, f, out):
-        _check(load().sr_fmg_solve_async(self._h, _dev(f, self.n, "f"), _dev(out, self.n, "u"),
+        _check(load().sr_fmg_solve_async(self._h, _dev(f, self.shape, "f"), _dev(out, self.shape, "u"),
                                          _stream()), "sr_fmg_solve_async")
         return out
 
@@ -275,8 +321,8 @@ class Solver:
         if hasattr(f, "numpy"):
             f = f.numpy()
         f = np.ascontiguousarray(f, dtype=np.float64)
-        if f.shape != (self.n,) * 3:
-            raise ValueError("f must have shape (n, n, n)")
+        if tuple(f.shape) != self.shape:
+            raise ValueError(f"f must have shape {self.shape}")
         if out is None:
             out = np.empty_like(f)
         fp = ctypes.c_void_p(f.ctypes.data)
@@ -322,8 +368,8 @@ class Batch:
     def _ptrs(self, fs, us):
         if len(fs) != len(self.solvers) or len(us) != len(self.solvers):
             raise ValueError("one f and one u per problem")
-        fp = (_VP * len(fs))(*[_dev(f, s.n, "f").value for f, s in zip(fs, self.solvers)])
-        up = (_VP * len(us))(*[_dev(u, s.n, "u").value for u, s in zip(us, self.solvers)])
+        fp = (_VP * len(fs))(*[_dev(f, s.shape, "f").value for f, s in zip(fs, self.solvers)])
+        up = (_VP * len(us))(*[_dev(u, s.shape, "u").value for u, s in zip(us, self.solvers)])
         return fp, up
 
     def solve(self, fs, us):
@@ -356,8 +402,8 @@ class Batch:
 def solve_batched(solvers, fs, us):
     """One-shot batched solve through sr_fmg_solve_batched."""
     hs = (_VP * len(solvers))(*[s._h for s in solvers])
-    fp = (_VP * len(fs))(*[_dev(f, s.n, "f").value for f, s in zip(fs, solvers)])
-    up = (_VP * len(us))(*[_dev(u, s.n, "u").value for u, s in zip(us, solvers)])
+    fp = (_VP * len(fs))(*[_dev(f, s.shape, "f").value for f, s in zip(fs, solvers)])
+    up = (_VP * len(us))(*[_dev(u, s.shape, "u").value for u, s in zip(us, solvers)])
     _check(load().sr_fmg_solve_batched(hs, fp, up, len(solvers), _stream()),
            "sr_fmg_solve_batched")
     return us
@@ -365,26 +411,46 @@ def solve_batched(solvers, fs, us):
 
 # ---- single components on whole grids (for parity tests) ----
 
-def op_apply(u):
+def _geo_cfg(t, geo, **extra):
+    return make_config(_per_unit(t, geo.get("lengths", (1, 1, 1))), **geo, **extra)
+
+
+def op_apply(u, **geo):
+    """A u; geo: lengths, stencil, weights (default: unit cube, 7-point)."""
     import torch
     out = torch.empty_like(u)
-    _check(load().sr_op_apply(u.shape[0], _dev(u), _dev(out), _stream()), "sr_op_apply")
+    if geo:
+        c = _geo_cfg(u, geo)
+        _check(load().sr_op_apply_ex(ctypes.byref(c), _dev(u, u.shape), _dev(out, u.shape),
+                                     _stream()), "sr_op_apply_ex")
+    else:
+        _check(load().sr_op_apply(u.shape[0], _dev(u), _dev(out), _stream()), "sr_op_apply")
     return out
 
 
-def op_residual(u, f):
+def op_residual(u, f, **geo):
     import torch
     r = torch.empty_like(u)
-    _check(load().sr_op_residual(u.shape[0], _dev(f), _dev(u), _dev(r), _stream()),
-           "sr_op_residual")
+    if geo:
+        c = _geo_cfg(u, geo)
+        _check(load().sr_op_residual_ex(ctypes.byref(c), _dev(f, u.shape), _dev(u, u.shape),
+                                        _dev(r, u.shape), _stream()), "sr_op_residual_ex")
+    else:
+        _check(load().sr_op_residual(u.shape[0], _dev(f), _dev(u), _dev(r), _stream()),
+               "sr_op_residual")
     return r
 
 
-def op_smooth(u, f, nu, cheb_lo=1.0 / 6.0, cheb_hi=1.0):
+def op_smooth(u, f, nu, cheb_lo=1.0 / 6.0, cheb_hi=1.0, **geo):
     """Chebyshev smoother; returns a new tensor (u is not modified)."""
     u = u.clone()
-    _check(load().sr_op_smooth(u.shape[0], nu, cheb_lo, cheb_hi, _dev(f), _dev(u), _stream()),
-           "sr_op_smooth")
+    if geo:
+        c = _geo_cfg(u, geo, cheb_lo=cheb_lo, cheb_hi=cheb_hi)
+        _check(load().sr_op_smooth_ex(ctypes.byref(c), nu, _dev(f, u.shape), _dev(u, u.shape),
+                                      _stream()), "sr_op_smooth_ex")
+    else:
+        _check(load().sr_op_smooth(u.shape[0], nu, cheb_lo, cheb_hi, _dev(f), _dev(u),
+                                   _stream()), "sr_op_smooth")
     return u
 
 
@@ -402,35 +468,51 @@ def op_smooth_noalloc(u, f, nu, cheb_lo=1.0 / 6.0, cheb_hi=1.0):
     return u
 
 
-def op_restrict(a):
+def op_restrict(a, **geo):
     import torch
-    n = a.shape[0]
-    out = torch.empty((n // 2,) * 3, dtype=a.dtype, device=a.device)
-    _check(load().sr_op_restrict(n, _dev(a), _dev(out), _stream()), "sr_op_restrict")
+    out = torch.empty(tuple(v // 2 for v in a.shape), dtype=a.dtype, device=a.device)
+    if geo:
+        c = _geo_cfg(a, geo)
+        _check(load().sr_op_restrict_ex(ctypes.byref(c), _dev(a, a.shape), _dev(out, out.shape),
+                                        _stream()), "sr_op_restrict_ex")
+    else:
+        _check(load().sr_op_restrict(a.shape[0], _dev(a), _dev(out), _stream()),
+               "sr_op_restrict")
     return out
 
 
-def op_prolong(ac):
+def op_prolong(ac, **geo):
     import torch
-    nc = ac.shape[0]
-    out = torch.empty((2 * nc,) * 3, dtype=ac.dtype, device=ac.device)
-    _check(load().sr_op_prolong(nc, _dev(ac), _dev(out), _stream()), "sr_op_prolong")
+    out = torch.empty(tuple(2 * v for v in ac.shape), dtype=ac.dtype, device=ac.device)
+    if geo:
+        c = _geo_cfg(ac, geo)
+        _check(load().sr_op_prolong_ex(ctypes.byref(c), _dev(ac, ac.shape),
+                                       _dev(out, out.shape), _stream()), "sr_op_prolong_ex")
+    else:
+        _check(load().sr_op_prolong(ac.shape[0], _dev(ac), _dev(out), _stream()),
+               "sr_op_prolong")
     return out
 
 
-def op_coarse_solve(f):
+def op_coarse_solve(f, **geo):
     import torch
     u = torch.empty_like(f)
-    _check(load().sr_op_coarse_solve(f.shape[0], _dev(f), _dev(u), _stream()),
-           "sr_op_coarse_solve")
+    if geo:
+        c = _geo_cfg(f, geo)
+        _check(load().sr_op_coarse_solve_ex(ctypes.byref(c), _dev(f, f.shape), _dev(u, f.shape),
+                                            _stream()), "sr_op_coarse_solve_ex")
+    else:
+        _check(load().sr_op_coarse_solve(f.shape[0], _dev(f), _dev(u), _stream()),
+               "sr_op_coarse_solve")
     return u
 
 
 def op_vcycle(f, u, **kw):
     """One FAS V-cycle; returns a new tensor."""
     u = u.clone()
-    c = make_config(f.shape[0], **kw)
-    _check(load().sr_op_vcycle(ctypes.byref(c), _dev(f), _dev(u), _stream()), "sr_op_vcycle")
+    c = make_config(_per_unit(f, kw.get("lengths", (1, 1, 1))), **kw)
+    _check(load().sr_op_vcycle(ctypes.byref(c), _dev(f, f.shape), _dev(u, f.shape), _stream()),
+           "sr_op_vcycle")
     return u
 
 

@@ -6,17 +6,40 @@ Sec. 4 (compute region Omega^C, its ghost shell inside the domain Omega^GSR,
 the support Omega^F, the genuine level-0 cells) are boolean masks.  Cells a
 segment does not own start as NaN, so any read outside the regions the paper
 allows shows up as NaN in the result.  Transfers are applied dimension by
-dimension, the coarsest solve uses the DST (exact.dst_solve) instead of
+dimension, the coarsest solve uses the DST (exact.dst_solve_g) instead of
 elimination, and restriction uses reshape/mean: the arithmetic order differs
 from the oracle's, the results agree to rounding.
 
-Readings follow the oracle's (A = -Delta_h, ghost = -mirror, Chebyshev on
-D^-1 A over [lo, hi] * 2, averaging restriction, trilinear prolongation,
-owner-writes at the transition level).
+Readings follow the oracle's (A = -Delta_h with the 7-point or a 27-point
+stencil, ghost = -mirror, Chebyshev on D^-1 A over [lo, hi] * lambda_max,
+averaging restriction, trilinear prolongation, owner-writes at the
+transition level).  Grids cover [0, l0] x [0, l1] x [0, l2] with n cells per
+unit length; arrays are [z][y][x].
 """
+import itertools
+
 import numpy as np
 
-from exact import dst_solve
+import exact
+
+
+class Params:
+    def __init__(self, alpha=1, nu1=2, nu2=2, cheb_lo=1.0 / 6.0, cheb_hi=1.0,
+                 lengths=(1, 1, 1), stencil=7, weights=None):
+        self.alpha, self.nu1, self.nu2 = alpha, nu1, nu2
+        self.lo, self.hi = cheb_lo, cheb_hi
+        self.lengths = tuple(int(v) for v in lengths)
+        self.stencil = stencil
+        self.w = (1.0, 0.0, 0.0) if stencil == 7 else tuple(weights)
+        w1, w2, w3 = self.w
+        self.w0 = 6 * w1 + 12 * w2 + 8 * w3
+        # largest value of the multilinear symbol over [-1, 1]^3, at a corner
+        self.lmax = max(exact.symbol(self.w, c) for c in itertools.product((-1, 1), repeat=3)) \
+            / self.w0
+
+    def shape(self, n):
+        lx, ly, lz = self.lengths
+        return (n * lz, n * ly, n * lx)
 
 
 def pad(a, fill=0.0):
@@ -39,16 +62,25 @@ def fill_bc(p):
     p[-1] = -p[-2]
 
 
-def apply(p, n):
-    c = p[1:-1, 1:-1, 1:-1]
-    nb = (p[:-2, 1:-1, 1:-1] + p[2:, 1:-1, 1:-1] + p[1:-1, :-2, 1:-1]
-          + p[1:-1, 2:, 1:-1] + p[1:-1, 1:-1, :-2] + p[1:-1, 1:-1, 2:])
-    return (6.0 * c - nb) * float(n * n)
+def _shifted(p, dz, dy, dx):
+    nz, ny, nx = (s - 2 for s in p.shape)
+    return p[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+
+
+def apply(p, n, P):
+    """A u on the interior of the padded p (ghosts must be valid); h = 1/n."""
+    sums = [0.0, 0.0, 0.0, 0.0]
+    for dz, dy, dx in itertools.product((-1, 0, 1), repeat=3):
+        far = (dz != 0) + (dy != 0) + (dx != 0)
+        if far and P.w[far - 1] != 0.0:
+            sums[far] = sums[far] + _shifted(p, dz, dy, dx)
+    w1, w2, w3 = P.w
+    return (P.w0 * inner(p) - w1 * sums[1] - w2 * sums[2] - w3 * sums[3]) * float(n * n)
 
 
 def restrict(a):
-    m = a.shape[0] // 2
-    return a.reshape(m, 2, m, 2, m, 2).mean(axis=(1, 3, 5))
+    z, y, x = (s // 2 for s in a.shape)
+    return a.reshape(z, 2, y, 2, x, 2).mean(axis=(1, 3, 5))
 
 
 def _prolong1d(p, axis):
@@ -62,19 +94,20 @@ def _prolong1d(p, axis):
 
 
 def prolong(p):
-    """trilinear interpolation of a padded coarse grid onto the fine interior."""
+    """trilinear interpolation of a padded coarse grid onto the fine interior
+    (x, then y, then z; each pass drops the padding of its own axis)."""
     return _prolong1d(_prolong1d(_prolong1d(p, 2), 1), 0)
 
 
-def cheb(p, f, mask, n, nu, lo, hi):
+def cheb(p, f, mask, n, nu, P):
     """Chebyshev smoother on the cells of mask; p is updated in place."""
     if nu <= 0:
         return
-    a, b = 2.0 * lo, 2.0 * hi
+    a, b = P.lo * P.lmax, P.hi * P.lmax
     theta, delta = 0.5 * (a + b), 0.5 * (b - a)
-    dinv = 1.0 / (6.0 * n * n)
+    dinv = 1.0 / (P.w0 * n * n)
     fill_bc(p)
-    d = dinv * (f - apply(p, n)) / theta
+    d = dinv * (f - apply(p, n, P)) / theta
     rho_old = delta / theta
     for m in range(nu):
         u = inner(p)
@@ -82,37 +115,34 @@ def cheb(p, f, mask, n, nu, lo, hi):
         if m == nu - 1:
             break
         fill_bc(p)
-        r = dinv * (f - apply(p, n))
+        r = dinv * (f - apply(p, n, P))
         rho = 1.0 / (2.0 * theta / delta - rho_old)
         d = rho * rho_old * d + (2.0 * rho / delta) * r
         rho_old = rho
 
 
-class Params:
-    def __init__(self, alpha=1, nu1=2, nu2=2, cheb_lo=1.0 / 6.0, cheb_hi=1.0):
-        self.alpha, self.nu1, self.nu2 = alpha, nu1, nu2
-        self.lo, self.hi = cheb_lo, cheb_hi
+def _direct(f, n, P):
+    return exact.dst_solve_g(f, n, P.w)
 
 
-def fasmgv(p, rhs, P, coarsest):
-    """FAS V-cycle on a whole padded grid p (updated in place)."""
-    n = p.shape[0] - 2
+def fasmgv(p, rhs, n, P, coarsest):
+    """FAS V-cycle on a whole padded grid p (updated in place), n per unit."""
     if n <= coarsest:
-        inner(p)[...] = dst_solve(rhs)
+        inner(p)[...] = _direct(rhs, n, P)
         return
-    full = np.ones((n,) * 3, dtype=bool)
-    cheb(p, rhs, full, n, P.nu1, P.lo, P.hi)
+    full = np.ones(rhs.shape, dtype=bool)
+    cheb(p, rhs, full, n, P.nu1, P)
     fill_bc(p)
-    r = rhs - apply(p, n)
+    r = rhs - apply(p, n, P)
     pc = pad(restrict(inner(p)))
     fill_bc(pc)
     t = pc.copy()
-    rc = restrict(r) + apply(pc, n // 2)
-    fasmgv(pc, rc, P, coarsest)
+    rc = restrict(r) + apply(pc, n // 2, P)
+    fasmgv(pc, rc, n // 2, P, coarsest)
     e = pc - t
     fill_bc(e)
     inner(p)[...] += prolong(e)
-    cheb(p, rhs, full, n, P.nu2, P.lo, P.hi)
+    cheb(p, rhs, full, n, P.nu2, P)
 
 
 def _coarsest(n):
@@ -121,63 +151,69 @@ def _coarsest(n):
     return n
 
 
-def fmg(f, P, coarsest=None):
+def fmg(f, P, coarsest=None, n=None):
     """Full multigrid on the whole grid; returns the padded finest solution."""
-    n = f.shape[0]
+    n = f.shape[2] // P.lengths[0] if n is None else n
     coarsest = _coarsest(n) if coarsest is None else coarsest
-    fs = [f]
-    while fs[-1].shape[0] > coarsest:
+    fs, ns = [f], [n]
+    while ns[-1] > coarsest:
         fs.append(restrict(fs[-1]))
-    fs = fs[::-1]
-    p = pad(dst_solve(fs[0]))
-    for fk in fs[1:]:
+        ns.append(ns[-1] // 2)
+    fs, ns = fs[::-1], ns[::-1]
+    p = pad(_direct(fs[0], ns[0], P))
+    for fk, nk in zip(fs[1:], ns[1:]):
         fill_bc(p)
         q = pad(prolong(p))
-        nk = fk.shape[0]
-        cheb(q, fk, np.ones((nk,) * 3, dtype=bool), nk, P.alpha, P.lo, P.hi)
-        fasmgv(q, fk, P, coarsest)
+        cheb(q, fk, np.ones(fk.shape, dtype=bool), nk, P.alpha, P)
+        fasmgv(q, fk, nk, P, coarsest)
         p = q
     return p
 
 
-def box_mask(n, lo, hi):
-    m = np.zeros((n,) * 3, dtype=bool)
+def box_mask(shape, lo, hi):
+    m = np.zeros(shape, dtype=bool)
     m[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = True
     return m
 
 
 def sr_fmg(f, seg, K, J, P):
     """FASFMGSR with full-grid masks; returns u on the fine grid."""
-    n = f.shape[0]
+    n = f.shape[2] // P.lengths[0]
     nk = [n >> (K - k) for k in range(K + 1)]
+    dims = lambda k: [nk[k] * l for l in P.lengths]  # noqa: E731  (x, y, z)
     fsr = {K: f}
     for k in range(K, 0, -1):
         fsr[k - 1] = restrict(fsr[k])
     coarsest = _coarsest(nk[0])
-    u0 = fmg(fsr[0], P, coarsest)
-    rho0 = np.full((nk[0],) * 3, np.nan)
-    uhat0 = np.full((nk[0],) * 3, np.nan)
-    nseg1 = n // seg
+    u0 = fmg(fsr[0], P, coarsest, nk[0])
+    rho0 = np.full(P.shape(nk[0]), np.nan)
+    uhat0 = np.full(P.shape(nk[0]), np.nan)
+    nsd = [n * l // seg for l in P.lengths]
     segs = []
-    for pz in range(nseg1):
-        for py in range(nseg1):
-            for px in range(nseg1):
+    for pz in range(nsd[2]):
+        for py in range(nsd[1]):
+            for px in range(nsd[0]):
                 q = (px, py, pz)
                 s = {"C": {}, "CG": {}, "F": {}, "U": {}, "T": {}, "R": {}}
                 for k in range(1, K + 1):
                     sk = seg >> (K - k)
+                    nd = dims(k)
                     lo = [max(0, qd * sk - J[k - 1]) for qd in q]
-                    hi = [min(nk[k], (qd + 1) * sk + J[k - 1]) for qd in q]
-                    s["C"][k] = box_mask(nk[k], lo, hi)
-                    s["CG"][k] = box_mask(nk[k], [max(0, v - 1) for v in lo],
-                                          [min(nk[k], v + 1) for v in hi])
-                    s["F"][k - 1] = box_mask(nk[k - 1], [v // 2 for v in lo], [v // 2 for v in hi])
-                    s["U"][k] = np.full((nk[k] + 2,) * 3, np.nan)
-                    s["T"][k] = np.full((nk[k] + 2,) * 3, np.nan)
-                    s["R"][k] = np.full((nk[k],) * 3, np.nan)
+                    hi = [min(nd[d], (q[d] + 1) * sk + J[k - 1]) for d in range(3)]
+                    sh = P.shape(nk[k])
+                    s["C"][k] = box_mask(sh, lo, hi)
+                    s["CG"][k] = box_mask(sh, [max(0, v - 1) for v in lo],
+                                          [min(nd[d], hi[d] + 1) for d in range(3)])
+                    s["F"][k - 1] = box_mask(P.shape(nk[k - 1]), [v // 2 for v in lo],
+                                             [v // 2 for v in hi])
+                    s["U"][k] = np.full(tuple(v + 2 for v in sh), np.nan)
+                    s["T"][k] = np.full(tuple(v + 2 for v in sh), np.nan)
+                    s["R"][k] = np.full(sh, np.nan)
                 s0 = seg >> K
-                s["G0"] = box_mask(nk[0], [qd * s0 for qd in q], [(qd + 1) * s0 for qd in q])
-                s["GK"] = box_mask(n, [qd * seg for qd in q], [(qd + 1) * seg for qd in q])
+                s["G0"] = box_mask(P.shape(nk[0]), [qd * s0 for qd in q],
+                                   [(qd + 1) * s0 for qd in q])
+                s["GK"] = box_mask(P.shape(n), [qd * seg for qd in q],
+                                   [(qd + 1) * seg for qd in q])
                 segs.append(s)
     for k in range(1, K + 1):
         fill_bc(u0)
@@ -190,12 +226,12 @@ def sr_fmg(f, seg, K, J, P):
             pr = prolong(src)
             inner(s["U"][k])[s["CG"][k]] = pr[s["CG"][k]]
             s["R"][k][s["C"][k]] = fsr[k][s["C"][k]]
-            cheb(s["U"][k], s["R"][k], s["C"][k], nk[k], P.alpha, P.lo, P.hi)
+            cheb(s["U"][k], s["R"][k], s["C"][k], nk[k], P.alpha, P)
             for j in range(k, 0, -1):
                 U = s["U"][j]
-                cheb(U, s["R"][j], s["C"][j], nk[j], P.nu1, P.lo, P.hi)
+                cheb(U, s["R"][j], s["C"][j], nk[j], P.nu1, P)
                 fill_bc(U)
-                r = s["R"][j] - apply(U, nk[j])
+                r = s["R"][j] - apply(U, nk[j], P)
                 uc, rc = restrict(inner(U)), restrict(r)
                 if j > 1:
                     F = s["F"][j - 1]
@@ -203,7 +239,7 @@ def sr_fmg(f, seg, K, J, P):
                     inner(Uc)[F] = uc[F]
                     fill_bc(Uc)
                     s["T"][j - 1] = Uc.copy()
-                    Au = apply(Uc, nk[j - 1])
+                    Au = apply(Uc, nk[j - 1], P)
                     C = s["C"][j - 1]
                     s["R"][j - 1][C] = Au[C]
                     s["R"][j - 1][F] += rc[F]
@@ -214,8 +250,8 @@ def sr_fmg(f, seg, K, J, P):
         inner(u0)[...] = uhat0
         fill_bc(u0)
         t0 = u0.copy()
-        rhs0 = rho0 + apply(u0, nk[0])
-        fasmgv(u0, rhs0, P, coarsest)
+        rhs0 = rho0 + apply(u0, nk[0], P)
+        fasmgv(u0, rhs0, nk[0], P, coarsest)
         e0 = u0 - t0
         fill_bc(e0)
         for s in segs:
@@ -228,8 +264,8 @@ def sr_fmg(f, seg, K, J, P):
                 pr = prolong(e)
                 CG = s["CG"][j]
                 inner(s["U"][j])[CG] += pr[CG]
-                cheb(s["U"][j], s["R"][j], s["C"][j], nk[j], P.nu2, P.lo, P.hi)
-    u = np.full((n,) * 3, np.nan)
+                cheb(s["U"][j], s["R"][j], s["C"][j], nk[j], P.nu2, P)
+    u = np.full(P.shape(n), np.nan)
     for s in segs:
         u[s["GK"]] = inner(s["U"][K])[s["GK"]]
     return u
