@@ -73,7 +73,8 @@ SR = [(8, dict(seg=4, K=1, J=[2])), (16, dict(seg=8, K=2, J=[2, 4])),
 def _oracle_kw(kw):
     kw = dict(kw)
     if kw.pop("mbs", False):
-        kw["J"] = [kw.pop("A") << k for k in range(kw["K"])]
+        J1 = kw.pop("A")
+        kw["J"] = [J1 << k for k in range(kw["K"])]
     elif "J" not in kw:
         from oracle import buffer_schedule
         kw["J"] = buffer_schedule(kw.pop("A"), kw.pop("B"), kw["K"])
