@@ -253,7 +253,8 @@ def run_ours(args):
         barrier()
         return max_over_ranks(e0.elapsed_time(e1))
 
-    sr = srfmg.Solver(N, **SR)
+    # graph mode: each solve is one captured CUDA graph (same kernels)
+    sr = srfmg.Solver(N, graph=True, **SR)
     for _ in range(args.warmup):
         sr.solve_async(ft, ut)
     sr.check()
@@ -295,8 +296,16 @@ def run_ours(args):
                    "tfp64ops": v["ops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] else None}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
 
+    # the same solve launched kernel by kernel (no graph)
+    direct = srfmg.Solver(N, **SR)
+    for _ in range(args.warmup):
+        direct.solve_async(ft, ut)
+    direct.check()
+    direct_ms = timed(direct, args.steps) / args.steps
+    direct.close()
+
     # the same solve without segmental refinement (plain FMG), same f
-    plain = srfmg.Solver(N)
+    plain = srfmg.Solver(N, graph=True)
     for _ in range(args.warmup):
         plain.solve_async(ft, ut)
     plain.check()
@@ -333,9 +342,11 @@ def run_ours(args):
     del fh, uh
 
     mixed = batch = None
+    paper = None
     if not args.no_extras:
         mixed = measure_mixed(args, timed_fn=max_over_ranks, world=world, rank=rank)
         batch = measure_batch(args, max_over_ranks, world)
+        paper = measure_paper(args, max_over_ranks, world)
 
     if rank != 0:
         if world > 1:
@@ -390,6 +401,9 @@ def run_ours(args):
                                "hbm_gbs": plain_bytes / (plain_ms / 1e3) / 1e9,
                                "hbm_frac_of_measured": plain_bytes / (plain_ms / 1e3) / 1e9 / hbm
                                if hbm else None},
+        "sr_fmg_fp64_256_kernel_by_kernel": {"ms": direct_ms,
+                                             "dof_s": world * N ** 3 / (direct_ms / 1e3)},
+        "paper_problem_27pt": paper,
         "sr_fmg_fp64_256": {"dof_s": value, "ms": ms,
                             "hbm_gbs": sr_bytes / (ms / 1e3) / 1e9,
                             "hbm_frac_of_measured": sr_bytes / (ms / 1e3) / 1e9 / hbm
@@ -450,6 +464,52 @@ def _time_loop(step, steps, stream=None):
     return e0.elapsed_time(e1)
 
 
+def measure_paper(args, timed_fn, world):
+    """The paper's own model problem (Sec. 5.1) at Table 2's N = 256 column:
+    [0,2]x[0,1]^2 with 1024 x 512 x 512 cells, 27-point operator ((14,3,1)/30),
+    4 x 2 x 2 segments of 256^3, K = 5, A = 8, B = 0; plain FMG on the same f.
+    Reports both solves' times, the error ratio e_r against the exact u
+    (the paper prints 1.13 for its stencil), and the FP64 rate of the
+    dominant 27-point kernel from the library's per-kernel profile."""
+    import numpy as np
+    import torch
+    from paper_1406_7808_gb300 import inputs, srfmg
+    n = 512
+    geo = dict(lengths=(2, 1, 1), stencil=27)
+    f, u = inputs.paper_problem(n)
+    ft = torch.from_numpy(f).cuda()
+    ut = torch.empty_like(ft)
+    out = {"grid": [1024, 512, 512], "segments": [4, 2, 2], "seg": 256, "K": 5, "A": 8, "B": 0,
+           "weights": list(srfmg.W27_DEFAULT), "paper_e_r": 1.13}
+    steps = max(2, min(args.steps, 5))
+    err = {}
+    for name, kw in (("sr", dict(seg=256, K=5, A=8, B=0)), ("plain", {})):
+        with srfmg.Solver(n, graph=True, **geo, **kw) as s:
+            for _ in range(3):
+                s.solve_async(ft, ut)
+            s.check()
+            ms = timed_fn(_time_loop(lambda: s.solve_async(ft, ut), steps)) / steps
+            s.check()
+            err[name] = float(np.abs(ut.cpu().numpy() - u).max())
+            out[name + "_ms"] = ms
+            out[name + "_dof_s"] = world * f.size / (ms / 1e3)
+            if name == "sr":
+                s.profile(True)
+                s.solve_async(ft, ut)
+                s.check()
+                prof = s.profile_read()
+                s.profile(False)
+                top = max(prof, key=lambda k: prof[k]["ms"])
+                d = prof[top]
+                out["dominant_kernel"] = {
+                    "kind": top, "share": d["ms"] / sum(v["ms"] for v in prof.values()),
+                    "tfp64ops": d["ops"] / (d["ms"] / 1e3) / 1e12,
+                    "frac_of_fp64_peak": d["ops"] / (d["ms"] / 1e3) / 1e12 / FP64_PEAK_TOPS}
+    out["e_sr"], out["e_conv"] = err["sr"], err["plain"]
+    out["e_r"] = err["sr"] / err["plain"]
+    return out
+
+
 def measure_mixed(args, timed_fn, world, rank):
     """Mixed-precision SR-FMG, 512^3 cells, 64^3-cell segments, K = 4 (f of
     the manufactured problem at seed 1)."""
@@ -461,7 +521,7 @@ def measure_mixed(args, timed_fn, world, rank):
     f, _ = inputs.manufactured(n, 1 + rank)
     ft = torch.from_numpy(f).cuda()
     ut = torch.empty_like(ft)
-    with srfmg.Solver(n, **workloads.config(kw)) as s:
+    with srfmg.Solver(n, graph=True, **workloads.config(kw)) as s:
         for _ in range(args.warmup):
             s.solve_async(ft, ut)
         s.check()

@@ -103,6 +103,14 @@ typedef struct sr_fmg_s* sr_fmg_t;
  *             weights must be consistent with -Delta (w[0] + 4 w[1] + 4 w[2]
  *             = 1) and give a positive definite operator; 27 requires
  *             SR_FP64.
+ *   graph     1: sr_fmg_solve_async (and sr_fmg_solve, sr_fmg_solve_host)
+ *             queue the whole solve as one CUDA graph, captured on the
+ *             first call for an (f, u) pair -- and again when the pair
+ *             changes -- and relaunched afterwards (same kernels, same
+ *             results, fewer launch gaps); solves made while the per-kernel
+ *             profiler is on launch kernel by kernel.  Not for use inside
+ *             the caller's own stream capture.  0 (default): kernel by
+ *             kernel.
  */
 typedef struct {
   int n;
@@ -120,6 +128,7 @@ typedef struct {
   int len[3];
   int stencil;
   double w[3];
+  int graph;
 } sr_fmg_config;
 
 /* Fill cfg with the defaults for an n^3 grid: unit cube, 7-point operator,

@@ -9,9 +9,9 @@
 // dimension, so edge and corner ghosts of the reflection are exact); a
 // neighbour inside the domain but outside the box's compute region is read
 // from the box's one-cell shell (frozen SR ghosts, or zero in the smoother's
-// residual array).  These kernels read every neighbour through the L1 cache;
-// the operator is used for the paper's accuracy experiments, not for the
-// 7-point throughput path.
+// residual array).  The smoother passes and the residual walk columns in z
+// (below); the coarse-level kernels read every neighbour through the L1
+// cache.
 #include "srfmg_internal.cuh"
 
 namespace srfmg {
@@ -69,49 +69,6 @@ __device__ __forceinline__ bool finite27(double v) {
   return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
 }
 
-// r = D^-1 (f - A u) = f h^2/w0 - u + (w1 sf + w2 se + w3 sc)/w0
-__global__ void __launch_bounds__(kThreads27) k27_cheb_residual(LevelView L,
-                                                                const double* __restrict__ u,
-                                                                double* __restrict__ r,
-                                                                FieldT<double> f, double cf,
-                                                                double cf1, double ce, double cc) {
-  __shared__ BoxDesc B, FB;
-  if (threadIdx.x == 0) {
-    B = L.boxes[blockIdx.y];
-    FB = f.single ? f.boxes[0] : f.boxes[blockIdx.y];
-  }
-  __syncthreads();
-  const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
-  const int ncell = ex * ey * ez;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
-    const Cell27 q = cell27(i, B.lo, ex, ey);
-    const long long c = at27(B, q.x, q.y, q.z);
-    double s[3];
-    sums27(u, B, L.nx, L.ny, L.nz, q.x, q.y, q.z, s);
-    r[c] = f.p[at27(FB, q.x, q.y, q.z)] * cf - u[c] + cf1 * s[0] + ce * s[1] + cc * s[2];
-  }
-}
-
-// u += a r + bf sf(r) + be se(r) + bc sc(r): the degree-2 Chebyshev
-// polynomial x0 + c1 r0 + c2 D^-1 A r0 written with D^-1 A = I - W
-__global__ void __launch_bounds__(kThreads27) k27_cheb2_update(LevelView L, double* __restrict__ u,
-                                                               const double* __restrict__ r,
-                                                               double a, double bf, double be,
-                                                               double bc) {
-  __shared__ BoxDesc B;
-  if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
-  __syncthreads();
-  const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
-  const int ncell = ex * ey * ez;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
-    const Cell27 q = cell27(i, B.lo, ex, ey);
-    const long long c = at27(B, q.x, q.y, q.z);
-    double s[3];
-    sums27(r, B, L.nx, L.ny, L.nz, q.x, q.y, q.z, s);
-    u[c] += a * r[c] + bf * s[0] + be * s[1] + bc * s[2];
-  }
-}
-
 // n^2 (w0 v - w1 sf - w2 se - w3 sc) at (x, y, z)
 __device__ __forceinline__ double op27(const double* __restrict__ a, const BoxDesc& B,
                                        const LevelView& L, W27 w, double n2, int x, int y,
@@ -138,43 +95,6 @@ __global__ void __launch_bounds__(kThreads27) k27_apply(LevelView L, const doubl
     const Cell27 q = cell27(i, B.lo, ex, ey);
     const double au = op27(u, B, L, w, n2, q.x, q.y, q.z);
     out[at27(B, q.x, q.y, q.z)] = residual ? f.p[at27(FB, q.x, q.y, q.z)] - au : au;
-  }
-}
-
-// per coarse cell of the fine boxes' restriction region: uhat = average of
-// the 8 children of u, rho = average of the 8 children of f - A u
-__global__ void __launch_bounds__(kThreads27) k27_resid_restrict(LevelView F,
-                                                                 const double* __restrict__ u,
-                                                                 FieldT<double> f, LevelView C,
-                                                                 double* __restrict__ uhat_dst,
-                                                                 double* __restrict__ rho_dst,
-                                                                 W27 w, double n2) {
-  __shared__ BoxDesc B, FB, CB;
-  if (threadIdx.x == 0) {
-    B = F.boxes[blockIdx.y];
-    FB = f.single ? f.boxes[0] : f.boxes[blockIdx.y];
-    CB = (C.nbox == 1) ? C.boxes[0] : C.boxes[blockIdx.y];
-  }
-  __syncthreads();
-  const int lo[3] = {B.rlo[0], B.rlo[1], B.rlo[2]};
-  const int ex = B.rhi[0] - lo[0], ey = B.rhi[1] - lo[1], ez = B.rhi[2] - lo[2];
-  const int ncell = ex * ey * ez;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
-    const Cell27 q = cell27(i, lo, ex, ey);
-    double su = 0.0, sr = 0.0;
-#pragma unroll
-    for (int cz = 0; cz < 2; ++cz)
-#pragma unroll
-      for (int cy = 0; cy < 2; ++cy)
-#pragma unroll
-        for (int cx = 0; cx < 2; ++cx) {
-          const int x = 2 * q.x + cx, y = 2 * q.y + cy, z = 2 * q.z + cz;
-          su += u[at27(B, x, y, z)];
-          sr += f.p[at27(FB, x, y, z)] - op27(u, B, F, w, n2, x, y, z);
-        }
-    const long long cc = at27(CB, q.x, q.y, q.z);
-    uhat_dst[cc] = 0.125 * su;
-    rho_dst[cc] = 0.125 * sr;
   }
 }
 
@@ -276,6 +196,167 @@ __global__ void __launch_bounds__(kThreads27) k27_resid_norm(LevelView L,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Column (z-marching) forms of the operator's two hot passes.  With, for
+// every (x, y) column and plane z, the in-plane quantities
+//   c(z) = a(x, y, z),  e(z) = sum of the 4 in-plane face neighbours,
+//   k(z) = sum of the 4 in-plane corner neighbours,
+// the neighbour classes of cell (x, y, z) are
+//   faces   = e(z) + c(z-1) + c(z+1),
+//   edges   = k(z) + e(z-1) + e(z+1),
+//   corners = k(z-1) + k(z+1),
+// so a thread walking a column forms one new plane per cell (6 additions)
+// plus 5 additions, instead of 26.  A plane outside the domain is the
+// mirror plane negated; in-plane neighbours outside the domain are mirrored
+// with one sign flip per outside dimension.  Threads of a block take
+// consecutive cells of the box's flattened (x, y) compute plane; blockIdx.x
+// enumerates (plane block, z chunk).
+constexpr int kZ27Threads = 256, kZ27Chunk = 16;
+
+struct Plane27 {
+  double c, e, k;
+};
+
+struct Col27 {
+  long long xm, xp, ym, yp;  // offsets of the in-plane neighbours (mirrored)
+  bool fxm, fxp, fym, fyp;   // sign flips
+};
+
+__device__ __forceinline__ Col27 column27(const BoxDesc& B, const LevelView& L, int x, int y) {
+  Col27 q;
+  q.fxm = x == 0;
+  q.fxp = x == L.nx - 1;
+  q.fym = y == 0;
+  q.fyp = y == L.ny - 1;
+  q.xm = q.fxm ? 0 : -1;
+  q.xp = q.fxp ? 0 : 1;
+  q.ym = q.fym ? 0 : -(long long)B.sy;
+  q.yp = q.fyp ? 0 : (long long)B.sy;
+  return q;
+}
+
+__device__ __forceinline__ double sgn27(double v, bool flip) { return flip ? -v : v; }
+
+// in-plane quantities of the plane through offset p (the column's cell)
+__device__ __forceinline__ Plane27 plane27(const double* __restrict__ a, long long p,
+                                           const Col27& q) {
+  Plane27 r;
+  r.c = a[p];
+  r.e = sgn27(a[p + q.xm], q.fxm) + sgn27(a[p + q.xp], q.fxp) + sgn27(a[p + q.ym], q.fym) +
+        sgn27(a[p + q.yp], q.fyp);
+  r.k = sgn27(a[p + q.xm + q.ym], q.fxm ^ q.fym) + sgn27(a[p + q.xp + q.ym], q.fxp ^ q.fym) +
+        sgn27(a[p + q.xm + q.yp], q.fxm ^ q.fyp) + sgn27(a[p + q.xp + q.yp], q.fxp ^ q.fyp);
+  return r;
+}
+
+__device__ __forceinline__ Plane27 neg27(Plane27 p) { return Plane27{-p.c, -p.e, -p.k}; }
+
+__device__ __forceinline__ bool ztile27(const BoxDesc& B, int nplane, int& x, int& y, int& z0,
+                                        int& z1) {
+  const int tz = blockIdx.x / nplane, pb = blockIdx.x - tz * nplane;
+  const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1];
+  const int i = pb * kZ27Threads + threadIdx.x;
+  const int iy = i / ex;
+  x = B.lo[0] + (i - iy * ex);
+  y = B.lo[1] + iy;
+  z0 = B.lo[2] + tz * kZ27Chunk;
+  z1 = min(z0 + kZ27Chunk, B.hi[2]);
+  return iy < ey && z0 < z1;
+}
+
+// mode 0: r = D^-1 (f - A u) (the smoother's residual);
+// mode 1: u += a r + bf F(r) + be E(r) + bc C(r) (the degree-2 update; here
+//         `a_in` is r and `u` is updated);
+// mode 2: out = f - A u (the plain residual).
+template <int kMode>
+__global__ void __launch_bounds__(kZ27Threads) k27_column(LevelView L,
+                                                          const double* __restrict__ a_in,
+                                                          double* __restrict__ out,
+                                                          FieldT<double> f, double c0,
+                                                          double cf, double ce, double cc,
+                                                          int nplane) {
+  __shared__ BoxDesc B, FB;
+  if (threadIdx.x == 0) {
+    B = L.boxes[blockIdx.y];
+    FB = (kMode != 1) ? (f.single ? f.boxes[0] : f.boxes[blockIdx.y]) : B;
+  }
+  __syncthreads();
+  int x, y, z0, z1;
+  if (!ztile27(B, nplane, x, y, z0, z1)) return;
+  const Col27 q = column27(B, L, x, y);
+  const long long sz = B.sz;
+  long long p = at27(B, x, y, z0);
+  long long fp = at27(FB, x, y, z0);
+  const long long fsz = FB.sz;
+  Plane27 pc = plane27(a_in, p, q);
+  Plane27 pm = (z0 > 0) ? plane27(a_in, p - sz, q) : neg27(pc);
+  for (int z = z0; z < z1; ++z) {
+    const Plane27 pp = (z < L.nz - 1) ? plane27(a_in, p + sz, q) : neg27(pc);
+    const double F = pc.e + pm.c + pp.c;
+    const double E = pc.k + pm.e + pp.e;
+    const double C = pm.k + pp.k;
+    const double nb = cf * F + ce * E + cc * C;
+    if (kMode == 0) {
+      out[p] = f.p[fp] * c0 - pc.c + nb;
+    } else if (kMode == 1) {
+      out[p] += c0 * pc.c + nb;
+    } else {
+      out[p] = f.p[fp] - (c0 * pc.c - nb);
+    }
+    pm = pc;
+    pc = pp;
+    p += sz;
+    fp += fsz;
+  }
+}
+
+// uhat = average of the 8 children of u, rho = average of the 8 children of r
+// (r = f - A u already formed on the fine compute region)
+__global__ void __launch_bounds__(kThreads27) k27_restrict_pair(LevelView F,
+                                                                const double* __restrict__ u,
+                                                                const double* __restrict__ r,
+                                                                LevelView C,
+                                                                double* __restrict__ uhat_dst,
+                                                                double* __restrict__ rho_dst) {
+  __shared__ BoxDesc B, CB;
+  if (threadIdx.x == 0) {
+    B = F.boxes[blockIdx.y];
+    CB = (C.nbox == 1) ? C.boxes[0] : C.boxes[blockIdx.y];
+  }
+  __syncthreads();
+  const int lo[3] = {B.rlo[0], B.rlo[1], B.rlo[2]};
+  const int ex = B.rhi[0] - lo[0], ey = B.rhi[1] - lo[1], ez = B.rhi[2] - lo[2];
+  const int ncell = ex * ey * ez;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
+    const Cell27 q = cell27(i, lo, ex, ey);
+    const long long c0 = at27(B, 2 * q.x, 2 * q.y, 2 * q.z);
+    const long long sy = B.sy, sz = B.sz;
+    double su = 0.0, sr = 0.0;
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+      for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx) {
+          const long long c = c0 + cz * sz + cy * sy + cx;
+          su += u[c];
+          sr += r[c];
+        }
+    const long long cc = at27(CB, q.x, q.y, q.z);
+    uhat_dst[cc] = 0.125 * su;
+    rho_dst[cc] = 0.125 * sr;
+  }
+}
+
+int nplane27(const LevelView& L) {
+  return (L.max_ex * L.max_ey + kZ27Threads - 1) / kZ27Threads;
+}
+
+dim3 zgrid27(const LevelView& L) {
+  const int nzc = (L.max_ez + kZ27Chunk - 1) / kZ27Chunk;
+  return dim3((unsigned)(nplane27(L) * nzc), (unsigned)L.nbox, 1);
+}
+
 dim3 grid27(const LevelView& L, int cells) {
   int bx = (cells + kThreads27 - 1) / kThreads27;
   if (bx < 1) bx = 1;
@@ -288,16 +369,35 @@ double sq27(int n) { return (double)n * (double)n; }
 
 cudaError_t launch27_cheb_residual(const LevelView& L, const double* u, double* r,
                                    FieldT<double> f, W27 w, cudaStream_t s) {
-  k27_cheb_residual<<<grid27(L, L.max_cells), kThreads27, 0, s>>>(
-      L, u, r, f, 1.0 / (w.w0 * sq27(L.n)), w.w1 / w.w0, w.w2 / w.w0, w.w3 / w.w0);
+  k27_column<0><<<zgrid27(L), kZ27Threads, 0, s>>>(L, u, r, f, 1.0 / (w.w0 * sq27(L.n)),
+                                                   w.w1 / w.w0, w.w2 / w.w0, w.w3 / w.w0,
+                                                   nplane27(L));
   return cudaGetLastError();
 }
 
 cudaError_t launch27_cheb2_update(const LevelView& L, double* u, const double* r, double a,
                                   double c2, W27 w, cudaStream_t s) {
   // W r = (w1 sf + w2 se + w3 sc)/w0 enters with the factor -c2
-  k27_cheb2_update<<<grid27(L, L.max_cells), kThreads27, 0, s>>>(
-      L, u, r, a, -c2 * w.w1 / w.w0, -c2 * w.w2 / w.w0, -c2 * w.w3 / w.w0);
+  FieldT<double> none{nullptr, L.boxes, 0};
+  k27_column<1><<<zgrid27(L), kZ27Threads, 0, s>>>(L, r, u, none, a, -c2 * w.w1 / w.w0,
+                                                   -c2 * w.w2 / w.w0, -c2 * w.w3 / w.w0,
+                                                   nplane27(L));
+  return cudaGetLastError();
+}
+
+cudaError_t launch27_residual_zm(const LevelView& L, const double* u, FieldT<double> f,
+                                 double* r, W27 w, cudaStream_t s) {
+  const double n2 = sq27(L.n);
+  k27_column<2><<<zgrid27(L), kZ27Threads, 0, s>>>(L, u, r, f, n2 * w.w0, n2 * w.w1, n2 * w.w2,
+                                                   n2 * w.w3, nplane27(L));
+  return cudaGetLastError();
+}
+
+cudaError_t launch27_restrict_pair(const LevelView& F, const double* u, const double* r,
+                                   const LevelView& C, double* uhat_dst, double* rho_dst,
+                                   cudaStream_t s) {
+  k27_restrict_pair<<<grid27(F, F.max_restrict), kThreads27, 0, s>>>(F, u, r, C, uhat_dst,
+                                                                     rho_dst);
   return cudaGetLastError();
 }
 
@@ -311,14 +411,6 @@ cudaError_t launch27_apply(const LevelView& L, const double* u, double* out, W27
 cudaError_t launch27_residual(const LevelView& L, const double* u, FieldT<double> f, double* r,
                               W27 w, cudaStream_t s) {
   k27_apply<<<grid27(L, L.max_cells), kThreads27, 0, s>>>(L, u, r, f, 1, w, sq27(L.n));
-  return cudaGetLastError();
-}
-
-cudaError_t launch27_resid_restrict(const LevelView& F, const double* u, FieldT<double> f,
-                                    const LevelView& C, double* uhat_dst, double* rho_dst, W27 w,
-                                    cudaStream_t s) {
-  k27_resid_restrict<<<grid27(F, F.max_restrict), kThreads27, 0, s>>>(F, u, f, C, uhat_dst,
-                                                                      rho_dst, w, sq27(F.n));
   return cudaGetLastError();
 }
 

@@ -133,6 +133,7 @@ struct sr_fmg_s {
   double* hbuf_f = nullptr;        // device staging for sr_fmg_solve_host
   double* hbuf_u = nullptr;
   unsigned long long* norms = nullptr;  // sr_fmg_vsolve: ||f||, ||f - A u|| as double bits
+  sr_fmg_batch_t graph = nullptr;  // graph mode: a batch of this one handle
   int launches = 0;                // kernel launches queued by the last solve
   Profile prof;
 
@@ -578,14 +579,6 @@ cudaError_t op_cheb2_update(const sr_fmg_s* h, const LevelView& L, T* u, const T
   return launch_cheb2_update<T>(L, u, r, c.a, c.b, s);
 }
 template <typename T>
-cudaError_t op_resid_restrict(const sr_fmg_s* h, const LevelView& F, const T* u, FieldT<T> f,
-                              const LevelView& C, T* uhat, T* rho, cudaStream_t s) {
-  if constexpr (sizeof(T) == 8) {
-    if (h->op27) return launch27_resid_restrict(F, u, f, C, uhat, rho, h->w27, s);
-  }
-  return launch_resid_restrict<T>(F, u, f, C, uhat, rho, s);
-}
-template <typename T>
 cudaError_t op_coarse_rhs(const sr_fmg_s* h, const LevelView& C, const LevelView& F, const T* u,
                           const T* rho, T* rhs, T* t, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
@@ -605,9 +598,31 @@ cudaError_t op_transition_rhs(const sr_fmg_s* h, const LevelView& C, const T* t,
 // algorithmic floating-point operations per unit of the operator kernels
 // (7-point / 27-point): smoother passes per cell, residual + restriction per
 // coarse cell, coarse right-hand side per cell
-double ops_smooth(const sr_fmg_s* h) { return h->op27 ? 30 : 7; }
-double ops_restrict(const sr_fmg_s* h) { return h->op27 ? 258 : 42; }
+double ops_smooth(const sr_fmg_s* h) { return h->op27 ? 15 : 7; }
 double ops_rhs(const sr_fmg_s* h) { return h->op27 ? 31 : 7; }
+
+// uhat, rho on the coarse cells of F's restriction region from the fine u
+// and right-hand side f: one fused 7-point pass (the residual of the 8
+// children summed through the faces of the 2x2x2 block), or for the
+// 27-point operator the residual into F's smoother scratch r (column form)
+// followed by the restriction of u and r
+template <typename T>
+int resid_restrict(sr_fmg_s* h, const Level<T>& F, const T* u, FieldT<T> f, const Level<T>& C,
+                   T* uhat, T* rho, cudaStream_t s) {
+  const double w = sizeof(T);
+  if constexpr (sizeof(T) == 8) {
+    if (h->op27) {
+      LAUNCH(h, kResidRestrict, F.tot_cells, 16, 3 * w, s,
+             launch27_residual_zm(F.view, u, f, F.r, h->w27, s));
+      LAUNCH(h, kResidRestrict, F.tot_restrict, 16, 18 * w, s,
+             launch27_restrict_pair(F.view, u, F.r, C.view, uhat, rho, s));
+      return SR_OK;
+    }
+  }
+  LAUNCH(h, kind_of<T>(kResidRestrict), F.tot_restrict, 42, 18 * w, s,
+         launch_resid_restrict<T>(F.view, u, f, C.view, uhat, rho, s));
+  return SR_OK;
+}
 
 template <typename T>
 int smooth(sr_fmg_s* h, const Level<T>& L, const Cheb& c, T* u, FieldT<T> f, cudaStream_t s) {
@@ -647,8 +662,8 @@ int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStrea
   Level<T>& C = H.glev[g - 1];
   int rc = smooth(h, L, h->pre, u, rhs, s);
   if (rc) return rc;
-  LAUNCH(h, kind_of<T>(kResidRestrict), L.tot_restrict, ops_restrict(h), 18 * w, s,
-         op_resid_restrict<T>(h, L.view, u, rhs, C.view, C.u, C.rho, s));
+  rc = resid_restrict<T>(h, L, u, rhs, C, C.u, C.rho, s);
+  if (rc) return rc;
   LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h), 4 * w, s,
          op_coarse_rhs<T>(h, C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
   rc = vcycle_global(h, H, g - 1, C.u, view_global<T>(C, C.rhs), s);
@@ -741,13 +756,13 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
       if (rc) return rc;
       if (j > 1) {
         Level<T>& C = H.slev[j - 1];
-        LAUNCH(h, kind_of<T>(kResidRestrict), Lj.tot_restrict, ops_restrict(h), 18 * w, s,
-               op_resid_restrict<T>(h, Lj.view, Lj.u, rhs, C.view, C.u, C.rho, s));
+        rc = resid_restrict<T>(h, Lj, Lj.u, rhs, C, C.u, C.rho, s);
+        if (rc) return rc;
         LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h), 4 * w, s,
                op_coarse_rhs<T>(h, C.view, Lj.view, C.u, C.rho, C.rhs, C.t, s));
       } else {
-        LAUNCH(h, kind_of<T>(kResidRestrict), Lj.tot_restrict, ops_restrict(h), 18 * w, s,
-               op_resid_restrict<T>(h, Lj.view, Lj.u, rhs, L0.view, L0.t, L0.rho, s));
+        rc = resid_restrict<T>(h, Lj, Lj.u, rhs, L0, L0.t, L0.rho, s);
+        if (rc) return rc;
       }
     }
     // transition level: u_0 <- \hat I u_1, t_0 = u_0, r_0 = rho_0 + L_0 u_0, FASMGV
@@ -863,6 +878,17 @@ int collect_profile(sr_fmg_s* h) {
 
 }  // namespace
 
+// the solve queued kernel by kernel, or (graph mode, profiler off) as the
+// handle's captured graph
+static int queue_solve(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
+  if (!h->cfg.graph || h->prof.on) return enqueue_solve(h, f, u, s);
+  if (!h->graph) {
+    int rc = sr_fmg_batch_create(&h->graph, &h, 1);
+    if (rc) return rc;
+  }
+  return sr_fmg_batch_solve_async(h->graph, &f, &u, s);
+}
+
 int srfmg::enqueue_solve_unchecked(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
   DeviceGuard g(h->device);
   return enqueue_solve(h, f, u, s);
@@ -940,6 +966,7 @@ int sr_fmg_create(sr_fmg_t* out, const sr_fmg_config* cfg) {
 int sr_fmg_destroy(sr_fmg_t h) {
   if (!h) return SR_OK;
   DeviceGuard g(h->device);
+  if (h->graph) sr_fmg_batch_destroy(h->graph);
   free_all(h);
   delete h;
   return SR_OK;
@@ -959,7 +986,7 @@ int sr_fmg_solve_async(sr_fmg_t h, const double* f_dev, double* u_dev, void* str
   if (fa < ua + bytes && ua < fa + bytes) return SR_ERR_INVALID;
   if (!is_device_ptr(f_dev) || !is_device_ptr(u_dev)) return SR_ERR_INVALID;
   DeviceGuard g(h->device);
-  return enqueue_solve(h, f_dev, u_dev, (cudaStream_t)stream);
+  return queue_solve(h, f_dev, u_dev, (cudaStream_t)stream);
 }
 
 int sr_fmg_check(sr_fmg_t h, void* stream) {
@@ -991,7 +1018,7 @@ int sr_fmg_solve_host(sr_fmg_t h, const double* f_host, double* u_host, void* st
   }
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(h->hbuf_f, f_host, bytes, cudaMemcpyHostToDevice, s));
-  int rc = enqueue_solve(h, h->hbuf_f, h->hbuf_u, s);
+  int rc = queue_solve(h, h->hbuf_f, h->hbuf_u, s);
   if (rc) return rc;
   CK(cudaMemcpyAsync(u_host, h->hbuf_u, bytes, cudaMemcpyDeviceToHost, s));
   return sr_fmg_check(h, stream);

@@ -163,9 +163,14 @@ cudaError_t launch27_apply(const LevelView& L, const double* u, double* out, W27
                            cudaStream_t s);
 cudaError_t launch27_residual(const LevelView& L, const double* u, FieldT<double> f, double* r,
                               W27 w, cudaStream_t s);
-cudaError_t launch27_resid_restrict(const LevelView& F, const double* u, FieldT<double> f,
-                                    const LevelView& C, double* uhat_dst, double* rho_dst, W27 w,
-                                    cudaStream_t s);
+// r = f - A u on the compute region (column form; r's shell is not written)
+cudaError_t launch27_residual_zm(const LevelView& L, const double* u, FieldT<double> f,
+                                 double* r, W27 w, cudaStream_t s);
+// uhat = average of the 8 children of u, rho = average of the 8 children of r
+// on the fine boxes' restriction region
+cudaError_t launch27_restrict_pair(const LevelView& F, const double* u, const double* r,
+                                   const LevelView& C, double* uhat_dst, double* rho_dst,
+                                   cudaStream_t s);
 cudaError_t launch27_coarse_rhs(const LevelView& C, const LevelView& F, const double* u,
                                 const double* rho, double* rhs, double* t, W27 w,
                                 cudaStream_t s);

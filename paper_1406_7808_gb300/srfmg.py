@@ -57,6 +57,7 @@ class Config(ctypes.Structure):
         ("len", ctypes.c_int * 3),
         ("stencil", ctypes.c_int),
         ("w", ctypes.c_double * 3),
+        ("graph", ctypes.c_int),
     ]
 
 
@@ -153,11 +154,11 @@ def buffer_schedule(A, B, K):
 
 def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, nu2=2,
                 cheb_lo=1.0 / 6.0, cheb_hi=1.0, precision=SR_FP64, n_outer=2, mixed=False,
-                mbs=False, lengths=(1, 1, 1), stencil=7, weights=None):
+                mbs=False, lengths=(1, 1, 1), stencil=7, weights=None, graph=False):
     """sr_fmg_config with n cells per unit length (mixed=True selects SR_MIXED;
     mbs=True the maximum buffer schedule J_k = 2^(k-1) A; lengths the domain
     [0, l0] x [0, l1] x [0, l2]; stencil 7 or 27 with weights (faces, edges,
-    corners))."""
+    corners); graph=True queues each solve as one captured CUDA graph)."""
     c = Config()
     load().sr_fmg_default_config(ctypes.byref(c), int(n))
     c.n_coarse, c.seg, c.K, c.A, c.B = n_coarse, seg, K, A, B
@@ -174,6 +175,7 @@ def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, 
     for d in range(3):
         c.len[d] = int(lengths[d])
     c.stencil = int(stencil)
+    c.graph = int(bool(graph))
     if weights is None and int(stencil) == 27:
         weights = W27_DEFAULT
     if weights is not None:
