@@ -210,7 +210,10 @@ __global__ void __launch_bounds__(kThreads27) k27_resid_norm(LevelView L,
 // mirror plane negated; in-plane neighbours outside the domain are mirrored
 // with one sign flip per outside dimension.  Threads of a block take
 // consecutive cells of the box's flattened (x, y) compute plane; blockIdx.x
-// enumerates (plane block, z chunk).
+// enumerates (plane block, z chunk).  As in the 7-point kernels, every
+// float64 operation is a fused multiply-add with kernel-parameter constants
+// (additions as fma(a, one, b)) and sign flips are integer XORs: on sm_103a
+// that form issues faster than DADD, DMUL or a float64 negation.
 constexpr int kZ27Threads = 256, kZ27Chunk = 16;
 
 struct Plane27 {
@@ -235,21 +238,33 @@ __device__ __forceinline__ Col27 column27(const BoxDesc& B, const LevelView& L, 
   return q;
 }
 
-__device__ __forceinline__ double sgn27(double v, bool flip) { return flip ? -v : v; }
+// v or -v, the sign bit flipped on the integer pipe (inline PTX, so that the
+// compiler cannot turn it into a float64 negation)
+__device__ __forceinline__ double sgn27(double v, bool flip) {
+  int hi = __double2hiint(v);
+  const unsigned m = (unsigned)flip << 31;
+  asm("xor.b32 %0, %0, %1;" : "+r"(hi) : "r"(m));
+  return __hiloint2double(hi, __double2loint(v));
+}
 
 // in-plane quantities of the plane through offset p (the column's cell)
 __device__ __forceinline__ Plane27 plane27(const double* __restrict__ a, long long p,
-                                           const Col27& q) {
+                                           const Col27& q, double one) {
   Plane27 r;
   r.c = a[p];
-  r.e = sgn27(a[p + q.xm], q.fxm) + sgn27(a[p + q.xp], q.fxp) + sgn27(a[p + q.ym], q.fym) +
-        sgn27(a[p + q.yp], q.fyp);
-  r.k = sgn27(a[p + q.xm + q.ym], q.fxm ^ q.fym) + sgn27(a[p + q.xp + q.ym], q.fxp ^ q.fym) +
-        sgn27(a[p + q.xm + q.yp], q.fxm ^ q.fyp) + sgn27(a[p + q.xp + q.yp], q.fxp ^ q.fyp);
+  r.e = fma(sgn27(a[p + q.xm], q.fxm), one, sgn27(a[p + q.xp], q.fxp));
+  r.e = fma(sgn27(a[p + q.ym], q.fym), one, r.e);
+  r.e = fma(sgn27(a[p + q.yp], q.fyp), one, r.e);
+  r.k = fma(sgn27(a[p + q.xm + q.ym], q.fxm ^ q.fym), one,
+            sgn27(a[p + q.xp + q.ym], q.fxp ^ q.fym));
+  r.k = fma(sgn27(a[p + q.xm + q.yp], q.fxm ^ q.fyp), one, r.k);
+  r.k = fma(sgn27(a[p + q.xp + q.yp], q.fxp ^ q.fyp), one, r.k);
   return r;
 }
 
-__device__ __forceinline__ Plane27 neg27(Plane27 p) { return Plane27{-p.c, -p.e, -p.k}; }
+__device__ __forceinline__ Plane27 neg27(Plane27 p) {
+  return Plane27{sgn27(p.c, true), sgn27(p.e, true), sgn27(p.k, true)};
+}
 
 __device__ __forceinline__ bool ztile27(const BoxDesc& B, int nplane, int& x, int& y, int& z0,
                                         int& z1) {
@@ -264,17 +279,17 @@ __device__ __forceinline__ bool ztile27(const BoxDesc& B, int nplane, int& x, in
   return iy < ey && z0 < z1;
 }
 
-// mode 0: r = D^-1 (f - A u) (the smoother's residual);
-// mode 1: u += a r + bf F(r) + be E(r) + bc C(r) (the degree-2 update; here
-//         `a_in` is r and `u` is updated);
-// mode 2: out = f - A u (the plain residual).
+// With nb = cf F + ce E + cc C over the neighbour classes of a_in:
+// mode 0: out = f c0 - a_in + nb        (r = D^-1 (f - A u), a_in = u);
+// mode 1: out += c0 a_in + nb           (u += a r - c2 W r, a_in = r, out = u);
+// mode 2: out = f + c0 a_in + nb        (r = f - A u with c0 = -w0 n^2).
 template <int kMode>
 __global__ void __launch_bounds__(kZ27Threads) k27_column(LevelView L,
                                                           const double* __restrict__ a_in,
                                                           double* __restrict__ out,
                                                           FieldT<double> f, double c0,
                                                           double cf, double ce, double cc,
-                                                          int nplane) {
+                                                          double one, int nplane) {
   __shared__ BoxDesc B, FB;
   if (threadIdx.x == 0) {
     B = L.boxes[blockIdx.y];
@@ -288,21 +303,22 @@ __global__ void __launch_bounds__(kZ27Threads) k27_column(LevelView L,
   long long p = at27(B, x, y, z0);
   long long fp = at27(FB, x, y, z0);
   const long long fsz = FB.sz;
-  Plane27 pc = plane27(a_in, p, q);
-  Plane27 pm = (z0 > 0) ? plane27(a_in, p - sz, q) : neg27(pc);
+  Plane27 pc = plane27(a_in, p, q, one);
+  Plane27 pm = (z0 > 0) ? plane27(a_in, p - sz, q, one) : neg27(pc);
   for (int z = z0; z < z1; ++z) {
-    const Plane27 pp = (z < L.nz - 1) ? plane27(a_in, p + sz, q) : neg27(pc);
-    const double F = pc.e + pm.c + pp.c;
-    const double E = pc.k + pm.e + pp.e;
-    const double C = pm.k + pp.k;
-    const double nb = cf * F + ce * E + cc * C;
+    const Plane27 pp = (z < L.nz - 1) ? plane27(a_in, p + sz, q, one) : neg27(pc);
+    const double F = fma(pp.c, one, fma(pm.c, one, pc.e));
+    const double E = fma(pp.e, one, fma(pm.e, one, pc.k));
+    const double C = fma(pm.k, one, pp.k);
+    double base;
     if (kMode == 0) {
-      out[p] = f.p[fp] * c0 - pc.c + nb;
+      base = fma(f.p[fp], c0, sgn27(pc.c, true));
     } else if (kMode == 1) {
-      out[p] += c0 * pc.c + nb;
+      base = fma(c0, pc.c, out[p]);
     } else {
-      out[p] = f.p[fp] - (c0 * pc.c - nb);
+      base = fma(c0, pc.c, f.p[fp]);
     }
+    out[p] = fma(cc, C, fma(ce, E, fma(cf, F, base)));
     pm = pc;
     pc = pp;
     p += sz;
@@ -370,7 +386,7 @@ double sq27(int n) { return (double)n * (double)n; }
 cudaError_t launch27_cheb_residual(const LevelView& L, const double* u, double* r,
                                    FieldT<double> f, W27 w, cudaStream_t s) {
   k27_column<0><<<zgrid27(L), kZ27Threads, 0, s>>>(L, u, r, f, 1.0 / (w.w0 * sq27(L.n)),
-                                                   w.w1 / w.w0, w.w2 / w.w0, w.w3 / w.w0,
+                                                   w.w1 / w.w0, w.w2 / w.w0, w.w3 / w.w0, 1.0,
                                                    nplane27(L));
   return cudaGetLastError();
 }
@@ -380,7 +396,7 @@ cudaError_t launch27_cheb2_update(const LevelView& L, double* u, const double* r
   // W r = (w1 sf + w2 se + w3 sc)/w0 enters with the factor -c2
   FieldT<double> none{nullptr, L.boxes, 0};
   k27_column<1><<<zgrid27(L), kZ27Threads, 0, s>>>(L, r, u, none, a, -c2 * w.w1 / w.w0,
-                                                   -c2 * w.w2 / w.w0, -c2 * w.w3 / w.w0,
+                                                   -c2 * w.w2 / w.w0, -c2 * w.w3 / w.w0, 1.0,
                                                    nplane27(L));
   return cudaGetLastError();
 }
@@ -388,8 +404,8 @@ cudaError_t launch27_cheb2_update(const LevelView& L, double* u, const double* r
 cudaError_t launch27_residual_zm(const LevelView& L, const double* u, FieldT<double> f,
                                  double* r, W27 w, cudaStream_t s) {
   const double n2 = sq27(L.n);
-  k27_column<2><<<zgrid27(L), kZ27Threads, 0, s>>>(L, u, r, f, n2 * w.w0, n2 * w.w1, n2 * w.w2,
-                                                   n2 * w.w3, nplane27(L));
+  k27_column<2><<<zgrid27(L), kZ27Threads, 0, s>>>(L, u, r, f, -n2 * w.w0, n2 * w.w1,
+                                                   n2 * w.w2, n2 * w.w3, 1.0, nplane27(L));
   return cudaGetLastError();
 }
 

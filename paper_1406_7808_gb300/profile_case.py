@@ -8,6 +8,10 @@ captures (ncu): each case runs a fixed, seeded workload once and exits.
       warm-up solves then one solve of the benchmark configuration (SR,
       32^3 segments, K = 3, J = 8; --plain without segments; --mixed in the
       mixed-precision mode)
+  python -m paper_1406_7808_gb300.profile_case smooth27 --n 256
+      one degree-2 smoothing with the 27-point operator ((14,3,1)/30) on the
+      paper's domain [0,2]x[0,1]^2 with n cells per unit length (two
+      column-form kernels)
 """
 import argparse
 import os
@@ -24,7 +28,7 @@ def main():
     from paper_1406_7808_gb300 import build, inputs, srfmg
 
     p = argparse.ArgumentParser()
-    p.add_argument("case", choices=["smooth", "solve"])
+    p.add_argument("case", choices=["smooth", "solve", "smooth27"])
     p.add_argument("--n", type=int, default=256)
     p.add_argument("--plain", action="store_true")
     p.add_argument("--mixed", action="store_true")
@@ -32,6 +36,13 @@ def main():
     a = p.parse_args()
     build.build()
     torch.cuda.set_device(0)
+    if a.case == "smooth27":
+        f, _ = inputs.paper_problem(a.n)
+        ft = torch.from_numpy(f).cuda()
+        u = torch.zeros_like(ft)
+        srfmg.op_smooth(u, ft, 2, lengths=(2, 1, 1), stencil=27)
+        torch.cuda.synchronize()
+        return
     f, _ = inputs.manufactured(a.n, 0)
     ft = torch.from_numpy(f).cuda()
     if a.case == "smooth":
