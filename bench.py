@@ -154,9 +154,15 @@ def cpu_baseline(f, min_seconds=10.0, max_solves=6):
         if time.perf_counter() - t_start >= min_seconds:
             break
     mean = sum(times) / len(times)
+    # one more solve on a single thread (the oracle's segment loop serialised)
+    t0 = time.perf_counter()
+    oracle.solve(f, n_threads=1, **SR)
+    single = time.perf_counter() - t0
     return u, {"value": N ** 3 / mean, "unit": "DOF/s", "cores": threads, "kind": "oracle",
+               "single_thread_dof_s": N ** 3 / single,
                "sample": f"{len(times)} full {N}^3 SR-FMG oracle solves (same f and geometry), "
-                         f"OpenMP over segments, mean {mean:.2f} s per solve"}
+                         f"OpenMP over segments, mean {mean:.2f} s per solve; plus one "
+                         f"single-thread solve ({single:.2f} s)"}
 
 
 def run_reference(args):

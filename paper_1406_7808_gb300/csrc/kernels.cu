@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
 constexpr int kPZChunk = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_prolong(LevelView C, const T* __restrict__ uc,
+__global__ void __launch_bounds__(kThreads, 3) k_prolong(LevelView C, const T* __restrict__ uc,
                                                       LevelView F, T* __restrict__ uf, int add,
                                                       T three, T w64, int nplane, Fk<T> k) {
   __shared__ BoxDesc B, CB;

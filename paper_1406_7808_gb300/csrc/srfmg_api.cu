@@ -21,6 +21,7 @@
 //   pass 1: u = S32(f);  pass p > 1: d = f - A u (float64), u += S32(d).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -61,6 +62,12 @@ template <typename T>
 struct Hier {
   std::vector<Level<T>> glev;  // global levels, glev[G-1] is level 0
   std::vector<Level<T>> slev;  // SR levels, slev[k], k = 1..K
+  // The finest level's boxes cut to what its genuine cells still depend on
+  // in the last operations of the solve (final correction and the degree-2
+  // post-smoother of the last stage): trim_r has the genuine region grown by
+  // one as compute region and grown by two as prolongation range, trim_u the
+  // genuine region as compute region (clipped to the full regions).
+  Geom trim_r, trim_u;
 };
 
 struct Cheb {
@@ -536,6 +543,25 @@ int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
     L.hboxes = boxes;
     int rc = finish_level(h, L);
     if (rc) return rc;
+    if (k == K) {
+      H.trim_r.n = H.trim_u.n = L.n;
+      for (int d = 0; d < 3; ++d) H.trim_r.nd[d] = H.trim_u.nd[d] = L.nd[d];
+      H.trim_r.hboxes = H.trim_u.hboxes = boxes;
+      for (size_t i = 0; i < boxes.size(); ++i) {
+        BoxDesc& r = H.trim_r.hboxes[i];
+        BoxDesc& u = H.trim_u.hboxes[i];
+        for (int d = 0; d < 3; ++d) {
+          r.lo[d] = std::max(r.lo[d], r.glo[d] - 1);
+          r.hi[d] = std::min(r.hi[d], r.ghi[d] + 1);
+          r.plo[d] = std::max(r.plo[d], r.glo[d] - 2);
+          r.phi[d] = std::min(r.phi[d], r.ghi[d] + 2);
+          u.lo[d] = u.glo[d];
+          u.hi[d] = u.ghi[d];
+        }
+      }
+      if ((rc = finish_level(h, H.trim_r))) return rc;
+      if ((rc = finish_level(h, H.trim_u))) return rc;
+    }
     const size_t elems = (size_t)slot * boxes.size();
     if ((rc = dalloc(h, &L.u, elems))) return rc;
     if ((rc = dalloc(h, &L.r, elems))) return rc;
@@ -776,9 +802,23 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
       const Level<T>& C = (j == 1) ? L0 : H.slev[j - 1];
       LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
              launch_diff<T>(C.view, C.u, C.t, C.rho, s));
+      const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
+      if (j == K && h->post.nu == 2) {
+        // the solve's last operations on the finest level: only the genuine
+        // cells are returned, and after the correction they depend on u
+        // within two cells and on r within one cell of them, so the
+        // correction, the residual and the update run on those regions only
+        // (every genuine value is computed exactly as on the full box)
+        LAUNCH(h, kind_of<T>(kProlongAdd), H.trim_r.tot_prolong, 26.0 / 8.0, 2.125 * w, s,
+               launch_prolong<T>(C.view, C.rho, H.trim_r.view, Lj.u, 1, s));
+        LAUNCH(h, kind_of<T>(kChebResidual), H.trim_r.tot_cells, ops_smooth(h), 3 * w, s,
+               op_cheb_residual<T>(h, H.trim_r.view, Lj.u, Lj.r, rhs, s));
+        LAUNCH(h, kind_of<T>(kCheb2Update), H.trim_u.tot_cells, ops_smooth(h), 3 * w, s,
+               op_cheb2_update<T>(h, H.trim_u.view, Lj.u, Lj.r, h->post, s));
+        continue;
+      }
       LAUNCH(h, kind_of<T>(kProlongAdd), Lj.tot_prolong, 26.0 / 8.0, 2.125 * w, s,
              launch_prolong<T>(C.view, C.rho, Lj.view, Lj.u, 1, s));
-      const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
       rc = smooth(h, Lj, h->post, Lj.u, rhs, s);
       if (rc) return rc;
     }
