@@ -22,9 +22,9 @@
 //     recurrence (19);
 //   - the residual of the 8 children of a coarse cell is summed through the
 //     24 faces of the 2x2x2 block (41 operations per coarse cell instead of 72);
-//   - trilinear interpolation runs per coarse cell over its 2x2x2 children as
-//     three separable passes of 3a + b (about 9 operations per fine cell for
-//     the correction instead of 16).
+//   - trilinear interpolation walks fine z-columns and forms each coarse
+//     plane's bilinear (x, y) value once per column, so a fine cell costs
+//     about 3.5 operations for the correction instead of 16.
 #include "srfmg_internal.cuh"
 
 namespace srfmg {
@@ -496,137 +496,6 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
   }
 }
 
-// Trilinear prolongation.  With 1D weights 3/4 (own coarse cell) and 1/4
-// (neighbour on the child's side), a child is (1/64) x the x, y, z passes of
-// 3 a + b.  Each thread owns a coarse (x, y) column of the fine box's
-// prolongation range and walks a chunk of coarse z: for every coarse plane it
-// reads the 3x3 neighbourhood once and forms the 2x2 (x, y)-interpolated
-// values; a child in z combines the plane of its coarse cell with the plane
-// on its side.  add == 0: uf = P uc;  add == 1: uf += P uc.  Coarse cells
-// outside the domain are mirrored with a sign flip; a coarse value is read
-// only if a child inside the fine range needs it.
-constexpr int kPZChunk = 4;
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) k_prolong(LevelView C, const T* __restrict__ uc,
-                                                      LevelView F, T* __restrict__ uf, int add,
-                                                      T three, T w64, int nplane, Fk<T> k) {
-  __shared__ BoxDesc B, CB;
-  if (threadIdx.x == 0) {
-    B = F.boxes[blockIdx.y];
-    CB = (C.nbox == 1) ? C.boxes[0] : C.boxes[blockIdx.y];
-  }
-  __syncthreads();
-  int plo[3], phi[3], clo[3], cex[3];
-  region_of(B, kProlong, plo, phi);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    clo[d] = plo[d] >> 1;
-    cex[d] = ((phi[d] - 1) >> 1) + 1 - clo[d];
-  }
-  const int tz = blockIdx.x / nplane, pb = blockIdx.x - tz * nplane;
-  const int i = pb * kThreads + threadIdx.x;
-  const int iy = i / cex[0];
-  if (iy >= cex[1]) return;
-  const int X = clo[0] + (i - iy * cex[0]), Y = clo[1] + iy;
-  const int Z0 = clo[2] + tz * kPZChunk;
-  const int Z1 = min(Z0 + kPZChunk, clo[2] + cex[2]);
-  if (Z0 >= Z1) return;
-  const int ncx = C.nx, ncy = C.ny, ncz = C.nz;
-  // columns of the 3x3 neighbourhood: mirrored index, sign flip, needed?
-  int xi[3], yi[3];
-  bool fx[3], fy[3], nx[3], ny[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    int x = X + d - 1, y = Y + d - 1;
-    fx[d] = x < 0 || x >= ncx;
-    fy[d] = y < 0 || y >= ncy;
-    xi[d] = x < 0 ? 0 : (x >= ncx ? ncx - 1 : x);
-    yi[d] = y < 0 ? 0 : (y >= ncy ? ncy - 1 : y);
-  }
-  nx[0] = 2 * X >= plo[0];
-  nx[1] = true;
-  nx[2] = 2 * X + 1 < phi[0];
-  ny[0] = 2 * Y >= plo[1];
-  ny[1] = true;
-  ny[2] = 2 * Y + 1 < phi[1];
-  // 2x2 (x, y)-interpolated values of coarse plane Z (unscaled)
-  auto plane = [&](int Z, T q[2][2]) {
-    const bool fz = Z < 0 || Z >= ncz;
-    const int zi = Z < 0 ? 0 : (Z >= ncz ? ncz - 1 : Z);
-    T px[3][2];
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-      T v[3];
-#pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        T val = k.zero;
-        if (nx[dx] && ny[dy]) val = neg_if(uc[at(CB, xi[dx], yi[dy], zi)], fx[dx] ^ fy[dy] ^ fz);
-        v[dx] = val;
-      }
-      px[dy][0] = fma(three, v[1], v[0]);
-      px[dy][1] = fma(three, v[1], v[2]);
-    }
-#pragma unroll
-    for (int cx = 0; cx < 2; ++cx) {
-      q[0][cx] = fma(three, px[1][cx], px[0][cx]);
-      q[1][cx] = fma(three, px[1][cx], px[2][cx]);
-    }
-  };
-  T qm[2][2], qc[2][2], qp[2][2];
-  if (2 * Z0 >= plo[2]) {
-    plane(Z0 - 1, qm);
-  } else {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) qm[a / 2][a % 2] = k.zero;
-  }
-  plane(Z0, qc);
-  for (int Z = Z0; Z < Z1; ++Z) {
-    // the fine values this step updates, loaded before the arithmetic
-    T old[2][2][2];
-#pragma unroll
-    for (int cz = 0; cz < 2; ++cz)
-#pragma unroll
-      for (int cy = 0; cy < 2; ++cy)
-#pragma unroll
-        for (int cx = 0; cx < 2; ++cx) {
-          const int fz = 2 * Z + cz, fy = 2 * Y + cy, fxx = 2 * X + cx;
-          const bool in = fz >= plo[2] && fz < phi[2] && fy >= plo[1] && fy < phi[1] &&
-                          fxx >= plo[0] && fxx < phi[0];
-          old[cz][cy][cx] = (add && in) ? uf[at(B, fxx, fy, fz)] : k.zero;
-        }
-    const bool odd_in = 2 * Z + 1 < phi[2];
-    if (odd_in) {
-      plane(Z + 1, qp);
-    } else {
-#pragma unroll
-      for (int a = 0; a < 4; ++a) qp[a / 2][a % 2] = k.zero;
-    }
-#pragma unroll
-    for (int cz = 0; cz < 2; ++cz) {
-      const int fz = 2 * Z + cz;
-      if (fz < plo[2] || fz >= phi[2]) continue;
-#pragma unroll
-      for (int cy = 0; cy < 2; ++cy) {
-        const int fy = 2 * Y + cy;
-        if (fy < plo[1] || fy >= phi[1]) continue;
-#pragma unroll
-        for (int cx = 0; cx < 2; ++cx) {
-          const int fxx = 2 * X + cx;
-          if (fxx < plo[0] || fxx >= phi[0]) continue;
-          const T e = fma(three, qc[cy][cx], cz == 0 ? qm[cy][cx] : qp[cy][cx]);
-          uf[at(B, fxx, fy, fz)] = fma(w64, e, old[cz][cy][cx]);
-        }
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      qm[a / 2][a % 2] = qc[a / 2][a % 2];
-      qc[a / 2][a % 2] = qp[a / 2][a % 2];
-    }
-  }
-}
-
 // e = u - t on every stored cell of the boxes that lies inside the domain
 // (compute cells and frozen SR ghosts): the coarse-grid correction w - t of
 // the FAS V-cycle, ready for prolongation
@@ -822,6 +691,155 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(long long cells, const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// float32 forms of the transfer and pointwise passes.  In the mixed mode these
+// kernels move float32 data at HBM speed and their arithmetic is cheap, so
+// they are written for memory-level parallelism: one thread per fine cell
+// for the prolongation (8 coarse reads through L1, 8 FMA), and z-columns of
+// kZChunk cells per thread over a box region for the pointwise passes.
+
+// region [lo, hi) of box B as z-columns: thread -> (x, y) of the flattened
+// region plane, blockIdx.x -> (plane block, z chunk)
+__device__ __forceinline__ bool zcolumn(const int lo[3], const int hi[3], int nplane, int& x,
+                                        int& y, int& z0, int& z1) {
+  const int tz = blockIdx.x / nplane, pb = blockIdx.x - tz * nplane;
+  const int ex = hi[0] - lo[0], ey = hi[1] - lo[1];
+  if (ex <= 0 || ey <= 0) return false;
+  const int i = pb * kZThreads + threadIdx.x;
+  const int iy = i / ex;
+  x = lo[0] + (i - iy * ex);
+  y = lo[1] + iy;
+  z0 = lo[2] + tz * kZChunk;
+  z1 = min(z0 + kZChunk, hi[2]);
+  return iy < ey && z0 < z1;
+}
+
+// trilinear prolongation in fine z-columns: a thread owns a fine (x, y) of
+// the box's prolongation range and walks kZChunk fine cells in z.  Its two
+// coarse columns per dimension are the fine cell's own coarse cell and the
+// neighbour on its side (mirrored with a sign flip outside the domain); for
+// every coarse plane it meets it forms the bilinear (x, y) value once
+// (4 reads, 3 FMA, weights 3/4 and 1/4 as 3 a + b), and a fine cell combines
+// the plane of its own coarse cell with the one on its side (1 FMA) and is
+// scaled by 1/64 into uf (add == 0: uf = P uc;  add == 1: uf += P uc).
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_prolong_zcol(LevelView C, const T* __restrict__ uc,
+                                                            LevelView F, T* __restrict__ uf,
+                                                            int add, T three, T w64, int nplane,
+                                                            Fk<T> k) {
+  __shared__ BoxDesc B, CB;
+  if (threadIdx.x == 0) {
+    B = F.boxes[blockIdx.y];
+    CB = (C.nbox == 1) ? C.boxes[0] : C.boxes[blockIdx.y];
+  }
+  __syncthreads();
+  int lo[3], hi[3];
+  region_of(B, kProlong, lo, hi);
+  int x, y, z0, z1;
+  if (!zcolumn(lo, hi, nplane, x, y, z0, z1)) return;
+  // coarse columns and their offsets within the coarse box
+  const int X0 = x >> 1, Y0 = y >> 1;
+  int Xo = (x & 1) ? X0 + 1 : X0 - 1, Yo = (y & 1) ? Y0 + 1 : Y0 - 1;
+  const bool fx = Xo < 0 || Xo >= C.nx, fy = Yo < 0 || Yo >= C.ny;
+  const long long dx = fx ? 0 : Xo - X0, dy = fy ? 0 : (long long)(Yo - Y0) * CB.sy;
+  // bilinear value of coarse plane Z (mirrored plane outside the domain)
+  auto plane = [&](int Z) -> T {
+    const bool fz = Z < 0 || Z >= C.nz;
+    const int Zi = fz ? (Z < 0 ? 0 : C.nz - 1) : Z;
+    const long long b0 = at(CB, X0, Y0, Zi);
+    const T a = fma(three, uc[b0], neg_if(uc[b0 + dx], fx));
+    const T b = fma(three, neg_if(uc[b0 + dy], fy), neg_if(uc[b0 + dy + dx], fx ^ fy));
+    return neg_if(fma(three, a, b), fz);
+  };
+  // walk the coarse planes Z of the chunk: the even fine cell 2Z combines
+  // plane Z with Z-1, the odd one 2Z+1 with Z+1; every plane is formed once,
+  // and only planes some cell of the chunk needs are read
+  const int Zlo = z0 >> 1, Zhi = (z1 - 1) >> 1;
+  T pm = (z0 & 1) ? k.zero : plane(Zlo - 1);
+  T pc = plane(Zlo);
+  const long long sz = B.sz;
+  long long o = at(B, x, y, 2 * Zlo);
+#pragma unroll 2
+  for (int Zc = Zlo; Zc <= Zhi; ++Zc, o += 2 * sz) {
+    const int fe = 2 * Zc, fo = fe + 1;
+    const bool we = fe >= z0, wo = fo < z1;
+    const T pp = wo ? plane(Zc + 1) : k.zero;
+    const T oe = (add && we) ? uf[o] : k.zero;
+    const T oo = (add && wo) ? uf[o + sz] : k.zero;
+    if (we) uf[o] = fma(w64, fma(three, pc, pm), oe);
+    if (wo) uf[o + sz] = fma(w64, fma(three, pc, pp), oo);
+    pm = pc;
+    pc = pp;
+  }
+}
+
+// d = alpha d + beta r (alpha == 0: d = beta r); u += d, over the compute
+// region in z-columns
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_cheb_step_zm(LevelView L, T* __restrict__ u,
+                                                            T* __restrict__ d,
+                                                            const T* __restrict__ r, T alpha,
+                                                            T beta, int write_d, int nplane) {
+  __shared__ BoxDesc B;
+  if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
+  __syncthreads();
+  int x, y, z0, z1;
+  if (!zcolumn(B.lo, B.hi, nplane, x, y, z0, z1)) return;
+  const bool use_d = alpha != T(0);
+  long long c = at(B, x, y, z0);
+#pragma unroll 4
+  for (int z = z0; z < z1; ++z, c += B.sz) {
+    T dn = beta * r[c];
+    if (use_d) dn = fma(alpha, d[c], dn);
+    if (write_d) d[c] = dn;
+    u[c] += dn;
+  }
+}
+
+// e = u - t on the stored cells of the box inside the domain, in z-columns
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_diff_zm(LevelView C, const T* __restrict__ u,
+                                                       const T* __restrict__ t,
+                                                       T* __restrict__ e, int nplane) {
+  __shared__ BoxDesc B;
+  if (threadIdx.x == 0) B = C.boxes[blockIdx.y];
+  __syncthreads();
+  const int nd[3] = {C.nx, C.ny, C.nz};
+  const bool shell = B.ox < B.lo[0];
+  int lo[3], hi[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = shell ? max(B.lo[d] - 1, 0) : B.lo[d];
+    hi[d] = shell ? min(B.hi[d] + 1, nd[d]) : B.hi[d];
+  }
+  int x, y, z0, z1;
+  if (!zcolumn(lo, hi, nplane, x, y, z0, z1)) return;
+  long long c = at(B, x, y, z0);
+#pragma unroll 4
+  for (int z = z0; z < z1; ++z, c += B.sz) e[c] = u[c] - t[c];
+}
+
+// genuine cells of the box into the global float64 array (out = u or
+// out += u), in z-columns
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_gather_zm(LevelView L, const T* __restrict__ u,
+                                                         double* __restrict__ out, int add,
+                                                         int nplane, Fk<double> k) {
+  __shared__ BoxDesc B;
+  if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
+  __syncthreads();
+  int x, y, z0, z1;
+  if (!zcolumn(B.glo, B.ghi, nplane, x, y, z0, z1)) return;
+  const long long pz = (long long)L.nx * L.ny;
+  long long c = at(B, x, y, z0);
+  long long o = (long long)z0 * pz + (long long)y * L.nx + x;
+#pragma unroll 4
+  for (int z = z0; z < z1; ++z, c += B.sz, o += pz) {
+    const double v = widen(u[c]);
+    out[o] = add ? fma(v, k.one, out[o]) : v;
+  }
+}
+
 dim3 grid_for(const LevelView& L, int cells) {
   int bx = (cells + kThreads - 1) / kThreads;
   if (bx < 1) bx = 1;
@@ -846,6 +864,13 @@ ZTiles ztiles(const LevelView& L) {
 
 dim3 zgrid(const LevelView& L, ZTiles t) {
   return dim3((unsigned)(t.nplane * t.nzc), (unsigned)L.nbox, 1);
+}
+
+// z-column tiling of a region no larger than the compute region grown by
+// one cell on every side (the stored region)
+ZTiles ztiles_stored(const LevelView& L) {
+  const int plane = (L.max_ex + 2) * (L.max_ey + 2);
+  return ZTiles{(plane + kZThreads - 1) / kZThreads, (L.max_ez + 2 + kZChunk - 1) / kZChunk};
 }
 
 // float64: per-cell form; float32: column form
@@ -878,8 +903,14 @@ cudaError_t launch_cheb2_update(const LevelView& L, T* u, const T* r, double a, 
 template <typename T>
 cudaError_t launch_cheb_step(const LevelView& L, T* u, T* d, const T* r, double alpha,
                              double beta, int write_d, cudaStream_t s) {
-  k_cheb_step<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, d, r, T(alpha), T(beta),
-                                                               write_d, fk<T>());
+  if (sizeof(T) == 8) {
+    k_cheb_step<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, d, r, T(alpha), T(beta),
+                                                                 write_d, fk<T>());
+  } else {
+    const ZTiles t = ztiles(L);
+    k_cheb_step_zm<T><<<zgrid(L, t), kZThreads, 0, s>>>(L, u, d, r, T(alpha), T(beta), write_d,
+                                                        t.nplane);
+  }
   return cudaGetLastError();
 }
 
@@ -927,19 +958,20 @@ cudaError_t launch_transition_rhs(const LevelView& C, const T* t, const T* rho, 
 template <typename T>
 cudaError_t launch_prolong(const LevelView& C, const T* uc, const LevelView& F, T* uf, int add,
                            cudaStream_t s) {
-  // coarse columns: every fine box's prolongation range spans at most
-  // max_e + 2 fine cells per side, i.e. max_e / 2 + 2 coarse cells
-  const int cx = F.max_ex / 2 + 2, cy = F.max_ey / 2 + 2, cz = F.max_ez / 2 + 2;
-  const int nplane = (cx * cy + kThreads - 1) / kThreads;
-  const int nzc = (cz + kPZChunk - 1) / kPZChunk;
-  k_prolong<T><<<dim3((unsigned)(nplane * nzc), (unsigned)F.nbox), kThreads, 0, s>>>(
-      C, uc, F, uf, add, T(3.0), T(1.0 / 64.0), nplane, fk<T>());
+  const ZTiles z = ztiles_stored(F);  // the prolongation range lies in the stored region
+  k_prolong_zcol<T><<<zgrid(F, z), kZThreads, 0, s>>>(C, uc, F, uf, add, T(3.0), T(1.0 / 64.0),
+                                                      z.nplane, fk<T>());
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaStream_t s) {
-  k_diff<T><<<grid_for(C, C.max_stored), kThreads, 0, s>>>(C, u, t, e, T(-1.0));
+  if (sizeof(T) == 8) {
+    k_diff<T><<<grid_for(C, C.max_stored), kThreads, 0, s>>>(C, u, t, e, T(-1.0));
+  } else {
+    const ZTiles z = ztiles_stored(C);
+    k_diff_zm<T><<<zgrid(C, z), kZThreads, 0, s>>>(C, u, t, e, z.nplane);
+  }
   return cudaGetLastError();
 }
 
@@ -965,8 +997,13 @@ cudaError_t launch_restrict_global(Dims fd, const T* ff, T* fc, int check, unsig
 template <typename T>
 cudaError_t launch_gather_genuine(const LevelView& L, const T* u, double* out, int add,
                                   cudaStream_t s) {
-  k_gather_genuine<T><<<grid_for(L, L.max_genuine), kThreads, 0, s>>>(L, u, out, add,
-                                                                      fk<double>());
+  if (sizeof(T) == 8) {
+    k_gather_genuine<T><<<grid_for(L, L.max_genuine), kThreads, 0, s>>>(L, u, out, add,
+                                                                        fk<double>());
+  } else {
+    const ZTiles z = ztiles(L);  // the genuine region lies inside the compute region
+    k_gather_zm<T><<<zgrid(L, z), kZThreads, 0, s>>>(L, u, out, add, z.nplane, fk<double>());
+  }
   return cudaGetLastError();
 }
 

@@ -696,7 +696,7 @@ int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStrea
   if (rc) return rc;
   LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
          launch_diff<T>(C.view, C.u, C.t, C.rho, s));
-  LAUNCH(h, kind_of<T>(kProlongAdd), L.tot_prolong, 26.0 / 8.0, 2.125 * w, s,
+  LAUNCH(h, kind_of<T>(kProlongAdd), L.tot_prolong, 3.75, 2.125 * w, s,
          launch_prolong<T>(C.view, C.rho, L.view, u, 1, s));
   return smooth(h, L, h->post, u, rhs, s);
 }
@@ -718,7 +718,7 @@ int run_fmg_global(sr_fmg_s* h, Hier<T>& H, const T* ftop, T* utop, cudaStream_t
   const double w = sizeof(T);
   for (int g = 1; g <= top; ++g) {
     Level<T>& L = H.glev[g];
-    LAUNCH(h, kind_of<T>(kProlongSet), L.tot_prolong, 26.0 / 8.0, 1.125 * w, s,
+    LAUNCH(h, kind_of<T>(kProlongSet), L.tot_prolong, 3.75, 1.125 * w, s,
            launch_prolong<T>(H.glev[g - 1].view, ug(g - 1), L.view, ug(g), 0, s));
     FieldT<T> f = view_global<T>(L, fg(g));
     int rc = smooth(h, L, h->fmg, ug(g), f, s);
@@ -769,7 +769,7 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
     // u_k <- Pi u_{k-1} on Omega^C_k u Omega^GSR_k, then S^alpha on Omega^C_k
     {
       const Level<T>& C = (k == 1) ? L0 : H.slev[k - 1];
-      LAUNCH(h, kind_of<T>(kProlongSet), Lk.tot_prolong, 26.0 / 8.0, 1.125 * w, s,
+      LAUNCH(h, kind_of<T>(kProlongSet), Lk.tot_prolong, 3.75, 1.125 * w, s,
              launch_prolong<T>(C.view, C.u, Lk.view, Lk.u, 0, s));
       int rc = smooth(h, Lk, h->fmg, Lk.u, fview(k), s);
       if (rc) return rc;
@@ -809,7 +809,7 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
         // within two cells and on r within one cell of them, so the
         // correction, the residual and the update run on those regions only
         // (every genuine value is computed exactly as on the full box)
-        LAUNCH(h, kind_of<T>(kProlongAdd), H.trim_r.tot_prolong, 26.0 / 8.0, 2.125 * w, s,
+        LAUNCH(h, kind_of<T>(kProlongAdd), H.trim_r.tot_prolong, 3.75, 2.125 * w, s,
                launch_prolong<T>(C.view, C.rho, H.trim_r.view, Lj.u, 1, s));
         LAUNCH(h, kind_of<T>(kChebResidual), H.trim_r.tot_cells, ops_smooth(h), 3 * w, s,
                op_cheb_residual<T>(h, H.trim_r.view, Lj.u, Lj.r, rhs, s));
@@ -817,7 +817,7 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
                op_cheb2_update<T>(h, H.trim_u.view, Lj.u, Lj.r, h->post, s));
         continue;
       }
-      LAUNCH(h, kind_of<T>(kProlongAdd), Lj.tot_prolong, 26.0 / 8.0, 2.125 * w, s,
+      LAUNCH(h, kind_of<T>(kProlongAdd), Lj.tot_prolong, 3.75, 2.125 * w, s,
              launch_prolong<T>(C.view, C.rho, Lj.view, Lj.u, 1, s));
       rc = smooth(h, Lj, h->post, Lj.u, rhs, s);
       if (rc) return rc;
