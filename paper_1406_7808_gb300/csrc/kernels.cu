@@ -290,28 +290,6 @@ __global__ void __launch_bounds__(kThreads) k_cheb2_update(LevelView L, T* __res
   }
 }
 
-// d = alpha d + beta r (alpha == 0: d = beta r); u += d
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_cheb_step(LevelView L, T* __restrict__ u,
-                                                        T* __restrict__ d,
-                                                        const T* __restrict__ r, T alpha, T beta,
-                                                        int write_d, Fk<T> k) {
-  __shared__ BoxDesc B;
-  if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
-  __syncthreads();
-  const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
-  const int ncell = ex * ey * ez;
-  const bool use_d = alpha != T(0);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
-    const Cell q = cell_of(i, B.lo, ex, ey);
-    const long long c = at(B, q.x, q.y, q.z);
-    T dn = fma(beta, r[c], k.zero);
-    if (use_d) dn = fma(alpha, d[c], dn);
-    if (write_d) d[c] = dn;
-    u[c] = fma(dn, k.one, u[c]);
-  }
-}
-
 // residual == 0: out = A u = n^2 (6 u - sum);  residual == 1: out = f - A u
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const T* __restrict__ u,
@@ -496,33 +474,6 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
   }
 }
 
-// e = u - t on every stored cell of the boxes that lies inside the domain
-// (compute cells and frozen SR ghosts): the coarse-grid correction w - t of
-// the FAS V-cycle, ready for prolongation
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_diff(LevelView C, const T* __restrict__ u,
-                                                   const T* __restrict__ t, T* __restrict__ e,
-                                                   T mone) {
-  __shared__ BoxDesc B;
-  if (threadIdx.x == 0) B = C.boxes[blockIdx.y];
-  __syncthreads();
-  const int nd[3] = {C.nx, C.ny, C.nz};
-  const bool shell = B.ox < B.lo[0];
-  int lo[3], hi[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    lo[d] = shell ? max(B.lo[d] - 1, 0) : B.lo[d];
-    hi[d] = shell ? min(B.hi[d] + 1, nd[d]) : B.hi[d];
-  }
-  const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
-  const int ncell = ex * ey * ez;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
-    const Cell q = cell_of(i, lo, ex, ey);
-    const long long c = at(B, q.x, q.y, q.z);
-    e[c] = fma(t[c], mone, u[c]);
-  }
-}
-
 // One warp per row of the dense inverse (float64 arithmetic).
 template <typename T>
 __global__ void k_coarse_solve(LevelView L, const double* __restrict__ minv, FieldT<T> f,
@@ -579,26 +530,6 @@ __global__ void __launch_bounds__(kThreads) k_restrict_global(Dims fd, const T* 
     fc[i] = s;
   }
   if (check && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_gather_genuine(LevelView L, const T* __restrict__ u,
-                                                             double* __restrict__ out, int add,
-                                                             Fk<double> k) {
-  __shared__ BoxDesc B;
-  if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
-  __syncthreads();
-  int lo[3], hi[3];
-  region_of(B, kGenuine, lo, hi);
-  const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
-  const int ncell = ex * ey * ez;
-  const long long nx = L.nx, ny = L.ny;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
-    const Cell q = cell_of(i, lo, ex, ey);
-    const long long o = (q.z * ny + q.y) * nx + q.x;
-    const double v = widen(u[at(B, q.x, q.y, q.z)]);
-    out[o] = add ? fma(v, k.one, out[o]) : v;
-  }
 }
 
 // d = float(f - A u) with float64 arithmetic, or d = float(f) without u
@@ -692,11 +623,10 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(long long cells, const 
 }
 
 // ---------------------------------------------------------------------------
-// float32 forms of the transfer and pointwise passes.  In the mixed mode these
-// kernels move float32 data at HBM speed and their arithmetic is cheap, so
-// they are written for memory-level parallelism: one thread per fine cell
-// for the prolongation (8 coarse reads through L1, 8 FMA), and z-columns of
-// kZChunk cells per thread over a box region for the pointwise passes.
+// The transfer and pointwise passes walk z-columns: a thread owns an (x, y)
+// of the region and kZChunk cells in z, which keeps many independent loads
+// in flight per thread (these passes are memory- or latency-bound in both
+// precisions) and amortises the index arithmetic.
 
 // region [lo, hi) of box B as z-columns: thread -> (x, y) of the flattened
 // region plane, blockIdx.x -> (plane block, z chunk)
@@ -773,13 +703,14 @@ __global__ void __launch_bounds__(kZThreads) k_prolong_zcol(LevelView C, const T
   }
 }
 
-// d = alpha d + beta r (alpha == 0: d = beta r); u += d, over the compute
-// region in z-columns
+// d = alpha d + beta r (alpha == 0: d = beta r); u += d (the Chebyshev
+// recurrence step for degrees other than 2), over the compute region
 template <typename T>
 __global__ void __launch_bounds__(kZThreads) k_cheb_step_zm(LevelView L, T* __restrict__ u,
                                                             T* __restrict__ d,
                                                             const T* __restrict__ r, T alpha,
-                                                            T beta, int write_d, int nplane) {
+                                                            T beta, int write_d, int nplane,
+                                                            Fk<T> k) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
@@ -789,18 +720,20 @@ __global__ void __launch_bounds__(kZThreads) k_cheb_step_zm(LevelView L, T* __re
   long long c = at(B, x, y, z0);
 #pragma unroll 4
   for (int z = z0; z < z1; ++z, c += B.sz) {
-    T dn = beta * r[c];
+    T dn = fma(beta, r[c], k.zero);
     if (use_d) dn = fma(alpha, d[c], dn);
     if (write_d) d[c] = dn;
-    u[c] += dn;
+    u[c] = fma(dn, k.one, u[c]);
   }
 }
 
-// e = u - t on the stored cells of the box inside the domain, in z-columns
+// e = u - t on every stored cell of the box inside the domain (compute
+// cells and frozen SR ghosts): the coarse-grid correction w - t of the FAS
+// V-cycle, ready for prolongation
 template <typename T>
 __global__ void __launch_bounds__(kZThreads) k_diff_zm(LevelView C, const T* __restrict__ u,
                                                        const T* __restrict__ t,
-                                                       T* __restrict__ e, int nplane) {
+                                                       T* __restrict__ e, int nplane, T mone) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[blockIdx.y];
   __syncthreads();
@@ -816,7 +749,7 @@ __global__ void __launch_bounds__(kZThreads) k_diff_zm(LevelView C, const T* __r
   if (!zcolumn(lo, hi, nplane, x, y, z0, z1)) return;
   long long c = at(B, x, y, z0);
 #pragma unroll 4
-  for (int z = z0; z < z1; ++z, c += B.sz) e[c] = u[c] - t[c];
+  for (int z = z0; z < z1; ++z, c += B.sz) e[c] = fma(t[c], mone, u[c]);
 }
 
 // genuine cells of the box into the global float64 array (out = u or
@@ -903,14 +836,9 @@ cudaError_t launch_cheb2_update(const LevelView& L, T* u, const T* r, double a, 
 template <typename T>
 cudaError_t launch_cheb_step(const LevelView& L, T* u, T* d, const T* r, double alpha,
                              double beta, int write_d, cudaStream_t s) {
-  if (sizeof(T) == 8) {
-    k_cheb_step<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, d, r, T(alpha), T(beta),
-                                                                 write_d, fk<T>());
-  } else {
-    const ZTiles t = ztiles(L);
-    k_cheb_step_zm<T><<<zgrid(L, t), kZThreads, 0, s>>>(L, u, d, r, T(alpha), T(beta), write_d,
-                                                        t.nplane);
-  }
+  const ZTiles t = ztiles(L);
+  k_cheb_step_zm<T><<<zgrid(L, t), kZThreads, 0, s>>>(L, u, d, r, T(alpha), T(beta), write_d,
+                                                      t.nplane, fk<T>());
   return cudaGetLastError();
 }
 
@@ -966,12 +894,8 @@ cudaError_t launch_prolong(const LevelView& C, const T* uc, const LevelView& F, 
 
 template <typename T>
 cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaStream_t s) {
-  if (sizeof(T) == 8) {
-    k_diff<T><<<grid_for(C, C.max_stored), kThreads, 0, s>>>(C, u, t, e, T(-1.0));
-  } else {
-    const ZTiles z = ztiles_stored(C);
-    k_diff_zm<T><<<zgrid(C, z), kZThreads, 0, s>>>(C, u, t, e, z.nplane);
-  }
+  const ZTiles z = ztiles_stored(C);
+  k_diff_zm<T><<<zgrid(C, z), kZThreads, 0, s>>>(C, u, t, e, z.nplane, T(-1.0));
   return cudaGetLastError();
 }
 
@@ -997,13 +921,8 @@ cudaError_t launch_restrict_global(Dims fd, const T* ff, T* fc, int check, unsig
 template <typename T>
 cudaError_t launch_gather_genuine(const LevelView& L, const T* u, double* out, int add,
                                   cudaStream_t s) {
-  if (sizeof(T) == 8) {
-    k_gather_genuine<T><<<grid_for(L, L.max_genuine), kThreads, 0, s>>>(L, u, out, add,
-                                                                        fk<double>());
-  } else {
-    const ZTiles z = ztiles(L);  // the genuine region lies inside the compute region
-    k_gather_zm<T><<<zgrid(L, z), kZThreads, 0, s>>>(L, u, out, add, z.nplane, fk<double>());
-  }
+  const ZTiles z = ztiles(L);  // the genuine region lies inside the compute region
+  k_gather_zm<T><<<zgrid(L, z), kZThreads, 0, s>>>(L, u, out, add, z.nplane, fk<double>());
   return cudaGetLastError();
 }
 
