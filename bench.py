@@ -207,6 +207,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """Largest value of x over the ranks of the job (the slowest rank's time);
+    x itself on a single rank."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank processes units_per_rank (replicas,
+    weak scaling), the job takes the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
+def rank_seed(rank):
+    """Seed of the manufactured problem a rank solves (replica r: seed r)."""
+    return SEED + rank
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -229,16 +252,12 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def ranks_max(x):
+        return max_over_ranks(x, world)
 
     # replicas: every rank solves its own instance (seeded by rank); no data
     # is exchanged between ranks
-    f, u_exact = inputs.manufactured(N, SEED + rank)
+    f, u_exact = inputs.manufactured(N, rank_seed(rank))
     ft = torch.from_numpy(f).cuda()
     ut = torch.empty_like(ft)
     name, J = workload_name()
@@ -257,7 +276,7 @@ def run_ours(args):
             torch.cuda.synchronize()
         solver.check()
         barrier()
-        return max_over_ranks(e0.elapsed_time(e1))
+        return ranks_max(e0.elapsed_time(e1))
 
     # graph mode: each solve is one captured CUDA graph (same kernels)
     sr = srfmg.Solver(N, graph=True, **SR)
@@ -269,7 +288,7 @@ def run_ours(args):
     total_ms = timed(sr, args.steps, sampler)
     clocks = sampler.summary()
     ms = total_ms / args.steps
-    value = world * N ** 3 / (ms / 1e3)
+    value = job_rate(N ** 3, world, ms / 1e3)
     launches = sr.launches_per_solve
 
     # per-kernel device times (a profiled repeat of the timed loop)
@@ -328,7 +347,7 @@ def run_ours(args):
 
         def vstep():
             _, vstate["cycles"], vstate["rel"] = plain.vsolve(ft, ut.zero_(), rtol=VSOLVE_RTOL)
-        vs_ms = max_over_ranks(_time_loop(vstep, args.steps, stream)) / args.steps
+        vs_ms = ranks_max(_time_loop(vstep, args.steps, stream)) / args.steps
         vs = {"rtol": VSOLVE_RTOL, "ms": vs_ms, "dof_s": world * N ** 3 / (vs_ms / 1e3),
               "cycles": vstate["cycles"], "rel_resid": vstate["rel"],
               "e": float(np.abs(ut.cpu().numpy() - u_exact).max())}
@@ -343,16 +362,16 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         sr.solve_host(fh.numpy(), uh.numpy())
-    e2e_s = max_over_ranks(time.perf_counter() - t0) / args.steps
+    e2e_s = ranks_max(time.perf_counter() - t0) / args.steps
     sr.close()
     del fh, uh
 
     mixed = batch = None
     paper = None
     if not args.no_extras:
-        mixed = measure_mixed(args, timed_fn=max_over_ranks, world=world, rank=rank)
-        batch = measure_batch(args, max_over_ranks, world)
-        paper = measure_paper(args, max_over_ranks, world)
+        mixed = measure_mixed(args, timed_fn=ranks_max, world=world, rank=rank)
+        batch = measure_batch(args, ranks_max, world)
+        paper = measure_paper(args, ranks_max, world)
 
     if rank != 0:
         if world > 1:
