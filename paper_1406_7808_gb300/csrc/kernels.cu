@@ -419,27 +419,13 @@ __global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView 
     FBx = (F.nbox == 1) ? F.boxes[0] : F.boxes[blockIdx.y];
   }
   __syncthreads();
-
-  const bool shell = B.ox < B.lo[0];
-  int lo[3], hi[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    lo[d] = shell ? B.lo[d] - 1 : B.lo[d];
-    hi[d] = shell ? B.hi[d] + 1 : B.hi[d];
-  }
-  const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
+  const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
   const int ncell = ex * ey * ez;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
-    const Cell q = cell_of(i, lo, ex, ey);
-    const bool inside_domain =
-        q.x >= 0 && q.x < C.nx && q.y >= 0 && q.y < C.ny && q.z >= 0 && q.z < C.nz;
-    if (!inside_domain) continue;
+    const Cell q = cell_of(i, B.lo, ex, ey);
     const long long c = at(B, q.x, q.y, q.z);
     const T uc = u[c];
     t[c] = uc;
-    const bool compute = q.x >= B.lo[0] && q.x < B.hi[0] && q.y >= B.lo[1] && q.y < B.hi[1] &&
-                         q.z >= B.lo[2] && q.z < B.hi[2];
-    if (!compute) continue;
     const bool inF = q.x >= FBx.rlo[0] && q.x < FBx.rhi[0] && q.y >= FBx.rlo[1] &&
                      q.y < FBx.rhi[1] && q.z >= FBx.rlo[2] && q.z < FBx.rhi[2];
     double v[6];
@@ -752,6 +738,37 @@ __global__ void __launch_bounds__(kZThreads) k_diff_zm(LevelView C, const T* __r
   for (int z = z0; z < z1; ++z, c += B.sz) e[c] = fma(t[c], mone, u[c]);
 }
 
+// t = u on the shell cells of every box that lie inside the domain (the
+// compute cells get t from k_coarse_rhs), in z-columns of the stored region:
+// a column on the ring of the stored plane copies its whole chunk, any other
+// column only the chunk's cells below or above the compute region
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_shell_copy(LevelView C, const T* __restrict__ u,
+                                                          T* __restrict__ t, int nplane) {
+  __shared__ BoxDesc B;
+  if (threadIdx.x == 0) B = C.boxes[blockIdx.y];
+  __syncthreads();
+  const int nd[3] = {C.nx, C.ny, C.nz};
+  int lo[3], hi[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = max(B.lo[d] - 1, 0);
+    hi[d] = min(B.hi[d] + 1, nd[d]);
+  }
+  int x, y, z0, z1;
+  if (!zcolumn(lo, hi, nplane, x, y, z0, z1)) return;
+  const bool ring = x < B.lo[0] || x >= B.hi[0] || y < B.lo[1] || y >= B.hi[1];
+  if (!ring) {  // only the cells outside the compute region in z
+    if (z0 >= B.lo[2]) z0 = max(z0, B.hi[2]);
+    if (z1 <= B.hi[2]) z1 = min(z1, B.lo[2]);
+  }
+  for (int z = z0; z < z1; ++z) {
+    if (!ring && z >= B.lo[2] && z < B.hi[2]) continue;
+    const long long c = at(B, x, y, z);
+    t[c] = u[c];
+  }
+}
+
 // genuine cells of the box into the global float64 array (out = u or
 // out += u), in z-columns
 template <typename T>
@@ -869,9 +886,16 @@ cudaError_t launch_resid_restrict(const LevelView& F, const T* u, FieldT<T> f,
 template <typename T>
 cudaError_t launch_coarse_rhs(const LevelView& C, const LevelView& F, const T* u, const T* rho,
                               T* rhs, T* t, cudaStream_t s) {
-  k_coarse_rhs<T><<<grid_for(C, C.max_stored), kThreads, 0, s>>>(C, F, u, rho, rhs, t,
-                                                                 6.0 * sq(C.n), -sq(C.n),
-                                                                 fk<double>());
+  k_coarse_rhs<T><<<grid_for(C, C.max_cells), kThreads, 0, s>>>(C, F, u, rho, rhs, t,
+                                                                6.0 * sq(C.n), -sq(C.n),
+                                                                fk<double>());
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_shell_copy(const LevelView& C, const T* u, T* t, cudaStream_t s) {
+  const ZTiles z = ztiles_stored(C);
+  k_shell_copy<T><<<zgrid(C, z), kZThreads, 0, s>>>(C, u, t, z.nplane);
   return cudaGetLastError();
 }
 
@@ -961,6 +985,7 @@ cudaError_t launch_accumulate(long long cells, const float* e, double* u, int ad
                                                 const LevelView&, T*, T*, cudaStream_t);       \
   template cudaError_t launch_coarse_rhs<T>(const LevelView&, const LevelView&, const T*,      \
                                             const T*, T*, T*, cudaStream_t);                   \
+  template cudaError_t launch_shell_copy<T>(const LevelView&, const T*, T*, cudaStream_t);     \
   template cudaError_t launch_transition_rhs<T>(const LevelView&, const T*, const T*, T*, T*,  \
                                                 cudaStream_t);                                 \
   template cudaError_t launch_prolong<T>(const LevelView&, const T*, const LevelView&, T*, int, \

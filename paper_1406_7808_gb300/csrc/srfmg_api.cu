@@ -84,7 +84,8 @@ enum Kind {
   kProlongSet, kProlongAdd, kCoarseSolve, kRestrictF, kGather, kApply,
   kChebResidualF32, kCheb2UpdateF32, kChebStepF32, kResidRestrictF32, kCoarseRhsMixed,
   kTransitionRhsMixed, kProlongSetF32, kProlongAddF32, kCoarseSolveMixed, kRestrictFF32,
-  kGatherMixed, kDefect, kAccumulate, kDiff, kDiffF32, kResidNorm, kKinds
+  kGatherMixed, kDefect, kAccumulate, kDiff, kDiffF32, kResidNorm, kShellCopy, kShellCopyF32,
+  kKinds
 };
 const char* const kKindName[kKinds] = {
   "cheb_residual", "cheb2_update", "cheb_step", "resid_restrict", "coarse_rhs",
@@ -93,13 +94,14 @@ const char* const kKindName[kKinds] = {
   "cheb_residual_f32", "cheb2_update_f32", "cheb_step_f32", "resid_restrict_f32",
   "coarse_rhs_mixed", "transition_rhs_mixed", "prolong_f32", "prolong_correct_f32",
   "coarse_solve_mixed", "restrict_f_f32", "gather_genuine_mixed", "defect", "accumulate",
-  "correction", "correction_f32", "resid_norm"};
+  "correction", "correction_f32", "resid_norm", "shell_copy", "shell_copy_f32"};
 
 // kind of a kernel for storage type T: float64 kinds shift to their float32
 // counterparts (same order)
 template <typename T>
 int kind_of(int k64) {
   if (k64 == kDiff) return sizeof(T) == 8 ? kDiff : kDiffF32;
+  if (k64 == kShellCopy) return sizeof(T) == 8 ? kShellCopy : kShellCopyF32;
   return sizeof(T) == 8 ? k64 : k64 + kChebResidualF32;
 }
 
@@ -384,6 +386,7 @@ int finish_level(sr_fmg_s* h, Geom& L) {
   v.nx = L.nd[0];
   v.ny = L.nd[1];
   v.nz = L.nd[2];
+  v.shell = !L.hboxes.empty() && L.hboxes[0].ox < L.hboxes[0].lo[0];
   for (const BoxDesc& b : L.hboxes) {
     const int slo[3] = {b.ox, b.oy, b.oz};
     int shi[3];
@@ -786,6 +789,9 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
         if (rc) return rc;
         LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h), 4 * w, s,
                op_coarse_rhs<T>(h, C.view, Lj.view, C.u, C.rho, C.rhs, C.t, s));
+        if (!h->op27)
+          LAUNCH(h, kind_of<T>(kShellCopy), C.tot_cells / 4, 0, 2 * w, s,
+                 launch_shell_copy<T>(C.view, C.u, C.t, s));
       } else {
         rc = resid_restrict<T>(h, Lj, Lj.u, rhs, L0, L0.t, L0.rho, s);
         if (rc) return rc;

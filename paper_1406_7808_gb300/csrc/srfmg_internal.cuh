@@ -47,6 +47,7 @@ struct LevelView {
   int max_restrict;      // largest restriction-target cell count
   int max_genuine;       // largest genuine-region cell count
   int max_ex, max_ey, max_ez;  // largest compute-region extents
+  int shell;             // 1: the boxes are stored with a one-cell shell (SR levels)
 };
 
 // A field read with a possibly different layout than the level's boxes (the
@@ -94,11 +95,15 @@ cudaError_t launch_resid_restrict(const LevelView& F, const T* u, FieldT<T> f,
                                   const LevelView& C, T* uhat_dst, T* rho_dst, cudaStream_t s);
 // Coarse right-hand side of the FAS cycle (Eq. eq:cresid2 and its SR form):
 // rhs = rho + A u inside the fine boxes' restriction region, rhs = A u on the
-// rest of the compute region; t = u on the whole stored box.  Arithmetic in
+// rest of the compute region; t = u on the compute region.  Arithmetic in
 // float64 whatever T.
 template <typename T>
 cudaError_t launch_coarse_rhs(const LevelView& C, const LevelView& F, const T* u, const T* rho,
                               T* rhs, T* t, cudaStream_t s);
+// t = u on the shell cells of the boxes that lie inside the domain (levels
+// stored with a shell; with launch_coarse_rhs, t = u on the whole box).
+template <typename T>
+cudaError_t launch_shell_copy(const LevelView& C, const T* u, T* t, cudaStream_t s);
 // Transition level: u = t (the owner-written restricted solution) and
 // rhs = rho + A t on the whole (global) level; float64 arithmetic.
 template <typename T>
