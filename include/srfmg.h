@@ -161,7 +161,8 @@ int sr_fmg_solve(sr_fmg_t h, const double* f_dev, double* u_dev, void* stream);
 int sr_fmg_solve_async(sr_fmg_t h, const double* f_dev, double* u_dev, void* stream);
 
 /* Wait for stream and return the status of the solves queued on h since the
- * previous check (SR_OK, SR_ERR_NONFINITE, SR_ERR_TIMEOUT). */
+ * previous check (SR_OK, SR_ERR_NONFINITE, SR_ERR_TIMEOUT); the status is
+ * then cleared. */
 int sr_fmg_check(sr_fmg_t h, void* stream);
 
 /* End-to-end solve from host memory: copies f_host (n^3 doubles) to the
@@ -186,6 +187,19 @@ int sr_fmg_solve_host(sr_fmg_t h, const double* f_host, double* u_host, void* st
  */
 int sr_fmg_vsolve(sr_fmg_t h, const double* f_dev, double* u_dev, double rtol, int max_cycles,
                   int* cycles, double* rel_resid, void* stream);
+
+/*
+ * Pipelined end-to-end solves from host memory.  Each call queues: the copy
+ * of f_host (n^3 doubles) into one of two device staging slots on an internal
+ * stream, the solve on `stream`, and the copy of the solution to u_host on a
+ * second internal stream; consecutive calls alternate slots, so one call's
+ * copies overlap its neighbours' solves.  The host buffers must stay valid
+ * and unchanged until sr_fmg_check_host returns (page-locked memory lets
+ * the copies run asynchronously).  sr_fmg_check_host waits for every copy
+ * out and returns the accumulated status of the solves (as sr_fmg_check).
+ */
+int sr_fmg_solve_host_async(sr_fmg_t h, const double* f_host, double* u_host, void* stream);
+int sr_fmg_check_host(sr_fmg_t h);
 
 /* Number of kernel launches the handle's last queued solve made. */
 int sr_fmg_launches_per_solve(sr_fmg_t h, int* launches);

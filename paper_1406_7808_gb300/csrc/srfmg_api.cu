@@ -142,7 +142,21 @@ struct sr_fmg_s {
   double* hbuf_f = nullptr;        // device staging for sr_fmg_solve_host
   double* hbuf_u = nullptr;
   unsigned long long* norms = nullptr;  // sr_fmg_vsolve: ||f||, ||f - A u|| as double bits
-  sr_fmg_batch_t graph = nullptr;  // graph mode: a batch of this one handle
+  // graph mode: a captured graph (a batch of this one handle) per (f, u)
+  // pair, the most recent few pairs
+  struct GraphEntry {
+    const double* f;
+    double* u;
+    sr_fmg_batch_t b;
+  };
+  std::vector<GraphEntry> graphs;
+  // pipelined host solves: two slots of device staging, copy streams and
+  // the events that order copies, solves and reuse of a slot
+  double *pf[2] = {nullptr, nullptr}, *pu[2] = {nullptr, nullptr};
+  cudaStream_t cin = nullptr, cout = nullptr, last = nullptr;
+  cudaEvent_t ev_in[2] = {}, ev_solved[2] = {}, ev_out[2] = {};
+  int pslot = 0;
+  bool pused[2] = {false, false};
   int launches = 0;                // kernel launches queued by the last solve
   Profile prof;
 
@@ -857,7 +871,6 @@ int solve_once(sr_fmg_s* h, const T* f, double* out, int add, int check, cudaStr
 
 int enqueue_solve(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
   h->launches = 0;
-  CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned int), s));
   if (!h->mixed) return solve_once<double>(h, f, u, 0, 1, s);
   // float64 defect correction around the float32 solve
   const int n = h->cfg.n;
@@ -928,11 +941,29 @@ int collect_profile(sr_fmg_s* h) {
 // handle's captured graph
 static int queue_solve(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
   if (!h->cfg.graph || h->prof.on) return enqueue_solve(h, f, u, s);
-  if (!h->graph) {
-    int rc = sr_fmg_batch_create(&h->graph, &h, 1);
-    if (rc) return rc;
+  constexpr size_t kGraphs = 4;
+  for (const sr_fmg_s::GraphEntry& g : h->graphs)
+    if (g.f == f && g.u == u) return sr_fmg_batch_solve_async(g.b, &f, &u, s);
+  if (h->graphs.size() >= kGraphs) {  // the oldest pair's graph goes (freed once idle)
+    sr_fmg_batch_destroy(h->graphs.front().b);
+    h->graphs.erase(h->graphs.begin());
   }
-  return sr_fmg_batch_solve_async(h->graph, &f, &u, s);
+  sr_fmg_batch_t b = nullptr;
+  int rc = sr_fmg_batch_create(&b, &h, 1);
+  if (rc) return rc;
+  h->graphs.push_back({f, u, b});
+  return sr_fmg_batch_solve_async(b, &f, &u, s);
+}
+
+// release the pipelined-host-solve resources
+void free_pipeline(sr_fmg_s* h) {
+  if (h->cin) cudaStreamDestroy(h->cin);
+  if (h->cout) cudaStreamDestroy(h->cout);
+  for (int k = 0; k < 2; ++k) {
+    if (h->ev_in[k]) cudaEventDestroy(h->ev_in[k]);
+    if (h->ev_solved[k]) cudaEventDestroy(h->ev_solved[k]);
+    if (h->ev_out[k]) cudaEventDestroy(h->ev_out[k]);
+  }
 }
 
 int srfmg::enqueue_solve_unchecked(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
@@ -1012,7 +1043,8 @@ int sr_fmg_create(sr_fmg_t* out, const sr_fmg_config* cfg) {
 int sr_fmg_destroy(sr_fmg_t h) {
   if (!h) return SR_OK;
   DeviceGuard g(h->device);
-  if (h->graph) sr_fmg_batch_destroy(h->graph);
+  for (const sr_fmg_s::GraphEntry& e : h->graphs) sr_fmg_batch_destroy(e.b);
+  free_pipeline(h);
   free_all(h);
   delete h;
   return SR_OK;
@@ -1041,9 +1073,61 @@ int sr_fmg_check(sr_fmg_t h, void* stream) {
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   unsigned int st = 0;
   CK(cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+  // the status accumulates over the solves since the previous check
+  CK(cudaMemset(h->status, 0, sizeof(st)));
   if (st & 1u) return SR_ERR_NONFINITE;
   if (st & 2u) return SR_ERR_TIMEOUT;
   return SR_OK;
+}
+
+int sr_fmg_solve_host_async(sr_fmg_t h, const double* f_host, double* u_host, void* stream) {
+  if (!h || !f_host || !u_host) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  const size_t cells = (size_t)srfmg::handle_cells(h);
+  const size_t bytes = cells * sizeof(double);
+  if (!h->cin) {
+    int rc = SR_OK;
+    for (int k = 0; k < 2 && !rc; ++k) {
+      rc = dalloc(h, &h->pf[k], cells);
+      if (!rc) rc = dalloc(h, &h->pu[k], cells);
+    }
+    if (rc) return rc;
+    CK(cudaStreamCreateWithFlags(&h->cin, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&h->cout, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaEventCreateWithFlags(&h->ev_in[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&h->ev_solved[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&h->ev_out[k], cudaEventDisableTiming));
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int k = h->pslot;
+  h->pslot ^= 1;
+  // copy in on its own stream once the solve that last read this slot is done
+  if (h->pused[k]) CK(cudaStreamWaitEvent(h->cin, h->ev_solved[k], 0));
+  CK(cudaMemcpyAsync(h->pf[k], f_host, bytes, cudaMemcpyHostToDevice, h->cin));
+  CK(cudaEventRecord(h->ev_in[k], h->cin));
+  // solve on the caller's stream once the copy is in and the slot's previous
+  // result has been copied out
+  CK(cudaStreamWaitEvent(s, h->ev_in[k], 0));
+  if (h->pused[k]) CK(cudaStreamWaitEvent(s, h->ev_out[k], 0));
+  int rc = queue_solve(h, h->pf[k], h->pu[k], s);
+  if (rc) return rc;
+  CK(cudaEventRecord(h->ev_solved[k], s));
+  // copy out on its own stream
+  CK(cudaStreamWaitEvent(h->cout, h->ev_solved[k], 0));
+  CK(cudaMemcpyAsync(u_host, h->pu[k], bytes, cudaMemcpyDeviceToHost, h->cout));
+  CK(cudaEventRecord(h->ev_out[k], h->cout));
+  h->pused[k] = true;
+  h->last = s;
+  return SR_OK;
+}
+
+int sr_fmg_check_host(sr_fmg_t h) {
+  if (!h) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  if (h->cout) CK(cudaStreamSynchronize(h->cout));
+  return sr_fmg_check(h, h->last);
 }
 
 int sr_fmg_solve(sr_fmg_t h, const double* f_dev, double* u_dev, void* stream) {

@@ -86,6 +86,8 @@ def load():
     for name in ("sr_fmg_solve", "sr_fmg_solve_async", "sr_fmg_solve_host"):
         getattr(lib, name).argtypes = [_VP, _VP, _VP, _VP]
     lib.sr_fmg_check.argtypes = [_VP, _VP]
+    lib.sr_fmg_solve_host_async.argtypes = [_VP, _VP, _VP, _VP]
+    lib.sr_fmg_check_host.argtypes = [_VP]
     lib.sr_fmg_status_string.argtypes = [ctypes.c_int]
     lib.sr_fmg_status_string.restype = ctypes.c_char_p
     lib.sr_fmg_launches_per_solve.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
@@ -317,6 +319,19 @@ class Solver:
     def check(self):
         _check(load().sr_fmg_check(self._h, _stream()), "sr_fmg_check")
 
+    def solve_host_async(self, f, out):
+        """Queue a pipelined end-to-end solve of host f into host out (both
+        stay owned by the caller and must not change until check_host());
+        consecutive calls overlap their copies with each other's solves."""
+        _check(load().sr_fmg_solve_host_async(self._h, _host_ptr(f, self.shape, "f"),
+                                              _host_ptr(out, self.shape, "out"), _stream()),
+               "sr_fmg_solve_host_async")
+        return out
+
+    def check_host(self):
+        """Wait for every queued pipelined solve's result to reach the host."""
+        _check(load().sr_fmg_check_host(self._h), "sr_fmg_check_host")
+
     def solve_host(self, f, out=None):
         """End-to-end solve of a host array (numpy float64 (n, n, n) or a CPU
         tensor); the copies to and from the device run inside the library."""
@@ -332,6 +347,18 @@ class Solver:
             ctypes.c_void_p(out.data_ptr())
         _check(load().sr_fmg_solve_host(self._h, fp, up, _stream()), "sr_fmg_solve_host")
         return out
+
+
+def _host_ptr(a, shape, name):
+    """address of a host float64 array (numpy, or a CPU tensor) of the given shape"""
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or a.dtype.itemsize != 8 or not a.is_contiguous() or tuple(a.shape) != shape:
+            raise ValueError(f"{name} must be a contiguous float64 CPU tensor of shape {shape}")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous \
+            or a.shape != shape:
+        raise ValueError(f"{name} must be a contiguous float64 array of shape {shape}")
+    return ctypes.c_void_p(a.ctypes.data)
 
 
 class Batch:

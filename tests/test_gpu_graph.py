@@ -71,3 +71,33 @@ def test_graph_mode_profiles_kernel_by_kernel(gpu):
         g.profile(False)
         assert sum(v["launches"] for v in prof.values()) == g.launches_per_solve
         assert np.array_equal(u.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("kw", [dict(seg=16, K=2, A=8, B=0, graph=True), dict(mixed=True)])
+def test_pipelined_host_solves(gpu, kw):
+    """sr_fmg_solve_host_async: a run of solves from host arrays with copies
+    overlapping the neighbouring solves gives each f the same u as the
+    synchronous host solve; a non-finite f in the run is reported by
+    sr_fmg_check_host and the handle stays usable."""
+    import torch
+    n = 64
+    fs = [torch.from_numpy(inputs.manufactured(n, s)[0]).pin_memory() for s in range(5)]
+    outs = [torch.empty_like(f).pin_memory() for f in fs]
+    with gpu.Solver(n, **kw) as s:
+        ref = [s.solve_host(f.numpy()) for f in fs]
+        for f, o in zip(fs, outs):
+            s.solve_host_async(f, o)
+        s.check_host()
+        for r, o in zip(ref, outs):
+            assert np.array_equal(r, o.numpy())
+        bad = fs[2].clone()
+        bad[1, 2, 3] = float("nan")
+        s.solve_host_async(fs[0], outs[0])
+        s.solve_host_async(bad, outs[1])
+        s.solve_host_async(fs[1], outs[2])
+        with pytest.raises(gpu.SRFMGError) as e:
+            s.check_host()
+        assert e.value.status == gpu.SR_ERR_NONFINITE
+        s.solve_host_async(fs[3], outs[3])
+        s.check_host()
+        assert np.array_equal(outs[3].numpy(), ref[3])
