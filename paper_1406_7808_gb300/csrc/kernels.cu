@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kZThreads) k_cheb2_update_zm(LevelView L, T* _
 // column form saves.
 // r = D^-1 (f - A u) = f h^2/6 - u + (sum of neighbours)/6
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_cheb_residual(LevelView L, const T* __restrict__ u,
+__global__ void __launch_bounds__(kThreads, 7) k_cheb_residual(LevelView L, const T* __restrict__ u,
                                                             T* __restrict__ r, FieldT<T> f,
                                                             T cf, T sixth) {
   __shared__ BoxDesc B, FB;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) k_cheb_residual(LevelView L, const T
 
 // u += a r + b (sum of the neighbours of r)
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_cheb2_update(LevelView L, T* __restrict__ u,
+__global__ void __launch_bounds__(kThreads, 8) k_cheb2_update(LevelView L, T* __restrict__ u,
                                                            const T* __restrict__ r, T a, T b) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const T* __rest
 // across the outer faces of the 2x2x2 block (each inner face cancels), so
 //   rho = (sum of f)/8 - (3 n^2/8) S + (n^2/8) O,   uhat = S/8.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F, const T* __restrict__ u,
+__global__ void __launch_bounds__(kThreads, 5) k_resid_restrict(LevelView F, const T* __restrict__ u,
                                                              FieldT<T> f, LevelView C,
                                                              T* __restrict__ uhat_dst,
                                                              T* __restrict__ rho_dst, T cS, T cO,
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(LevelView F, const 
 // A u elsewhere in the compute region (float64 arithmetic); t = u on the
 // whole stored box
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_coarse_rhs(LevelView C, LevelView F,
+__global__ void __launch_bounds__(kThreads, 8) k_coarse_rhs(LevelView C, LevelView F,
                                                          const T* __restrict__ u,
                                                          const T* __restrict__ rho,
                                                          T* __restrict__ rhs, T* __restrict__ t,
@@ -639,7 +639,7 @@ __device__ __forceinline__ bool zcolumn(const int lo[3], const int hi[3], int np
 // the plane of its own coarse cell with the one on its side (1 FMA) and is
 // scaled by 1/64 into uf (add == 0: uf = P uc;  add == 1: uf += P uc).
 template <typename T>
-__global__ void __launch_bounds__(kZThreads) k_prolong_zcol(LevelView C, const T* __restrict__ uc,
+__global__ void __launch_bounds__(kZThreads, 6) k_prolong_zcol(LevelView C, const T* __restrict__ uc,
                                                             LevelView F, T* __restrict__ uf,
                                                             int add, T three, T w64, int nplane,
                                                             Fk<T> k) {
@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(kZThreads) k_prolong_zcol(LevelView C, const T
 // d = alpha d + beta r (alpha == 0: d = beta r); u += d (the Chebyshev
 // recurrence step for degrees other than 2), over the compute region
 template <typename T>
-__global__ void __launch_bounds__(kZThreads) k_cheb_step_zm(LevelView L, T* __restrict__ u,
+__global__ void __launch_bounds__(kZThreads, 8) k_cheb_step_zm(LevelView L, T* __restrict__ u,
                                                             T* __restrict__ d,
                                                             const T* __restrict__ r, T alpha,
                                                             T beta, int write_d, int nplane,
@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(kZThreads) k_cheb_step_zm(LevelView L, T* __re
 // cells and frozen SR ghosts): the coarse-grid correction w - t of the FAS
 // V-cycle, ready for prolongation
 template <typename T>
-__global__ void __launch_bounds__(kZThreads) k_diff_zm(LevelView C, const T* __restrict__ u,
+__global__ void __launch_bounds__(kZThreads, 8) k_diff_zm(LevelView C, const T* __restrict__ u,
                                                        const T* __restrict__ t,
                                                        T* __restrict__ e, int nplane, T mone) {
   __shared__ BoxDesc B;
