@@ -406,13 +406,15 @@ __global__ void __launch_bounds__(kThreads, 5) k_resid_restrict(LevelView F, con
 
 // rhs = rho + A u inside the restriction region of the matching fine box,
 // A u elsewhere in the compute region (float64 arithmetic); t = u on the
-// whole stored box
+// whole stored box; with r, the smoother's first residual D^-1 (rhs - A u),
+// which is D^-1 rho and 0 respectively (cr = D^-1)
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 8) k_coarse_rhs(LevelView C, LevelView F,
                                                          const T* __restrict__ u,
                                                          const T* __restrict__ rho,
                                                          T* __restrict__ rhs, T* __restrict__ t,
-                                                         double c6, double cn, Fk<double> k) {
+                                                         T* __restrict__ r, double c6, double cn,
+                                                         double cr, Fk<double> k) {
   __shared__ BoxDesc B, FBx;
   if (threadIdx.x == 0) {
     B = C.boxes[blockIdx.y];
@@ -430,19 +432,22 @@ __global__ void __launch_bounds__(kThreads, 8) k_coarse_rhs(LevelView C, LevelVi
                      q.y < FBx.rhi[1] && q.z >= FBx.rlo[2] && q.z < FBx.rhi[2];
     double v[6];
     neighbours<double>(u, c, B, C, q.x, q.y, q.z, uc, v);
-    rhs[c] = (T)fma6(cn, v, fma(c6, widen(uc), inF ? widen(rho[c]) : k.zero));
+    const double rh = inF ? widen(rho[c]) : k.zero;
+    rhs[c] = (T)fma6(cn, v, fma(c6, widen(uc), rh));
+    if (r) r[c] = (T)(cr * rh);
   }
 }
 
 // u = t, rhs = rho + A t on the whole (global) transition level (float64
-// arithmetic)
+// arithmetic); with r, the smoother's first residual D^-1 rho (cr = D^-1)
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
                                                              const T* __restrict__ t,
                                                              const T* __restrict__ rho,
                                                              T* __restrict__ u,
-                                                             T* __restrict__ rhs, double c6,
-                                                             double cn) {
+                                                             T* __restrict__ rhs,
+                                                             T* __restrict__ r, double c6,
+                                                             double cn, double cr) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[0];
   __syncthreads();
@@ -456,7 +461,9 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
     double v[6];
     neighbours<double>(t, c, B, C, q.x, q.y, q.z, tc, v);
     u[c] = tc;
-    rhs[c] = (T)fma6(cn, v, fma(c6, widen(tc), widen(rho[c])));
+    const double rh = widen(rho[c]);
+    rhs[c] = (T)fma6(cn, v, fma(c6, widen(tc), rh));
+    if (r) r[c] = (T)(cr * rh);
   }
 }
 
@@ -885,10 +892,9 @@ cudaError_t launch_resid_restrict(const LevelView& F, const T* u, FieldT<T> f,
 
 template <typename T>
 cudaError_t launch_coarse_rhs(const LevelView& C, const LevelView& F, const T* u, const T* rho,
-                              T* rhs, T* t, cudaStream_t s) {
-  k_coarse_rhs<T><<<grid_for(C, C.max_cells), kThreads, 0, s>>>(C, F, u, rho, rhs, t,
-                                                                6.0 * sq(C.n), -sq(C.n),
-                                                                fk<double>());
+                              T* rhs, T* t, T* r, cudaStream_t s) {
+  k_coarse_rhs<T><<<grid_for(C, C.max_cells), kThreads, 0, s>>>(
+      C, F, u, rho, rhs, t, r, 6.0 * sq(C.n), -sq(C.n), 1.0 / (6.0 * sq(C.n)), fk<double>());
   return cudaGetLastError();
 }
 
@@ -901,9 +907,9 @@ cudaError_t launch_shell_copy(const LevelView& C, const T* u, T* t, cudaStream_t
 
 template <typename T>
 cudaError_t launch_transition_rhs(const LevelView& C, const T* t, const T* rho, T* u, T* rhs,
-                                  cudaStream_t s) {
-  k_transition_rhs<T><<<grid_for(C, C.max_cells), kThreads, 0, s>>>(C, t, rho, u, rhs,
-                                                                     6.0 * sq(C.n), -sq(C.n));
+                                  T* r, cudaStream_t s) {
+  k_transition_rhs<T><<<grid_for(C, C.max_cells), kThreads, 0, s>>>(
+      C, t, rho, u, rhs, r, 6.0 * sq(C.n), -sq(C.n), 1.0 / (6.0 * sq(C.n)));
   return cudaGetLastError();
 }
 
@@ -984,10 +990,10 @@ cudaError_t launch_accumulate(long long cells, const float* e, double* u, int ad
   template cudaError_t launch_resid_restrict<T>(const LevelView&, const T*, FieldT<T>,         \
                                                 const LevelView&, T*, T*, cudaStream_t);       \
   template cudaError_t launch_coarse_rhs<T>(const LevelView&, const LevelView&, const T*,      \
-                                            const T*, T*, T*, cudaStream_t);                   \
+                                            const T*, T*, T*, T*, cudaStream_t);               \
   template cudaError_t launch_shell_copy<T>(const LevelView&, const T*, T*, cudaStream_t);     \
   template cudaError_t launch_transition_rhs<T>(const LevelView&, const T*, const T*, T*, T*,  \
-                                                cudaStream_t);                                 \
+                                                T*, cudaStream_t);                             \
   template cudaError_t launch_prolong<T>(const LevelView&, const T*, const LevelView&, T*, int, \
                                          cudaStream_t);                                        \
   template cudaError_t launch_diff<T>(const LevelView&, const T*, const T*, T*, cudaStream_t);  \

@@ -99,13 +99,15 @@ __global__ void __launch_bounds__(kThreads27) k27_apply(LevelView L, const doubl
 }
 
 // rhs = rho + A u inside the matching fine box's restriction region, A u on
-// the rest of the compute region; t = u on the whole stored box
+// the rest of the compute region; t = u on the whole stored box; with r, the
+// smoother's first residual D^-1 (rhs - A u): D^-1 rho and 0 (cr = D^-1)
 __global__ void __launch_bounds__(kThreads27) k27_coarse_rhs(LevelView C, LevelView F,
                                                              const double* __restrict__ u,
                                                              const double* __restrict__ rho,
                                                              double* __restrict__ rhs,
-                                                             double* __restrict__ t, W27 w,
-                                                             double n2) {
+                                                             double* __restrict__ t,
+                                                             double* __restrict__ r, W27 w,
+                                                             double n2, double cr) {
   __shared__ BoxDesc B, FBx;
   if (threadIdx.x == 0) {
     B = C.boxes[blockIdx.y];
@@ -135,16 +137,19 @@ __global__ void __launch_bounds__(kThreads27) k27_coarse_rhs(LevelView C, LevelV
                      q.y < FBx.rhi[1] && q.z >= FBx.rlo[2] && q.z < FBx.rhi[2];
     const double au = op27(u, B, C, w, n2, q.x, q.y, q.z);
     rhs[c] = inF ? rho[c] + au : au;
+    if (r) r[c] = inF ? cr * rho[c] : 0.0;
   }
 }
 
-// u = t, rhs = rho + A t on the whole (global) transition level
+// u = t, rhs = rho + A t on the whole (global) transition level; with r, the
+// smoother's first residual D^-1 rho (cr = D^-1)
 __global__ void __launch_bounds__(kThreads27) k27_transition_rhs(LevelView C,
                                                                  const double* __restrict__ t,
                                                                  const double* __restrict__ rho,
                                                                  double* __restrict__ u,
-                                                                 double* __restrict__ rhs, W27 w,
-                                                                 double n2) {
+                                                                 double* __restrict__ rhs,
+                                                                 double* __restrict__ r, W27 w,
+                                                                 double n2, double cr) {
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[0];
   __syncthreads();
@@ -155,6 +160,7 @@ __global__ void __launch_bounds__(kThreads27) k27_transition_rhs(LevelView C,
     const long long c = at27(B, q.x, q.y, q.z);
     u[c] = t[c];
     rhs[c] = rho[c] + op27(t, B, C, w, n2, q.x, q.y, q.z);
+    if (r) r[c] = cr * rho[c];
   }
 }
 
@@ -431,17 +437,17 @@ cudaError_t launch27_residual(const LevelView& L, const double* u, FieldT<double
 }
 
 cudaError_t launch27_coarse_rhs(const LevelView& C, const LevelView& F, const double* u,
-                                const double* rho, double* rhs, double* t, W27 w,
+                                const double* rho, double* rhs, double* t, double* r, W27 w,
                                 cudaStream_t s) {
-  k27_coarse_rhs<<<grid27(C, C.max_stored), kThreads27, 0, s>>>(C, F, u, rho, rhs, t, w,
-                                                                sq27(C.n));
+  k27_coarse_rhs<<<grid27(C, C.max_stored), kThreads27, 0, s>>>(
+      C, F, u, rho, rhs, t, r, w, sq27(C.n), 1.0 / (w.w0 * sq27(C.n)));
   return cudaGetLastError();
 }
 
 cudaError_t launch27_transition_rhs(const LevelView& C, const double* t, const double* rho,
-                                    double* u, double* rhs, W27 w, cudaStream_t s) {
-  k27_transition_rhs<<<grid27(C, C.max_cells), kThreads27, 0, s>>>(C, t, rho, u, rhs, w,
-                                                                   sq27(C.n));
+                                    double* u, double* rhs, double* r, W27 w, cudaStream_t s) {
+  k27_transition_rhs<<<grid27(C, C.max_cells), kThreads27, 0, s>>>(
+      C, t, rho, u, rhs, r, w, sq27(C.n), 1.0 / (w.w0 * sq27(C.n)));
   return cudaGetLastError();
 }
 

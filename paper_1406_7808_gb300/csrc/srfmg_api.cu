@@ -623,19 +623,19 @@ cudaError_t op_cheb2_update(const sr_fmg_s* h, const LevelView& L, T* u, const T
 }
 template <typename T>
 cudaError_t op_coarse_rhs(const sr_fmg_s* h, const LevelView& C, const LevelView& F, const T* u,
-                          const T* rho, T* rhs, T* t, cudaStream_t s) {
+                          const T* rho, T* rhs, T* t, T* r, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
-    if (h->op27) return launch27_coarse_rhs(C, F, u, rho, rhs, t, h->w27, s);
+    if (h->op27) return launch27_coarse_rhs(C, F, u, rho, rhs, t, r, h->w27, s);
   }
-  return launch_coarse_rhs<T>(C, F, u, rho, rhs, t, s);
+  return launch_coarse_rhs<T>(C, F, u, rho, rhs, t, r, s);
 }
 template <typename T>
 cudaError_t op_transition_rhs(const sr_fmg_s* h, const LevelView& C, const T* t, const T* rho,
-                              T* u, T* rhs, cudaStream_t s) {
+                              T* u, T* rhs, T* r, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
-    if (h->op27) return launch27_transition_rhs(C, t, rho, u, rhs, h->w27, s);
+    if (h->op27) return launch27_transition_rhs(C, t, rho, u, rhs, r, h->w27, s);
   }
-  return launch_transition_rhs<T>(C, t, rho, u, rhs, s);
+  return launch_transition_rhs<T>(C, t, rho, u, rhs, r, s);
 }
 
 // algorithmic floating-point operations per unit of the operator kernels
@@ -667,21 +667,35 @@ int resid_restrict(sr_fmg_s* h, const Level<T>& F, const T* u, FieldT<T> f, cons
   return SR_OK;
 }
 
+// After restriction the coarse smoother's first residual D^-1 (rhs - A u) is
+// D^-1 rho inside the restriction region and 0 elsewhere (rhs = rho + A u,
+// or A u, with the same u), so the float64 solve writes it with the coarse
+// right-hand side instead of forming rhs - A u again.  The float32 inner
+// solver of the mixed mode keeps the literal pass: its rhs is rounded to
+// float32, and the later residuals see that rounding.
 template <typename T>
-int smooth(sr_fmg_s* h, const Level<T>& L, const Cheb& c, T* u, FieldT<T> f, cudaStream_t s) {
+constexpr bool kFirstResidual = sizeof(T) == 8;
+
+// r_ready: L.r already holds the first residual D^-1 (f - A u) (written with
+// the level's coarse right-hand side), so the first residual pass is skipped
+template <typename T>
+int smooth(sr_fmg_s* h, const Level<T>& L, const Cheb& c, T* u, FieldT<T> f, cudaStream_t s,
+           bool r_ready = false) {
   if (c.nu == 0) return SR_OK;
   const double cells = L.tot_cells;
   const double w = sizeof(T);
   if (c.nu == 2) {
-    LAUNCH(h, kind_of<T>(kChebResidual), cells, ops_smooth(h), 3 * w, s,
-           op_cheb_residual<T>(h, L.view, u, L.r, f, s));
+    if (!r_ready)
+      LAUNCH(h, kind_of<T>(kChebResidual), cells, ops_smooth(h), 3 * w, s,
+             op_cheb_residual<T>(h, L.view, u, L.r, f, s));
     LAUNCH(h, kind_of<T>(kCheb2Update), cells, ops_smooth(h), 3 * w, s,
            op_cheb2_update<T>(h, L.view, u, L.r, c, s));
     return SR_OK;
   }
   for (int m = 0; m < c.nu; ++m) {
-    LAUNCH(h, kind_of<T>(kChebResidual), cells, ops_smooth(h), 3 * w, s,
-           op_cheb_residual<T>(h, L.view, u, L.r, f, s));
+    if (!(r_ready && m == 0))
+      LAUNCH(h, kind_of<T>(kChebResidual), cells, ops_smooth(h), 3 * w, s,
+             op_cheb_residual<T>(h, L.view, u, L.r, f, s));
     const int write_d = (c.nu > 1 && m < c.nu - 1) ? 1 : 0;
     const bool with_d = write_d || c.alpha[m] != 0.0;
     LAUNCH(h, kind_of<T>(kChebStep), cells, with_d ? 3 : 2, (with_d ? 5 : 3) * w, s,
@@ -693,7 +707,8 @@ int smooth(sr_fmg_s* h, const Level<T>& L, const Cheb& c, T* u, FieldT<T> f, cud
 // FASMGV on global level g (Fig. "FAS multigrid V-cycle"); u is the level's
 // u (or the caller's u on the finest plain FP64 level).
 template <typename T>
-int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStream_t s) {
+int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStream_t s,
+                  bool r_ready = false) {
   Level<T>& L = H.glev[g];
   const double w = sizeof(T);
   if (g == 0) {
@@ -703,13 +718,16 @@ int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStrea
     return SR_OK;
   }
   Level<T>& C = H.glev[g - 1];
-  int rc = smooth(h, L, h->pre, u, rhs, s);
+  int rc = smooth(h, L, h->pre, u, rhs, s, r_ready);
   if (rc) return rc;
   rc = resid_restrict<T>(h, L, u, rhs, C, C.u, C.rho, s);
   if (rc) return rc;
-  LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h), 4 * w, s,
-         op_coarse_rhs<T>(h, C.view, L.view, C.u, C.rho, C.rhs, C.t, s));
-  rc = vcycle_global(h, H, g - 1, C.u, view_global<T>(C, C.rhs), s);
+  // the coarse level's first residual comes with its right-hand side in
+  // float64 (the coarsest level is solved directly and needs none)
+  const bool cr = kFirstResidual<T> && g - 1 >= 1;
+  LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h) + (cr ? 1 : 0), (cr ? 5 : 4) * w, s,
+         op_coarse_rhs<T>(h, C.view, L.view, C.u, C.rho, C.rhs, C.t, cr ? C.r : nullptr, s));
+  rc = vcycle_global(h, H, g - 1, C.u, view_global<T>(C, C.rhs), s, cr);
   if (rc) return rc;
   LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
          launch_diff<T>(C.view, C.u, C.t, C.rho, s));
@@ -795,14 +813,19 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
     for (int j = k; j >= 1; --j) {
       Level<T>& Lj = H.slev[j];
       const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
-      int rc = smooth(h, Lj, h->pre, Lj.u, rhs, s);
+      // below the stage's top level the first residual came with the
+      // level's right-hand side (float64)
+      int rc = smooth(h, Lj, h->pre, Lj.u, rhs, s, kFirstResidual<T> && j < k);
       if (rc) return rc;
       if (j > 1) {
         Level<T>& C = H.slev[j - 1];
         rc = resid_restrict<T>(h, Lj, Lj.u, rhs, C, C.u, C.rho, s);
         if (rc) return rc;
-        LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h), 4 * w, s,
-               op_coarse_rhs<T>(h, C.view, Lj.view, C.u, C.rho, C.rhs, C.t, s));
+        const bool cr = kFirstResidual<T>;
+        LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h) + (cr ? 1 : 0),
+               (cr ? 5 : 4) * w, s,
+               op_coarse_rhs<T>(h, C.view, Lj.view, C.u, C.rho, C.rhs, C.t, cr ? C.r : nullptr,
+                                s));
         if (!h->op27)
           LAUNCH(h, kind_of<T>(kShellCopy), C.tot_cells / 4, 0, 2 * w, s,
                  launch_shell_copy<T>(C.view, C.u, C.t, s));
@@ -812,9 +835,12 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
       }
     }
     // transition level: u_0 <- \hat I u_1, t_0 = u_0, r_0 = rho_0 + L_0 u_0, FASMGV
-    LAUNCH(h, kind_of<T>(kTransitionRhs), L0.tot_cells, ops_rhs(h), 4 * w, s,
-           op_transition_rhs<T>(h, L0.view, L0.t, L0.rho, L0.u, L0.rhs, s));
-    int rc = vcycle_global(h, H, h->G - 1, L0.u, view_global<T>(L0, L0.rhs), s);
+    // level 0 is solved directly and needs no residual
+    const bool cr = kFirstResidual<T> && h->G - 1 >= 1;
+    LAUNCH(h, kind_of<T>(kTransitionRhs), L0.tot_cells, ops_rhs(h) + (cr ? 1 : 0),
+           (cr ? 5 : 4) * w, s,
+           op_transition_rhs<T>(h, L0.view, L0.t, L0.rho, L0.u, L0.rhs, cr ? L0.r : nullptr, s));
+    int rc = vcycle_global(h, H, h->G - 1, L0.u, view_global<T>(L0, L0.rhs), s, cr);
     if (rc) return rc;
     // up-leg
     for (int j = 1; j <= k; ++j) {

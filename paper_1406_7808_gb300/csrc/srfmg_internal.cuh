@@ -96,19 +96,22 @@ cudaError_t launch_resid_restrict(const LevelView& F, const T* u, FieldT<T> f,
 // Coarse right-hand side of the FAS cycle (Eq. eq:cresid2 and its SR form):
 // rhs = rho + A u inside the fine boxes' restriction region, rhs = A u on the
 // rest of the compute region; t = u on the compute region.  Arithmetic in
-// float64 whatever T.
+// float64 whatever T.  With r (may be null), also the coarse smoother's first
+// residual D^-1 (rhs - A u) as it stands, which is D^-1 rho inside the
+// restriction region and 0 on the rest of the compute region.
 template <typename T>
 cudaError_t launch_coarse_rhs(const LevelView& C, const LevelView& F, const T* u, const T* rho,
-                              T* rhs, T* t, cudaStream_t s);
+                              T* rhs, T* t, T* r, cudaStream_t s);
 // t = u on the shell cells of the boxes that lie inside the domain (levels
 // stored with a shell; with launch_coarse_rhs, t = u on the whole box).
 template <typename T>
 cudaError_t launch_shell_copy(const LevelView& C, const T* u, T* t, cudaStream_t s);
 // Transition level: u = t (the owner-written restricted solution) and
-// rhs = rho + A t on the whole (global) level; float64 arithmetic.
+// rhs = rho + A t on the whole (global) level; float64 arithmetic.  With r
+// (may be null), also the smoother's first residual D^-1 rho.
 template <typename T>
 cudaError_t launch_transition_rhs(const LevelView& C, const T* t, const T* rho, T* u, T* rhs,
-                                  cudaStream_t s);
+                                  T* r, cudaStream_t s);
 // Prolongation onto the fine boxes' prolongation range:
 // add == 0: uf = P uc;  add == 1: uf += P uc.
 template <typename T>
@@ -176,11 +179,12 @@ cudaError_t launch27_residual_zm(const LevelView& L, const double* u, FieldT<dou
 cudaError_t launch27_restrict_pair(const LevelView& F, const double* u, const double* r,
                                    const LevelView& C, double* uhat_dst, double* rho_dst,
                                    cudaStream_t s);
+// (r: as launch_coarse_rhs and launch_transition_rhs, D = w0 n^2)
 cudaError_t launch27_coarse_rhs(const LevelView& C, const LevelView& F, const double* u,
-                                const double* rho, double* rhs, double* t, W27 w,
+                                const double* rho, double* rhs, double* t, double* r, W27 w,
                                 cudaStream_t s);
 cudaError_t launch27_transition_rhs(const LevelView& C, const double* t, const double* rho,
-                                    double* u, double* rhs, W27 w, cudaStream_t s);
+                                    double* u, double* rhs, double* r, W27 w, cudaStream_t s);
 // max |f - A u| (|f| without u) over the whole unpadded level L (one box)
 cudaError_t launch27_resid_norm(const LevelView& L, const double* f, const double* u,
                                 unsigned long long* norm, unsigned int* status, W27 w,

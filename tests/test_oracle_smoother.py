@@ -39,3 +39,29 @@ def test_smoother_fixed_point(oracle_mod):
     f = rng.standard_normal((n, n, n))
     uh = exact.dst_solve(f)
     assert np.allclose(oracle_mod.smooth(uh, f, 2), uh, rtol=0, atol=1e-14 * np.abs(uh).max() * 10)
+
+
+@pytest.mark.parametrize("geo", [{}, dict(lengths=(2, 1, 1), stencil=27)])
+def test_first_coarse_smoother_step_from_restricted_residual(oracle_mod, geo):
+    """After restriction (Sec. 2, FAS cycle: u_c = I u, rhs_c = rho + A_c u_c)
+    the coarse smoother's first residual f - A u is rho itself, so a degree-2
+    pass from (u_c, rhs_c) equals the same pass from (u_c, rho + A_c u_c)
+    whatever order the terms are formed in; the float64 GPU path relies on
+    this to take the first residual D^-1 rho from the coarse right-hand-side
+    pass.  Checked on the oracle's own residual, restriction and smoother."""
+    rng = np.random.default_rng(7)
+    lengths = geo.get("lengths", (1, 1, 1))
+    n = 16
+    shape = (n * lengths[2], n * lengths[1], n * lengths[0])
+    u = rng.standard_normal(shape)
+    f = rng.standard_normal(shape) * n * n
+    rho = oracle_mod.restrict(oracle_mod.residual(u, f, **geo), **geo)
+    uc = oracle_mod.restrict(u, **geo)
+    rhs = rho + oracle_mod.apply(uc, **geo)
+    first = oracle_mod.residual(uc, rhs, **geo)
+    scale = np.abs(rhs).max()
+    assert np.abs(first - rho).max() <= 1e-13 * scale
+    # two different roundings of the same right-hand side smooth to the same u
+    a = oracle_mod.smooth(uc, rhs, 2, **geo)
+    b = oracle_mod.smooth(uc, rho + (rhs - rho), 2, **geo)
+    assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(a).max())
