@@ -1,7 +1,7 @@
 """Step-by-step parity of the CUDA kernels with the oracle's components, on
 whole grids, through the C ABI (sr_op_*).  Sizes span several thread blocks
-and ragged edges; FP64 tolerance 1e-11 relative max-norm (the north-star
-bound for the solve)."""
+and ragged edges; FP64 tolerance 1e-11 relative max-norm (the bound the
+whole solve is held to)."""
 import numpy as np
 import pytest
 
