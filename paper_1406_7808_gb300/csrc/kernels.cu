@@ -290,6 +290,34 @@ __global__ void __launch_bounds__(kThreads, 8) k_cheb2_update(LevelView L, T* __
   }
 }
 
+// A degree-1 smoothing step followed by the residual the next smoothing of
+// the same level and f starts from: u += beta r and
+// r2 = D^-1 (f - A (u + beta r)) = r - beta D^-1 A r
+//    = (1 - beta) r + (beta / 6) (sum of the neighbours of r),
+// neighbours as in k_cheb2_update (mirrored with a sign flip outside the
+// domain, stored ghosts, which are zero in a residual array, inside it).
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 8) k_cheb1_next(LevelView L, T* __restrict__ u,
+                                                         const T* __restrict__ r,
+                                                         T* __restrict__ r2, T beta, T keep,
+                                                         T b6) {
+  __shared__ BoxDesc B;
+  if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
+  __syncthreads();
+  const int ex = B.hi[0] - B.lo[0], ey = B.hi[1] - B.lo[1], ez = B.hi[2] - B.lo[2];
+  const int ncell = ex * ey * ez;
+
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
+    const Cell q = cell_of(i, B.lo, ex, ey);
+    const long long c = at(B, q.x, q.y, q.z);
+    const T rc = r[c];
+    T v[6];
+    neighbours<T>(r, c, B, L, q.x, q.y, q.z, rc, v);
+    u[c] = fma(beta, rc, u[c]);
+    r2[c] = fma6(b6, v, keep * rc);
+  }
+}
+
 // residual == 0: out = A u = n^2 (6 u - sum);  residual == 1: out = f - A u
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const T* __restrict__ u,
@@ -858,6 +886,14 @@ cudaError_t launch_cheb2_update(const LevelView& L, T* u, const T* r, double a, 
 }
 
 template <typename T>
+cudaError_t launch_cheb1_next(const LevelView& L, T* u, const T* r, T* r2, double beta,
+                              cudaStream_t s) {
+  k_cheb1_next<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, r2, T(beta),
+                                                                T(1.0 - beta), T(beta / 6.0));
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_cheb_step(const LevelView& L, T* u, T* d, const T* r, double alpha,
                              double beta, int write_d, cudaStream_t s) {
   const ZTiles t = ztiles(L);
@@ -982,6 +1018,8 @@ cudaError_t launch_accumulate(long long cells, const float* e, double* u, int ad
                                                cudaStream_t);                                  \
   template cudaError_t launch_cheb2_update<T>(const LevelView&, T*, const T*, double, double,  \
                                               cudaStream_t);                                   \
+  template cudaError_t launch_cheb1_next<T>(const LevelView&, T*, const T*, T*, double,        \
+                                            cudaStream_t);                                     \
   template cudaError_t launch_cheb_step<T>(const LevelView&, T*, T*, const T*, double, double, \
                                            int, cudaStream_t);                                 \
   template cudaError_t launch_apply<T>(const LevelView&, const T*, T*, cudaStream_t);          \

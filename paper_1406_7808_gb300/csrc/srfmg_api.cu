@@ -355,6 +355,17 @@ int dalloc(sr_fmg_s* h, T** p, size_t count) {
   return SR_OK;
 }
 
+// With F(1, 2, ...) in float64 and the 7-point operator, the FMG degree-1
+// step S^alpha is followed by the V-cycle's degree-2 pre-smoother on the same
+// level and f; the step also forms that smoother's first residual
+// D^-1 (f - A u_new) = (1 - beta) r + (beta/6) (sum of the neighbours of r)
+// into the level's d, and the pre-smoother starts from it.
+template <typename T>
+bool fused_fmg_step(const sr_fmg_s* h) {
+  return sizeof(T) == 8 && !h->op27 && h->fmg.nu == 1 && h->fmg.alpha[0] == 0.0 &&
+         h->pre.nu == 2;
+}
+
 BoxDesc whole_box(const int nd[3]) {
   BoxDesc b;
   std::memset(&b, 0, sizeof(b));
@@ -476,7 +487,8 @@ int build_global_levels(sr_fmg_s* h, Hier<T>& H, int ntop, bool top_user) {
   const int m = halvings_to_coarsest(ntop, h->cfg.n_coarse);
   h->G = m + 1;
   H.glev.resize(h->G);
-  const bool need_d = h->cfg.alpha > 2 || h->cfg.nu1 > 2 || h->cfg.nu2 > 2;
+  const bool need_d =
+      h->cfg.alpha > 2 || h->cfg.nu1 > 2 || h->cfg.nu2 > 2 || fused_fmg_step<T>(h);
   const bool sr = h->K > 0;
   for (int g = 0; g < h->G; ++g) {
     Level<T>& L = H.glev[g];
@@ -513,7 +525,7 @@ int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
   schedule(c, J);
   int nsd[3];
   for (int d = 0; d < 3; ++d) nsd[d] = c.n * h->len[d] / c.seg;  // segments per dimension
-  const bool need_d = c.alpha > 2 || c.nu1 > 2 || c.nu2 > 2;
+  const bool need_d = c.alpha > 2 || c.nu1 > 2 || c.nu2 > 2 || fused_fmg_step<T>(h);
   H.slev.resize(K + 1);
   for (int k = 1; k <= K; ++k) {
     Level<T>& L = H.slev[k];
@@ -676,24 +688,26 @@ int resid_restrict(sr_fmg_s* h, const Level<T>& F, const T* u, FieldT<T> f, cons
 template <typename T>
 constexpr bool kFirstResidual = sizeof(T) == 8;
 
-// r_ready: L.r already holds the first residual D^-1 (f - A u) (written with
-// the level's coarse right-hand side), so the first residual pass is skipped
+// r_first: the first residual D^-1 (f - A u) is already formed there (L.r,
+// written with the level's coarse right-hand side, or L.d, written by the
+// fused FMG step), so the first residual pass is skipped; r_first == L.d only
+// with c.nu == 2
 template <typename T>
 int smooth(sr_fmg_s* h, const Level<T>& L, const Cheb& c, T* u, FieldT<T> f, cudaStream_t s,
-           bool r_ready = false) {
+           const T* r_first = nullptr) {
   if (c.nu == 0) return SR_OK;
   const double cells = L.tot_cells;
   const double w = sizeof(T);
   if (c.nu == 2) {
-    if (!r_ready)
+    if (!r_first)
       LAUNCH(h, kind_of<T>(kChebResidual), cells, ops_smooth(h), 3 * w, s,
              op_cheb_residual<T>(h, L.view, u, L.r, f, s));
     LAUNCH(h, kind_of<T>(kCheb2Update), cells, ops_smooth(h), 3 * w, s,
-           op_cheb2_update<T>(h, L.view, u, L.r, c, s));
+           op_cheb2_update<T>(h, L.view, u, r_first ? r_first : L.r, c, s));
     return SR_OK;
   }
   for (int m = 0; m < c.nu; ++m) {
-    if (!(r_ready && m == 0))
+    if (!(r_first && m == 0))
       LAUNCH(h, kind_of<T>(kChebResidual), cells, ops_smooth(h), 3 * w, s,
              op_cheb_residual<T>(h, L.view, u, L.r, f, s));
     const int write_d = (c.nu > 1 && m < c.nu - 1) ? 1 : 0;
@@ -704,11 +718,28 @@ int smooth(sr_fmg_s* h, const Level<T>& L, const Cheb& c, T* u, FieldT<T> f, cud
   return SR_OK;
 }
 
+// S^alpha on level L before the FMG V-cycle from it; returns (in *r_first)
+// the pre-smoother's first residual when the fused step formed it
+template <typename T>
+int fmg_step(sr_fmg_s* h, const Level<T>& L, T* u, FieldT<T> f, cudaStream_t s,
+             const T** r_first) {
+  *r_first = nullptr;
+  if (!fused_fmg_step<T>(h)) return smooth(h, L, h->fmg, u, f, s);
+  const double cells = L.tot_cells;
+  const double w = sizeof(T);
+  LAUNCH(h, kind_of<T>(kChebResidual), cells, ops_smooth(h), 3 * w, s,
+         op_cheb_residual<T>(h, L.view, u, L.r, f, s));
+  LAUNCH(h, kind_of<T>(kChebStep), cells, 8, 4 * w, s,
+         launch_cheb1_next<T>(L.view, u, L.r, L.d, h->fmg.beta[0], s));
+  *r_first = L.d;
+  return SR_OK;
+}
+
 // FASMGV on global level g (Fig. "FAS multigrid V-cycle"); u is the level's
 // u (or the caller's u on the finest plain FP64 level).
 template <typename T>
 int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStream_t s,
-                  bool r_ready = false) {
+                  const T* r_first = nullptr) {
   Level<T>& L = H.glev[g];
   const double w = sizeof(T);
   if (g == 0) {
@@ -718,7 +749,7 @@ int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStrea
     return SR_OK;
   }
   Level<T>& C = H.glev[g - 1];
-  int rc = smooth(h, L, h->pre, u, rhs, s, r_ready);
+  int rc = smooth(h, L, h->pre, u, rhs, s, r_first);
   if (rc) return rc;
   rc = resid_restrict<T>(h, L, u, rhs, C, C.u, C.rho, s);
   if (rc) return rc;
@@ -727,7 +758,7 @@ int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStrea
   const bool cr = kFirstResidual<T> && g - 1 >= 1;
   LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h) + (cr ? 1 : 0), (cr ? 5 : 4) * w, s,
          op_coarse_rhs<T>(h, C.view, L.view, C.u, C.rho, C.rhs, C.t, cr ? C.r : nullptr, s));
-  rc = vcycle_global(h, H, g - 1, C.u, view_global<T>(C, C.rhs), s, cr);
+  rc = vcycle_global(h, H, g - 1, C.u, view_global<T>(C, C.rhs), s, cr ? C.r : nullptr);
   if (rc) return rc;
   LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
          launch_diff<T>(C.view, C.u, C.t, C.rho, s));
@@ -756,9 +787,10 @@ int run_fmg_global(sr_fmg_s* h, Hier<T>& H, const T* ftop, T* utop, cudaStream_t
     LAUNCH(h, kind_of<T>(kProlongSet), L.tot_prolong, 3.75, 1.125 * w, s,
            launch_prolong<T>(H.glev[g - 1].view, ug(g - 1), L.view, ug(g), 0, s));
     FieldT<T> f = view_global<T>(L, fg(g));
-    int rc = smooth(h, L, h->fmg, ug(g), f, s);
+    const T* r_first = nullptr;
+    int rc = fmg_step(h, L, ug(g), f, s, &r_first);
     if (rc) return rc;
-    rc = vcycle_global(h, H, g, ug(g), f, s);
+    rc = vcycle_global(h, H, g, ug(g), f, s, r_first);
     if (rc) return rc;
   }
   return SR_OK;
@@ -802,20 +834,22 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
   for (int k = 1; k <= K; ++k) {
     Level<T>& Lk = H.slev[k];
     // u_k <- Pi u_{k-1} on Omega^C_k u Omega^GSR_k, then S^alpha on Omega^C_k
+    const T* r_first = nullptr;
     {
       const Level<T>& C = (k == 1) ? L0 : H.slev[k - 1];
       LAUNCH(h, kind_of<T>(kProlongSet), Lk.tot_prolong, 3.75, 1.125 * w, s,
              launch_prolong<T>(C.view, C.u, Lk.view, Lk.u, 0, s));
-      int rc = smooth(h, Lk, h->fmg, Lk.u, fview(k), s);
+      int rc = fmg_step(h, Lk, Lk.u, fview(k), s, &r_first);
       if (rc) return rc;
     }
     // FASMGVSR(k): down-leg
     for (int j = k; j >= 1; --j) {
       Level<T>& Lj = H.slev[j];
       const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
-      // below the stage's top level the first residual came with the
-      // level's right-hand side (float64)
-      int rc = smooth(h, Lj, h->pre, Lj.u, rhs, s, kFirstResidual<T> && j < k);
+      // at the stage's top level the first residual may come from the fused
+      // FMG step; below it, with the level's right-hand side (float64)
+      const T* rf = (j == k) ? r_first : (kFirstResidual<T> ? Lj.r : nullptr);
+      int rc = smooth(h, Lj, h->pre, Lj.u, rhs, s, rf);
       if (rc) return rc;
       if (j > 1) {
         Level<T>& C = H.slev[j - 1];
@@ -840,7 +874,8 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
     LAUNCH(h, kind_of<T>(kTransitionRhs), L0.tot_cells, ops_rhs(h) + (cr ? 1 : 0),
            (cr ? 5 : 4) * w, s,
            op_transition_rhs<T>(h, L0.view, L0.t, L0.rho, L0.u, L0.rhs, cr ? L0.r : nullptr, s));
-    int rc = vcycle_global(h, H, h->G - 1, L0.u, view_global<T>(L0, L0.rhs), s, cr);
+    int rc = vcycle_global(h, H, h->G - 1, L0.u, view_global<T>(L0, L0.rhs), s,
+                           cr ? L0.r : nullptr);
     if (rc) return rc;
     // up-leg
     for (int j = 1; j <= k; ++j) {

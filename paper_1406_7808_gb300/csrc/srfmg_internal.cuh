@@ -78,6 +78,13 @@ cudaError_t launch_cheb2_update(const LevelView& L, T* u, const T* r, double a, 
                                 cudaStream_t s);
 // One step of the Chebyshev recurrence: d = alpha d + beta r, u += d
 // (d untouched and unused when write_d == 0 and alpha == 0).
+// A degree-1 step u += beta r that also forms the residual the next
+// smoothing of the level starts from, r2 = D^-1 (f - A u_new) =
+// (1 - beta) r + (beta / 6) (sum of the neighbours of r) (7-point operator;
+// r2 must not alias r).
+template <typename T>
+cudaError_t launch_cheb1_next(const LevelView& L, T* u, const T* r, T* r2, double beta,
+                              cudaStream_t s);
 template <typename T>
 cudaError_t launch_cheb_step(const LevelView& L, T* u, T* d, const T* r, double alpha,
                              double beta, int write_d, cudaStream_t s);
