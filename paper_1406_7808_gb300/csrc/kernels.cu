@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(kZThreads) k_cheb_residual_zm(LevelView L,
                                                                const T* __restrict__ u,
                                                                T* __restrict__ r, FieldT<T> f,
                                                                T cf, T sixth, ZTiles tiles) {
+  grid_dep_wait();
   __shared__ BoxDesc B, FB;
   if (threadIdx.x == 0) {
     B = L.boxes[blockIdx.y];
@@ -214,6 +215,7 @@ template <typename T>
 __global__ void __launch_bounds__(kZThreads) k_cheb2_update_zm(LevelView L, T* __restrict__ u,
                                                               const T* __restrict__ r, T a, T b,
                                                               ZTiles tiles) {
+  grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
@@ -250,6 +252,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 7) k_cheb_residual(LevelView L, const T* __restrict__ u,
                                                             T* __restrict__ r, FieldT<T> f,
                                                             T cf, T sixth) {
+  grid_dep_wait();
   __shared__ BoxDesc B, FB;
   if (threadIdx.x == 0) {
     B = L.boxes[blockIdx.y];
@@ -274,6 +277,7 @@ __global__ void __launch_bounds__(kThreads, 7) k_cheb_residual(LevelView L, cons
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 8) k_cheb2_update(LevelView L, T* __restrict__ u,
                                                            const T* __restrict__ r, T a, T b) {
+  grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
@@ -301,6 +305,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_cheb1_next(LevelView L, T* __re
                                                          const T* __restrict__ r,
                                                          T* __restrict__ r2, T beta, T keep,
                                                          T b6) {
+  grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
@@ -323,6 +328,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_apply(LevelView L, const T* __restrict__ u,
                                                     T* __restrict__ out, FieldT<T> f,
                                                     int residual, T c6, T cn, Fk<T> k) {
+  grid_dep_wait();
   __shared__ BoxDesc B, FB;
   if (threadIdx.x == 0) {
     B = L.boxes[blockIdx.y];
@@ -355,6 +361,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_resid_restrict(LevelView F, con
                                                              T* __restrict__ uhat_dst,
                                                              T* __restrict__ rho_dst, T cS, T cO,
                                                              T eighth, Fk<T> k) {
+  grid_dep_wait();
   __shared__ BoxDesc B, FB, CB;
   if (threadIdx.x == 0) {
     B = F.boxes[blockIdx.y];
@@ -443,6 +450,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_coarse_rhs(LevelView C, LevelVi
                                                          T* __restrict__ rhs, T* __restrict__ t,
                                                          T* __restrict__ r, double c6, double cn,
                                                          double cr, Fk<double> k) {
+  grid_dep_wait();
   __shared__ BoxDesc B, FBx;
   if (threadIdx.x == 0) {
     B = C.boxes[blockIdx.y];
@@ -476,6 +484,7 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
                                                              T* __restrict__ rhs,
                                                              T* __restrict__ r, double c6,
                                                              double cn, double cr) {
+  grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[0];
   __syncthreads();
@@ -499,6 +508,7 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
 template <typename T>
 __global__ void k_coarse_solve(LevelView L, const double* __restrict__ minv, FieldT<T> f,
                                T* __restrict__ u, Fk<double> k) {
+  grid_dep_wait();
   const BoxDesc B = L.boxes[0];
   const BoxDesc FB = f.boxes[0];
   const int nx = L.nx, ny = L.ny, m = nx * ny * L.nz;
@@ -530,6 +540,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict_global(Dims fd, const T* 
                                                               T* __restrict__ fc, int check,
                                                               unsigned int* status, T eighth,
                                                               Fk<T> k) {
+  grid_dep_wait();
   const int cx = fd.x / 2, cy = fd.y / 2, cz = fd.z / 2;
   const long long ncell = (long long)cx * cy * cz;
   bool bad = false;
@@ -558,6 +569,7 @@ __global__ void __launch_bounds__(kThreads) k_defect(Dims g, const double* __res
                                                      const double* __restrict__ u,
                                                      float* __restrict__ d, unsigned int* status,
                                                      double c6, double cn) {
+  grid_dep_wait();
   const long long ncell = (long long)g.x * g.y * g.z;
   const long long sy = g.x, sz = (long long)g.x * g.y;
   bool bad = false;
@@ -595,6 +607,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_norm(Dims g, const double* _
                                                          unsigned long long* norm,
                                                          unsigned int* status, double c6,
                                                          double cn) {
+  grid_dep_wait();
   const long long ncell = (long long)g.x * g.y * g.z;
   const long long sy = g.x, sz = (long long)g.x * g.y;
   unsigned long long m = 0;
@@ -636,6 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_norm(Dims g, const double* _
 __global__ void __launch_bounds__(kThreads) k_accumulate(long long cells, const float* __restrict__ e,
                                                          double* __restrict__ u, int add,
                                                          Fk<double> k) {
+  grid_dep_wait();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cells;
        i += (long long)gridDim.x * blockDim.x) {
     const double v = widen(e[i]);
@@ -678,6 +692,7 @@ __global__ void __launch_bounds__(kZThreads, 6) k_prolong_zcol(LevelView C, cons
                                                             LevelView F, T* __restrict__ uf,
                                                             int add, T three, T w64, int nplane,
                                                             Fk<T> k) {
+  grid_dep_wait();
   __shared__ BoxDesc B, CB;
   if (threadIdx.x == 0) {
     B = F.boxes[blockIdx.y];
@@ -732,6 +747,7 @@ __global__ void __launch_bounds__(kZThreads, 8) k_cheb_step_zm(LevelView L, T* _
                                                             const T* __restrict__ r, T alpha,
                                                             T beta, int write_d, int nplane,
                                                             Fk<T> k) {
+  grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
@@ -755,6 +771,7 @@ template <typename T>
 __global__ void __launch_bounds__(kZThreads, 8) k_diff_zm(LevelView C, const T* __restrict__ u,
                                                        const T* __restrict__ t,
                                                        T* __restrict__ e, int nplane, T mone) {
+  grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[blockIdx.y];
   __syncthreads();
@@ -780,6 +797,7 @@ __global__ void __launch_bounds__(kZThreads, 8) k_diff_zm(LevelView C, const T* 
 template <typename T>
 __global__ void __launch_bounds__(kZThreads) k_shell_copy(LevelView C, const T* __restrict__ u,
                                                           T* __restrict__ t, int nplane) {
+  grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[blockIdx.y];
   __syncthreads();
@@ -810,6 +828,7 @@ template <typename T>
 __global__ void __launch_bounds__(kZThreads) k_gather_zm(LevelView L, const T* __restrict__ u,
                                                          double* __restrict__ out, int add,
                                                          int nplane, Fk<double> k) {
+  grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
@@ -864,11 +883,12 @@ cudaError_t launch_cheb_residual(const LevelView& L, const T* u, T* r, FieldT<T>
                                  cudaStream_t s) {
   const T cf = T(1.0 / (6.0 * sq(L.n)));
   if (sizeof(T) == 8) {
-    k_cheb_residual<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, cf,
-                                                                     T(1.0 / 6.0));
+    SRFMG_LAUNCH(pdl_launch(k_cheb_residual<T>, grid_for(L, L.max_cells), kThreads, 0, s, L, u, r,
+                            f, cf, T(1.0 / 6.0)));
   } else {
     const ZTiles t = ztiles(L);
-    k_cheb_residual_zm<T><<<zgrid(L, t), kZThreads, 0, s>>>(L, u, r, f, cf, T(1.0 / 6.0), t);
+    SRFMG_LAUNCH(pdl_launch(k_cheb_residual_zm<T>, zgrid(L, t), kZThreads, 0, s, L, u, r, f, cf,
+                            T(1.0 / 6.0), t));
   }
   return cudaGetLastError();
 }
@@ -877,10 +897,12 @@ template <typename T>
 cudaError_t launch_cheb2_update(const LevelView& L, T* u, const T* r, double a, double b,
                                 cudaStream_t s) {
   if (sizeof(T) == 8) {
-    k_cheb2_update<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, T(a), T(b));
+    SRFMG_LAUNCH(pdl_launch(k_cheb2_update<T>, grid_for(L, L.max_cells), kThreads, 0, s, L, u, r,
+                            T(a), T(b)));
   } else {
     const ZTiles t = ztiles(L);
-    k_cheb2_update_zm<T><<<zgrid(L, t), kZThreads, 0, s>>>(L, u, r, T(a), T(b), t);
+    SRFMG_LAUNCH(pdl_launch(k_cheb2_update_zm<T>, zgrid(L, t), kZThreads, 0, s, L, u, r, T(a),
+                            T(b), t));
   }
   return cudaGetLastError();
 }
@@ -888,8 +910,8 @@ cudaError_t launch_cheb2_update(const LevelView& L, T* u, const T* r, double a, 
 template <typename T>
 cudaError_t launch_cheb1_next(const LevelView& L, T* u, const T* r, T* r2, double beta,
                               cudaStream_t s) {
-  k_cheb1_next<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, r2, T(beta),
-                                                                T(1.0 - beta), T(beta / 6.0));
+  SRFMG_LAUNCH(pdl_launch(k_cheb1_next<T>, grid_for(L, L.max_cells), kThreads, 0, s, L, u, r, r2,
+                          T(beta), T(1.0 - beta), T(beta / 6.0)));
   return cudaGetLastError();
 }
 
@@ -897,23 +919,23 @@ template <typename T>
 cudaError_t launch_cheb_step(const LevelView& L, T* u, T* d, const T* r, double alpha,
                              double beta, int write_d, cudaStream_t s) {
   const ZTiles t = ztiles(L);
-  k_cheb_step_zm<T><<<zgrid(L, t), kZThreads, 0, s>>>(L, u, d, r, T(alpha), T(beta), write_d,
-                                                      t.nplane, fk<T>());
+  SRFMG_LAUNCH(pdl_launch(k_cheb_step_zm<T>, zgrid(L, t), kZThreads, 0, s, L, u, d, r, T(alpha),
+                          T(beta), write_d, t.nplane, fk<T>()));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_apply(const LevelView& L, const T* u, T* out, cudaStream_t s) {
   FieldT<T> none{nullptr, L.boxes, 0};
-  k_apply<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, out, none, 0, T(6.0 * sq(L.n)),
-                                                           T(-sq(L.n)), fk<T>());
+  SRFMG_LAUNCH(pdl_launch(k_apply<T>, grid_for(L, L.max_cells), kThreads, 0, s, L, u, out, none, 0,
+                          T(6.0 * sq(L.n)), T(-sq(L.n)), fk<T>()));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_residual(const LevelView& L, const T* u, FieldT<T> f, T* r, cudaStream_t s) {
-  k_apply<T><<<grid_for(L, L.max_cells), kThreads, 0, s>>>(L, u, r, f, 1, T(-6.0 * sq(L.n)),
-                                                           T(sq(L.n)), fk<T>());
+  SRFMG_LAUNCH(pdl_launch(k_apply<T>, grid_for(L, L.max_cells), kThreads, 0, s, L, u, r, f, 1,
+                          T(-6.0 * sq(L.n)), T(sq(L.n)), fk<T>()));
   return cudaGetLastError();
 }
 
@@ -921,31 +943,32 @@ template <typename T>
 cudaError_t launch_resid_restrict(const LevelView& F, const T* u, FieldT<T> f,
                                   const LevelView& C, T* uhat_dst, T* rho_dst, cudaStream_t s) {
   const double n2 = sq(F.n);
-  k_resid_restrict<T><<<grid_for(F, F.max_restrict), kThreads, 0, s>>>(
-      F, u, f, C, uhat_dst, rho_dst, T(-3.0 * n2 / 8.0), T(n2 / 8.0), T(0.125), fk<T>());
+  SRFMG_LAUNCH(pdl_launch(k_resid_restrict<T>, grid_for(F, F.max_restrict), kThreads, 0, s, F, u,
+                          f, C, uhat_dst, rho_dst, T(-3.0 * n2 / 8.0), T(n2 / 8.0), T(0.125),
+                          fk<T>()));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_coarse_rhs(const LevelView& C, const LevelView& F, const T* u, const T* rho,
                               T* rhs, T* t, T* r, cudaStream_t s) {
-  k_coarse_rhs<T><<<grid_for(C, C.max_cells), kThreads, 0, s>>>(
-      C, F, u, rho, rhs, t, r, 6.0 * sq(C.n), -sq(C.n), 1.0 / (6.0 * sq(C.n)), fk<double>());
+  SRFMG_LAUNCH(pdl_launch(k_coarse_rhs<T>, grid_for(C, C.max_cells), kThreads, 0, s, C, F, u, rho,
+                          rhs, t, r, 6.0 * sq(C.n), -sq(C.n), 1.0 / (6.0 * sq(C.n)), fk<double>()));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_shell_copy(const LevelView& C, const T* u, T* t, cudaStream_t s) {
   const ZTiles z = ztiles_stored(C);
-  k_shell_copy<T><<<zgrid(C, z), kZThreads, 0, s>>>(C, u, t, z.nplane);
+  SRFMG_LAUNCH(pdl_launch(k_shell_copy<T>, zgrid(C, z), kZThreads, 0, s, C, u, t, z.nplane));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_transition_rhs(const LevelView& C, const T* t, const T* rho, T* u, T* rhs,
                                   T* r, cudaStream_t s) {
-  k_transition_rhs<T><<<grid_for(C, C.max_cells), kThreads, 0, s>>>(
-      C, t, rho, u, rhs, r, 6.0 * sq(C.n), -sq(C.n), 1.0 / (6.0 * sq(C.n)));
+  SRFMG_LAUNCH(pdl_launch(k_transition_rhs<T>, grid_for(C, C.max_cells), kThreads, 0, s, C, t, rho,
+                          u, rhs, r, 6.0 * sq(C.n), -sq(C.n), 1.0 / (6.0 * sq(C.n))));
   return cudaGetLastError();
 }
 
@@ -953,15 +976,16 @@ template <typename T>
 cudaError_t launch_prolong(const LevelView& C, const T* uc, const LevelView& F, T* uf, int add,
                            cudaStream_t s) {
   const ZTiles z = ztiles_stored(F);  // the prolongation range lies in the stored region
-  k_prolong_zcol<T><<<zgrid(F, z), kZThreads, 0, s>>>(C, uc, F, uf, add, T(3.0), T(1.0 / 64.0),
-                                                      z.nplane, fk<T>());
+  SRFMG_LAUNCH(pdl_launch(k_prolong_zcol<T>, zgrid(F, z), kZThreads, 0, s, C, uc, F, uf, add,
+                          T(3.0), T(1.0 / 64.0), z.nplane, fk<T>()));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaStream_t s) {
   const ZTiles z = ztiles_stored(C);
-  k_diff_zm<T><<<zgrid(C, z), kZThreads, 0, s>>>(C, u, t, e, z.nplane, T(-1.0));
+  SRFMG_LAUNCH(pdl_launch(k_diff_zm<T>, zgrid(C, z), kZThreads, 0, s, C, u, t, e, z.nplane,
+                          T(-1.0)));
   return cudaGetLastError();
 }
 
@@ -971,7 +995,8 @@ cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldT<T
   const int m = L.nx * L.ny * L.nz;
   const int warps_per_block = 8;
   const int blocks = (m + warps_per_block - 1) / warps_per_block;
-  k_coarse_solve<T><<<blocks, warps_per_block * 32, 0, s>>>(L, minv, f, u, fk<double>());
+  SRFMG_LAUNCH(pdl_launch(k_coarse_solve<T>, blocks, warps_per_block * 32, 0, s, L, minv, f, u,
+                          fk<double>()));
   return cudaGetLastError();
 }
 
@@ -979,8 +1004,8 @@ template <typename T>
 cudaError_t launch_restrict_global(Dims fd, const T* ff, T* fc, int check, unsigned int* status,
                                    cudaStream_t s) {
   const long long cells = (long long)(fd.x / 2) * (fd.y / 2) * (fd.z / 2);
-  k_restrict_global<T><<<flat_blocks(cells), kThreads, 0, s>>>(fd, ff, fc, check, status,
-                                                               T(0.125), fk<T>());
+  SRFMG_LAUNCH(pdl_launch(k_restrict_global<T>, flat_blocks(cells), kThreads, 0, s, fd, ff, fc,
+                          check, status, T(0.125), fk<T>()));
   return cudaGetLastError();
 }
 
@@ -988,28 +1013,31 @@ template <typename T>
 cudaError_t launch_gather_genuine(const LevelView& L, const T* u, double* out, int add,
                                   cudaStream_t s) {
   const ZTiles z = ztiles(L);  // the genuine region lies inside the compute region
-  k_gather_zm<T><<<zgrid(L, z), kZThreads, 0, s>>>(L, u, out, add, z.nplane, fk<double>());
+  SRFMG_LAUNCH(pdl_launch(k_gather_zm<T>, zgrid(L, z), kZThreads, 0, s, L, u, out, add, z.nplane,
+                          fk<double>()));
   return cudaGetLastError();
 }
 
 cudaError_t launch_defect(Dims g, int n, const double* f, const double* u, float* d,
                           unsigned int* status, cudaStream_t s) {
   const long long cells = (long long)g.x * g.y * g.z;
-  k_defect<<<flat_blocks(cells), kThreads, 0, s>>>(g, f, u, d, status, -6.0 * sq(n), sq(n));
+  SRFMG_LAUNCH(pdl_launch(k_defect, flat_blocks(cells), kThreads, 0, s, g, f, u, d, status,
+                          -6.0 * sq(n), sq(n)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_resid_norm(Dims g, int n, const double* f, const double* u,
                               unsigned long long* norm, unsigned int* status, cudaStream_t s) {
   const long long cells = (long long)g.x * g.y * g.z;
-  k_resid_norm<<<flat_blocks(cells), kThreads, 0, s>>>(g, f, u, norm, status, -6.0 * sq(n),
-                                                       sq(n));
+  SRFMG_LAUNCH(pdl_launch(k_resid_norm, flat_blocks(cells), kThreads, 0, s, g, f, u, norm, status,
+                          -6.0 * sq(n), sq(n)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_accumulate(long long cells, const float* e, double* u, int add,
                               cudaStream_t s) {
-  k_accumulate<<<flat_blocks(cells), kThreads, 0, s>>>(cells, e, u, add, fk<double>());
+  SRFMG_LAUNCH(pdl_launch(k_accumulate, flat_blocks(cells), kThreads, 0, s, cells, e, u, add,
+                          fk<double>()));
   return cudaGetLastError();
 }
 

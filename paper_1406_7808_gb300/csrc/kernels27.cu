@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kThreads27) k27_apply(LevelView L, const doubl
                                                         double* __restrict__ out,
                                                         FieldT<double> f, int residual, W27 w,
                                                         double n2) {
+  grid_dep_wait();
   __shared__ BoxDesc B, FB;
   if (threadIdx.x == 0) {
     B = L.boxes[blockIdx.y];
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(kThreads27) k27_coarse_rhs(LevelView C, LevelV
                                                              double* __restrict__ t,
                                                              double* __restrict__ r, W27 w,
                                                              double n2, double cr) {
+  grid_dep_wait();
   __shared__ BoxDesc B, FBx;
   if (threadIdx.x == 0) {
     B = C.boxes[blockIdx.y];
@@ -150,6 +152,7 @@ __global__ void __launch_bounds__(kThreads27) k27_transition_rhs(LevelView C,
                                                                  double* __restrict__ rhs,
                                                                  double* __restrict__ r, W27 w,
                                                                  double n2, double cr) {
+  grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[0];
   __syncthreads();
@@ -173,6 +176,7 @@ __global__ void __launch_bounds__(kThreads27) k27_resid_norm(LevelView L,
                                                              unsigned long long* norm,
                                                              unsigned int* status, W27 w,
                                                              double n2) {
+  grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = L.boxes[0];
   __syncthreads();
@@ -296,6 +300,7 @@ __global__ void __launch_bounds__(kZ27Threads) k27_column(LevelView L,
                                                           FieldT<double> f, double c0,
                                                           double cf, double ce, double cc,
                                                           double one, int nplane) {
+  grid_dep_wait();
   __shared__ BoxDesc B, FB;
   if (threadIdx.x == 0) {
     B = L.boxes[blockIdx.y];
@@ -340,6 +345,7 @@ __global__ void __launch_bounds__(kThreads27) k27_restrict_pair(LevelView F,
                                                                 LevelView C,
                                                                 double* __restrict__ uhat_dst,
                                                                 double* __restrict__ rho_dst) {
+  grid_dep_wait();
   __shared__ BoxDesc B, CB;
   if (threadIdx.x == 0) {
     B = F.boxes[blockIdx.y];
@@ -391,9 +397,9 @@ double sq27(int n) { return (double)n * (double)n; }
 
 cudaError_t launch27_cheb_residual(const LevelView& L, const double* u, double* r,
                                    FieldT<double> f, W27 w, cudaStream_t s) {
-  k27_column<0><<<zgrid27(L), kZ27Threads, 0, s>>>(L, u, r, f, 1.0 / (w.w0 * sq27(L.n)),
-                                                   w.w1 / w.w0, w.w2 / w.w0, w.w3 / w.w0, 1.0,
-                                                   nplane27(L));
+  SRFMG_LAUNCH(pdl_launch(k27_column<0>, zgrid27(L), kZ27Threads, 0, s, L, u, r, f,
+                          1.0 / (w.w0 * sq27(L.n)), w.w1 / w.w0, w.w2 / w.w0, w.w3 / w.w0, 1.0,
+                          nplane27(L)));
   return cudaGetLastError();
 }
 
@@ -401,53 +407,55 @@ cudaError_t launch27_cheb2_update(const LevelView& L, double* u, const double* r
                                   double c2, W27 w, cudaStream_t s) {
   // W r = (w1 sf + w2 se + w3 sc)/w0 enters with the factor -c2
   FieldT<double> none{nullptr, L.boxes, 0};
-  k27_column<1><<<zgrid27(L), kZ27Threads, 0, s>>>(L, r, u, none, a, -c2 * w.w1 / w.w0,
-                                                   -c2 * w.w2 / w.w0, -c2 * w.w3 / w.w0, 1.0,
-                                                   nplane27(L));
+  SRFMG_LAUNCH(pdl_launch(k27_column<1>, zgrid27(L), kZ27Threads, 0, s, L, r, u, none, a,
+                          -c2 * w.w1 / w.w0, -c2 * w.w2 / w.w0, -c2 * w.w3 / w.w0, 1.0,
+                          nplane27(L)));
   return cudaGetLastError();
 }
 
 cudaError_t launch27_residual_zm(const LevelView& L, const double* u, FieldT<double> f,
                                  double* r, W27 w, cudaStream_t s) {
   const double n2 = sq27(L.n);
-  k27_column<2><<<zgrid27(L), kZ27Threads, 0, s>>>(L, u, r, f, -n2 * w.w0, n2 * w.w1,
-                                                   n2 * w.w2, n2 * w.w3, 1.0, nplane27(L));
+  SRFMG_LAUNCH(pdl_launch(k27_column<2>, zgrid27(L), kZ27Threads, 0, s, L, u, r, f, -n2 * w.w0,
+                          n2 * w.w1, n2 * w.w2, n2 * w.w3, 1.0, nplane27(L)));
   return cudaGetLastError();
 }
 
 cudaError_t launch27_restrict_pair(const LevelView& F, const double* u, const double* r,
                                    const LevelView& C, double* uhat_dst, double* rho_dst,
                                    cudaStream_t s) {
-  k27_restrict_pair<<<grid27(F, F.max_restrict), kThreads27, 0, s>>>(F, u, r, C, uhat_dst,
-                                                                     rho_dst);
+  SRFMG_LAUNCH(pdl_launch(k27_restrict_pair, grid27(F, F.max_restrict), kThreads27, 0, s, F, u, r,
+                          C, uhat_dst, rho_dst));
   return cudaGetLastError();
 }
 
 cudaError_t launch27_apply(const LevelView& L, const double* u, double* out, W27 w,
                            cudaStream_t s) {
   FieldT<double> none{nullptr, L.boxes, 0};
-  k27_apply<<<grid27(L, L.max_cells), kThreads27, 0, s>>>(L, u, out, none, 0, w, sq27(L.n));
+  SRFMG_LAUNCH(pdl_launch(k27_apply, grid27(L, L.max_cells), kThreads27, 0, s, L, u, out, none, 0,
+                          w, sq27(L.n)));
   return cudaGetLastError();
 }
 
 cudaError_t launch27_residual(const LevelView& L, const double* u, FieldT<double> f, double* r,
                               W27 w, cudaStream_t s) {
-  k27_apply<<<grid27(L, L.max_cells), kThreads27, 0, s>>>(L, u, r, f, 1, w, sq27(L.n));
+  SRFMG_LAUNCH(pdl_launch(k27_apply, grid27(L, L.max_cells), kThreads27, 0, s, L, u, r, f, 1, w,
+                          sq27(L.n)));
   return cudaGetLastError();
 }
 
 cudaError_t launch27_coarse_rhs(const LevelView& C, const LevelView& F, const double* u,
                                 const double* rho, double* rhs, double* t, double* r, W27 w,
                                 cudaStream_t s) {
-  k27_coarse_rhs<<<grid27(C, C.max_stored), kThreads27, 0, s>>>(
-      C, F, u, rho, rhs, t, r, w, sq27(C.n), 1.0 / (w.w0 * sq27(C.n)));
+  SRFMG_LAUNCH(pdl_launch(k27_coarse_rhs, grid27(C, C.max_stored), kThreads27, 0, s, C, F, u, rho,
+                          rhs, t, r, w, sq27(C.n), 1.0 / (w.w0 * sq27(C.n))));
   return cudaGetLastError();
 }
 
 cudaError_t launch27_transition_rhs(const LevelView& C, const double* t, const double* rho,
                                     double* u, double* rhs, double* r, W27 w, cudaStream_t s) {
-  k27_transition_rhs<<<grid27(C, C.max_cells), kThreads27, 0, s>>>(
-      C, t, rho, u, rhs, r, w, sq27(C.n), 1.0 / (w.w0 * sq27(C.n)));
+  SRFMG_LAUNCH(pdl_launch(k27_transition_rhs, grid27(C, C.max_cells), kThreads27, 0, s, C, t, rho,
+                          u, rhs, r, w, sq27(C.n), 1.0 / (w.w0 * sq27(C.n))));
   return cudaGetLastError();
 }
 
@@ -457,7 +465,8 @@ cudaError_t launch27_resid_norm(const LevelView& L, const double* f, const doubl
   long long blocks = ((long long)L.nx * L.ny * L.nz + kThreads27 - 1) / kThreads27;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
   if (blocks < 1) blocks = 1;
-  k27_resid_norm<<<(unsigned)blocks, kThreads27, 0, s>>>(L, f, u, norm, status, w, sq27(L.n));
+  SRFMG_LAUNCH(pdl_launch(k27_resid_norm, (unsigned)blocks, kThreads27, 0, s, L, f, u, norm,
+                          status, w, sq27(L.n)));
   return cudaGetLastError();
 }
 

@@ -61,6 +61,41 @@ struct FieldT {
 };
 using FieldView = FieldT<double>;
 
+// ---- launches.  Every kernel of the library is launched with programmatic
+// stream serialization (Programmatic Dependent Launch): its grid may be
+// scheduled while the kernel before it on the stream drains, and each of its
+// blocks first waits, in grid_dep_wait, until that kernel has completed and
+// its writes are visible.  As every block of every kernel waits before any
+// other work (or early return), completion stays ordered along the stream.
+// Launched without the attribute (or after a copy or an event) the wait
+// returns at once.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
+// return the launch status from the enclosing launcher on failure
+#define SRFMG_LAUNCH(call)                         \
+  do {                                             \
+    const cudaError_t launch_status_ = (call);     \
+    if (launch_status_ != cudaSuccess) return launch_status_; \
+  } while (0)
+
 enum Region { kCompute = 0, kProlong = 1, kRestrict = 2, kGenuine = 3 };
 
 // ---- launchers; all enqueue on stream and return the launch status.  T is
