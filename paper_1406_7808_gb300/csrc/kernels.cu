@@ -243,6 +243,42 @@ __global__ void __launch_bounds__(kZThreads) k_cheb2_update_zm(LevelView L, T* _
   }
 }
 
+// Column form of k_cheb1_next (float32, HBM bound): u += beta r and
+// r2 = (1 - beta) r + (beta / 6) (sum of the neighbours of r).
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_cheb1_next_zm(LevelView L, T* __restrict__ u,
+                                                            const T* __restrict__ r,
+                                                            T* __restrict__ r2, T beta, T keep,
+                                                            T b6, ZTiles tiles) {
+  grid_dep_wait();
+  __shared__ BoxDesc B;
+  if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
+  __syncthreads();
+  int x, y, z0, z1;
+  if (!ztile(B, tiles, x, y, z0, z1)) return;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const long long sy = B.sy, sz = B.sz;
+  long long c = at(B, x, y, z0);
+  T rc = r[c];
+  T rm = (z0 > 0) ? r[c - sz] : negx(rc);
+  for (int z = z0; z < z1; ++z) {
+    const T m = negx(rc);
+    const T rp = (z < nz - 1) ? r[c + sz] : m;
+    T v[6];
+    v[0] = (x > 0) ? r[c - 1] : m;
+    v[1] = (x < nx - 1) ? r[c + 1] : m;
+    v[2] = (y > 0) ? r[c - sy] : m;
+    v[3] = (y < ny - 1) ? r[c + sy] : m;
+    v[4] = rm;
+    v[5] = rp;
+    u[c] = fma(beta, rc, u[c]);
+    r2[c] = fma6(b6, v, keep * rc);
+    rm = rc;
+    rc = rp;
+    c += sz;
+  }
+}
+
 // Per-cell form of the two smoother passes (one thread per cell, x-fastest
 // over the box's compute region), used for float64: there the float64 pipe
 // binds and fully packed warps matter more than the index arithmetic the
@@ -910,8 +946,15 @@ cudaError_t launch_cheb2_update(const LevelView& L, T* u, const T* r, double a, 
 template <typename T>
 cudaError_t launch_cheb1_next(const LevelView& L, T* u, const T* r, T* r2, double beta,
                               cudaStream_t s) {
-  SRFMG_LAUNCH(pdl_launch(k_cheb1_next<T>, grid_for(L, L.max_cells), kThreads, 0, s, L, u, r, r2,
-                          T(beta), T(1.0 - beta), T(beta / 6.0)));
+  // float64: per-cell form (float64 pipe bound); float32: column form
+  if (sizeof(T) == 8) {
+    SRFMG_LAUNCH(pdl_launch(k_cheb1_next<T>, grid_for(L, L.max_cells), kThreads, 0, s, L, u, r,
+                            r2, T(beta), T(1.0 - beta), T(beta / 6.0)));
+  } else {
+    const ZTiles t = ztiles(L);
+    SRFMG_LAUNCH(pdl_launch(k_cheb1_next_zm<T>, zgrid(L, t), kZThreads, 0, s, L, u, r, r2,
+                            T(beta), T(1.0 - beta), T(beta / 6.0), t));
+  }
   return cudaGetLastError();
 }
 

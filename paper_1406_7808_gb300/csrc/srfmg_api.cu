@@ -362,8 +362,7 @@ int dalloc(sr_fmg_s* h, T** p, size_t count) {
 // into the level's d, and the pre-smoother starts from it.
 template <typename T>
 bool fused_fmg_step(const sr_fmg_s* h) {
-  return sizeof(T) == 8 && !h->op27 && h->fmg.nu == 1 && h->fmg.alpha[0] == 0.0 &&
-         h->pre.nu == 2;
+  return !h->op27 && h->fmg.nu == 1 && h->fmg.alpha[0] == 0.0 && h->pre.nu == 2;
 }
 
 BoxDesc whole_box(const int nd[3]) {
