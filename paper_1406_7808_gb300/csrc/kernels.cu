@@ -582,9 +582,8 @@ __global__ void __launch_bounds__(kThreads) k_restrict_global(Dims fd, const T* 
   bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
        i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % cx);
-    const long long t = i / cx;
-    const int y = (int)(t % cy), z = (int)(t / cy);
+    int x, y, z;
+    split3(i, cx, cy, x, y, z);
     const long long py = fd.x, pz = (long long)fd.x * fd.y;
     const long long f0 = (2 * z) * pz + (2 * y) * py + 2 * x;
     const T a[8] = {ff[f0], ff[f0 + 1], ff[f0 + py], ff[f0 + py + 1],
@@ -617,9 +616,8 @@ __global__ void __launch_bounds__(kThreads) k_defect(Dims g, const double* __res
       d[i] = (float)fv;
       continue;
     }
-    const int x = (int)(i % g.x);
-    const long long t = i / g.x;
-    const int y = (int)(t % g.y), z = (int)(t / g.y);
+    int x, y, z;
+    split3(i, g.x, g.y, x, y, z);
     const double uc = u[i];
     const double m = negx(uc);
     double v[6];
@@ -652,9 +650,8 @@ __global__ void __launch_bounds__(kThreads) k_resid_norm(Dims g, const double* _
        i += (long long)gridDim.x * blockDim.x) {
     double r = f[i];
     if (u) {
-      const int x = (int)(i % g.x);
-      const long long t = i / g.x;
-      const int y = (int)(t % g.y), z = (int)(t / g.y);
+      int x, y, z;
+      split3(i, g.x, g.y, x, y, z);
       const double uc = u[i];
       const double mu = negx(uc);
       double v[6];

@@ -185,9 +185,8 @@ __global__ void __launch_bounds__(kThreads27) k27_resid_norm(LevelView L,
   bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
        i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % L.nx);
-    const long long t = i / L.nx;
-    const int y = (int)(t % L.ny), z = (int)(t / L.ny);
+    int x, y, z;
+    split3(i, L.nx, L.ny, x, y, z);
     double r = f[i];
     if (u) r -= op27(u, B, L, w, n2, x, y, z);
     bad |= !finite27(r);

@@ -73,6 +73,23 @@ __device__ __forceinline__ void grid_dep_wait() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// (x, y, z) of flat index i of an nx x ny x nz grid, C order.  Grids of
+// fewer than 2^32 cells (up to 1625^3) take 32-bit divisions, several times
+// cheaper than the 64-bit ones the integer pipe emulates.
+__device__ __forceinline__ void split3(long long i, int nx, int ny, int& x, int& y, int& z) {
+  if (i <= 0xffffffffLL) {
+    const unsigned ui = (unsigned)i, t = ui / (unsigned)nx;
+    x = (int)(ui - t * (unsigned)nx);
+    y = (int)(t % (unsigned)ny);
+    z = (int)(t / (unsigned)ny);
+  } else {
+    const long long t = i / nx;
+    x = (int)(i - t * nx);
+    y = (int)(t % ny);
+    z = (int)(t / ny);
+  }
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                               cudaStream_t s, Args&&... args) {
