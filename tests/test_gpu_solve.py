@@ -52,6 +52,11 @@ SR_CASES = [
     (96, dict(seg=24, K=3, A=6, B=0)),
     (64, dict(seg=16, K=3, J=[2, 4, 8])),      # maximum buffer schedule, Sec. 5.2.1
     (128, dict(seg=32, K=3, J=[4, 8, 16])),
+    # other smoother degrees: the FMG step without the fused residual, the
+    # coarse levels' first residual inside the recurrence (nu1 = 3) and
+    # with a degree-1 pre-smoother
+    (32, dict(seg=8, K=2, J=[4, 4], alpha=2, nu1=3, nu2=1)),
+    (32, dict(seg=16, K=2, J=[4, 4], nu1=1, nu2=2)),
 ]
 
 
