@@ -372,11 +372,12 @@ def run_ours(args):
     del fh, uh
 
     mixed = batch = None
-    paper = None
+    paper = adjoint = None
     if not args.no_extras:
         mixed = measure_mixed(args, timed_fn=ranks_max, world=world, rank=rank)
         batch = measure_batch(args, ranks_max, world)
         paper = measure_paper(args, ranks_max, world)
+        adjoint = measure_adjoint(args, ranks_max, world, rank)
 
     if rank != 0:
         if world > 1:
@@ -441,6 +442,7 @@ def run_ours(args):
         "vcycle_solve_fp64_256": vs,
         "mixed_sr_512": mixed,
         "batched_mixed": batch,
+        "adjoint_sr_fp64_256": adjoint,
     }
     if mixed is not None and hbm:
         mixed["hbm_frac_of_measured"] = mixed["hbm_gbs"] / hbm
@@ -562,6 +564,33 @@ def measure_mixed(args, timed_fn, world, rank):
         nbytes = profiled_bytes(s, ft, ut)
     return {"n": n, "config": workloads.config(kw), "dof_s": world * n ** 3 / (ms / 1e3),
             "ms": ms, "hbm_gbs": nbytes / (ms / 1e3) / 1e9, "u": u}
+
+
+def measure_adjoint(args, timed_fn, world, rank):
+    """The differentiable solve at 256^3 (SR-FMG FP64, the benchmark's
+    segments): one step = forward solve, loss 0.5 ||u - u_target||^2 and
+    the backward pass (a second SR-FMG solve on u - u_target), through
+    torch.autograd."""
+    import torch
+    from paper_1406_7808_gb300 import inputs, srfmg
+    n = N
+    ft = torch.from_numpy(inputs.manufactured(n, rank)[0]).cuda().requires_grad_(True)
+    target = torch.from_numpy(inputs.target(n)).cuda()
+    with srfmg.Solver(n, **SR) as s:
+        def step():
+            if ft.grad is not None:
+                ft.grad = None
+            u = srfmg.solve_autograd(ft, s)
+            loss = 0.5 * ((u - target) ** 2).sum()
+            loss.backward()
+        for _ in range(max(1, args.warmup)):
+            step()
+        steps = max(2, min(args.steps, 5))
+        total = timed_fn(_time_loop(step, steps))
+        ms = total / steps
+    return {"n": n, "config": dict(SR), "steps": steps, "ms_per_step": ms,
+            "dof_s": world * n ** 3 / (ms / 1e3),
+            "note": "forward + backward solves, loss and gradient on the device"}
 
 
 def measure_batch(args, timed_fn, world):
