@@ -453,8 +453,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, "n": N, **SR, "J": J,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2: f is 134 MB and each solve sweeps 2.2 GB of "
-                         "workspace",
+                   "l2": "inputs larger than L2: f is 134 MB and each solve sweeps about 3 GB "
+                         "of workspace",
                    "plain_fmg_dof_s": world * N ** 3 / (plain_ms / 1e3),
                    "plain_fmg_ms_per_step": plain_ms},
         "e2e": {"value": world * N ** 3 / e2e_s, "unit": "DOF/s",
