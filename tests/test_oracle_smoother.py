@@ -65,3 +65,27 @@ def test_first_coarse_smoother_step_from_restricted_residual(oracle_mod, geo):
     a = oracle_mod.smooth(uc, rhs, 2, **geo)
     b = oracle_mod.smooth(uc, rho + (rhs - rho), 2, **geo)
     assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(a).max())
+
+
+@pytest.mark.parametrize("interval", [(1.0 / 6.0, 1.0), (0.1, 1.1)])
+def test_fused_fmg_step_residual(oracle_mod, interval):
+    """The degree-1 step u1 = u + beta r (r = D^-1 (f - A u), beta = 1/theta
+    of the Chebyshev interval, Sec. 5.1 smoother) leaves the residual
+    D^-1 (f - A u1) = r - beta D^-1 A r = (1 - beta) r + (beta/6) S(r),
+    S the 7-point neighbour sum with the boundary ghosts of A; the FMG step
+    kernel forms the next smoother's first residual this way.  Checked on the
+    oracle's own smoother and operator, with S(r) = 6 r - A r / n^2."""
+    rng = np.random.default_rng(11)
+    n = 12
+    u = rng.standard_normal((n, n, n))
+    f = rng.standard_normal((n, n, n)) * n * n
+    lo, hi = interval
+    beta = 1.0 / (lo + hi)  # 1 / theta, lambda_max(D^-1 A) = 2
+    d = 6.0 * n * n
+    r = oracle_mod.residual(u, f) / d
+    u1 = oracle_mod.smooth(u, f, 1, lo, hi)
+    assert np.allclose(u1, u + beta * r, rtol=0, atol=1e-13 * np.abs(u).max())
+    literal = oracle_mod.residual(u1, f) / d
+    s = 6.0 * r - oracle_mod.apply(r) / (n * n)
+    fused = (1.0 - beta) * r + (beta / 6.0) * s
+    assert np.abs(literal - fused).max() <= 1e-12 * np.abs(r).max()
