@@ -803,7 +803,8 @@ __global__ void __launch_bounds__(kZThreads, 8) k_cheb_step_zm(LevelView L, T* _
 template <typename T>
 __global__ void __launch_bounds__(kZThreads, 8) k_diff_zm(LevelView C, const T* __restrict__ u,
                                                        const T* __restrict__ t,
-                                                       T* __restrict__ e, int nplane, T mone) {
+                                                       T* __restrict__ e, int nplane, T mone,
+                                                       int prolong_range) {
   grid_dep_wait();
   __shared__ BoxDesc B;
   if (threadIdx.x == 0) B = C.boxes[blockIdx.y];
@@ -811,10 +812,14 @@ __global__ void __launch_bounds__(kZThreads, 8) k_diff_zm(LevelView C, const T* 
   const int nd[3] = {C.nx, C.ny, C.nz};
   const bool shell = B.ox < B.lo[0];
   int lo[3], hi[3];
+  if (prolong_range) {
+    region_of(B, kProlong, lo, hi);
+  } else {
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    lo[d] = shell ? max(B.lo[d] - 1, 0) : B.lo[d];
-    hi[d] = shell ? min(B.hi[d] + 1, nd[d]) : B.hi[d];
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = shell ? max(B.lo[d] - 1, 0) : B.lo[d];
+      hi[d] = shell ? min(B.hi[d] + 1, nd[d]) : B.hi[d];
+    }
   }
   int x, y, z0, z1;
   if (!zcolumn(lo, hi, nplane, x, y, z0, z1)) return;
@@ -1022,10 +1027,11 @@ cudaError_t launch_prolong(const LevelView& C, const T* uc, const LevelView& F, 
 }
 
 template <typename T>
-cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaStream_t s) {
+cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaStream_t s,
+                        int prolong_range) {
   const ZTiles z = ztiles_stored(C);
   SRFMG_LAUNCH(pdl_launch(k_diff_zm<T>, zgrid(C, z), kZThreads, 0, s, C, u, t, e, z.nplane,
-                          T(-1.0)));
+                          T(-1.0), prolong_range));
   return cudaGetLastError();
 }
 
@@ -1102,7 +1108,8 @@ cudaError_t launch_accumulate(long long cells, const float* e, double* u, int ad
                                                 T*, cudaStream_t);                             \
   template cudaError_t launch_prolong<T>(const LevelView&, const T*, const LevelView&, T*, int, \
                                          cudaStream_t);                                        \
-  template cudaError_t launch_diff<T>(const LevelView&, const T*, const T*, T*, cudaStream_t);  \
+  template cudaError_t launch_diff<T>(const LevelView&, const T*, const T*, T*, cudaStream_t,   \
+                                      int);                                                    \
   template cudaError_t launch_coarse_solve<T>(const LevelView&, const double*, FieldT<T>, T*,  \
                                               cudaStream_t);                                   \
   template cudaError_t launch_restrict_global<T>(Dims, const T*, T*, int, unsigned int*,       \

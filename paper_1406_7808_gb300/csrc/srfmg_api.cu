@@ -68,6 +68,13 @@ struct Hier {
   // one as compute region and grown by two as prolongation range, trim_u the
   // genuine region as compute region (clipped to the full regions).
   Geom trim_r, trim_u;
+  // The coarser SR levels j < K cut the same way for the last stage's
+  // up-leg, from the cells U_j that the trimmed correction of level j + 1
+  // reads: ctrim_u[j] has U_j inside the compute region as compute region
+  // (the post-smoother's update) and U_j as prolongation range (the cells
+  // of w - t formed); ctrim_r[j] has U_j grown by one as compute region (the
+  // residual) and by two as prolongation range (the correction onto level j).
+  std::vector<Geom> ctrim_r, ctrim_u;
 };
 
 struct Cheb {
@@ -601,6 +608,44 @@ int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
       if ((rc = dalloc(h, &L.f, (size_t)cells_of(L)))) return rc;
     }
   }
+  // the coarse levels' last-stage regions, from the finest level's trim down
+  H.ctrim_r.assign(K + 1, Geom{});
+  H.ctrim_u.assign(K + 1, Geom{});
+  auto floor_half = [](int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); };
+  for (int j = K - 1; j >= 1; --j) {
+    const Level<T>& L = H.slev[j];
+    const Geom& F = (j + 1 == K) ? H.trim_r : H.ctrim_r[j + 1];
+    Geom& R = H.ctrim_r[j];
+    Geom& U = H.ctrim_u[j];
+    R.n = U.n = L.n;
+    for (int d = 0; d < 3; ++d) R.nd[d] = U.nd[d] = L.nd[d];
+    R.hboxes = U.hboxes = L.hboxes;
+    for (size_t i = 0; i < L.hboxes.size(); ++i) {
+      const BoxDesc& c = L.hboxes[i];
+      const BoxDesc& f = F.hboxes[i];
+      BoxDesc& r = R.hboxes[i];
+      BoxDesc& u = U.hboxes[i];
+      for (int d = 0; d < 3; ++d) {
+        // the prolongation of fine cells [a, b) reads coarse cells
+        // floor((a - 1) / 2) .. floor(b / 2), inside the domain and the
+        // coarse box's stored cells
+        int ulo = floor_half(f.plo[d] - 1), uhi = floor_half(f.phi[d]) + 1;
+        ulo = std::max(ulo, std::max(c.lo[d] - 1, 0));
+        uhi = std::min(uhi, std::min(c.hi[d] + 1, L.nd[d]));
+        u.lo[d] = std::max(c.lo[d], ulo);
+        u.hi[d] = std::min(c.hi[d], uhi);
+        u.plo[d] = ulo;
+        u.phi[d] = uhi;
+        r.lo[d] = std::max(c.lo[d], ulo - 1);
+        r.hi[d] = std::min(c.hi[d], uhi + 1);
+        r.plo[d] = std::max(c.plo[d], ulo - 2);
+        r.phi[d] = std::min(c.phi[d], uhi + 2);
+      }
+    }
+    int rc = finish_level(h, R);
+    if (rc) return rc;
+    if ((rc = finish_level(h, U))) return rc;
+  }
   return SR_OK;
 }
 
@@ -880,21 +925,33 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
     for (int j = 1; j <= k; ++j) {
       Level<T>& Lj = H.slev[j];
       const Level<T>& C = (j == 1) ? L0 : H.slev[j - 1];
-      LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
-             launch_diff<T>(C.view, C.u, C.t, C.rho, s));
+      // The solve's last operations: only the finest level's genuine cells
+      // are returned.  After its correction they depend on u within two
+      // cells and on r within one cell of them; the correction reads the
+      // level below on the cells U its prolongation touches, which depend
+      // on that level's u and r within two and one cells of U, and so on
+      // down the SR levels.  In the last stage the correction, the residual
+      // and the update of every SR level therefore run on those regions only
+      // (every value they keep is computed exactly as on the full box).
+      const bool last = k == K && h->post.nu == 2;
+      if (last && j >= 2) {
+        const Geom& D = H.ctrim_u[j - 1];
+        LAUNCH(h, kind_of<T>(kDiff), D.tot_prolong, 1, 3 * w, s,
+               launch_diff<T>(D.view, C.u, C.t, C.rho, s, 1));
+      } else {
+        LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
+               launch_diff<T>(C.view, C.u, C.t, C.rho, s));
+      }
       const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
-      if (j == K && h->post.nu == 2) {
-        // the solve's last operations on the finest level: only the genuine
-        // cells are returned, and after the correction they depend on u
-        // within two cells and on r within one cell of them, so the
-        // correction, the residual and the update run on those regions only
-        // (every genuine value is computed exactly as on the full box)
-        LAUNCH(h, kind_of<T>(kProlongAdd), H.trim_r.tot_prolong, 3.75, 2.125 * w, s,
-               launch_prolong<T>(C.view, C.rho, H.trim_r.view, Lj.u, 1, s));
-        LAUNCH(h, kind_of<T>(kChebResidual), H.trim_r.tot_cells, ops_smooth(h), 3 * w, s,
-               op_cheb_residual<T>(h, H.trim_r.view, Lj.u, Lj.r, rhs, s));
-        LAUNCH(h, kind_of<T>(kCheb2Update), H.trim_u.tot_cells, ops_smooth(h), 3 * w, s,
-               op_cheb2_update<T>(h, H.trim_u.view, Lj.u, Lj.r, h->post, s));
+      if (last) {
+        const Geom& TR = (j == K) ? H.trim_r : H.ctrim_r[j];
+        const Geom& TU = (j == K) ? H.trim_u : H.ctrim_u[j];
+        LAUNCH(h, kind_of<T>(kProlongAdd), TR.tot_prolong, 3.75, 2.125 * w, s,
+               launch_prolong<T>(C.view, C.rho, TR.view, Lj.u, 1, s));
+        LAUNCH(h, kind_of<T>(kChebResidual), TR.tot_cells, ops_smooth(h), 3 * w, s,
+               op_cheb_residual<T>(h, TR.view, Lj.u, Lj.r, rhs, s));
+        LAUNCH(h, kind_of<T>(kCheb2Update), TU.tot_cells, ops_smooth(h), 3 * w, s,
+               op_cheb2_update<T>(h, TU.view, Lj.u, Lj.r, h->post, s));
         continue;
       }
       LAUNCH(h, kind_of<T>(kProlongAdd), Lj.tot_prolong, 3.75, 2.125 * w, s,

@@ -177,9 +177,12 @@ template <typename T>
 cudaError_t launch_prolong(const LevelView& C, const T* uc, const LevelView& F, T* uf, int add,
                            cudaStream_t s);
 // e = u - t on the stored cells of every box that lie inside the domain (the
-// coarse-grid correction w - t of the FAS V-cycle).
+// coarse-grid correction w - t of the FAS V-cycle); prolong_range != 0: on
+// each box's prolongation range [plo, phi) instead (the trimmed views of the
+// last stage carry the needed cells there).
 template <typename T>
-cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaStream_t s);
+cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaStream_t s,
+                        int prolong_range = 0);
 // Coarsest grid: u = Minv f, Minv the dense float64 inverse (m x m,
 // m = nx ny nz); float64 arithmetic.
 template <typename T>
