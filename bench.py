@@ -1,11 +1,13 @@
 #!/usr/bin/env python
-"""Benchmark: segmental-refinement FMG (FP64) on a 256^3 Poisson problem.
+"""Benchmark: segmental-refinement FMG (FP64) on a 256^3 Poisson problem at
+discretisation error.
 
 One step = one full SR-FMG solve (every step of the method: f hierarchy,
-global FMG to the transition level, K = 3 SR stages over 512 segments of 32^3
-genuine cells with J = 8 buffer cells per side, output) of A u = f with the
-seeded manufactured right-hand side.  Metric: fine-grid DOF/s = n^3 / time
-per solve (whole job: all ranks' DOF over the slowest rank's time).
+global FMG from the exactly solved 16^3 grid to the 32^3 transition level,
+K = 3 SR stages over 512 segments of 32^3 genuine cells with J = (12, 12, 10)
+buffer cells per side, output) of A u = f with the seeded manufactured
+right-hand side.  Metric: fine-grid DOF/s = n^3 / time per solve (whole job:
+all ranks' DOF over the slowest rank's time).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -27,24 +29,27 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_1406_7808_gb300 import workloads  # noqa: E402  (configuration only)
+
 METRIC = "3D Poisson FMG fine-grid DOF/s, SR vs plain, at discretization error; %HBM peak"
-N = 256
-SR = dict(seg=32, K=3, A=8, B=0)
+N = workloads.SR256["n"]
+SR = workloads.config(workloads.SR256)
+PLAIN = workloads.config(workloads.PLAIN256)
+SR_DEPTH2 = workloads.config(workloads.SR256_DEPTH2)
 SEED = 0
 VSOLVE_RTOL = 1e-4  # relative residual of the V-cycle comparison solver (Sec. 5.3)
-# float64 lanes per clock per SM (two FMA-capable lanes) x SMs x max SM clock
+# float64 FMA lanes per clock per SM on GB300 (the derived peak, reported
+# beside the measured one)
 FP64_LANES_PER_CLK_SM = 2
-GB300_SMS = 152
-GB300_MAX_MHZ = 2070.0
-FP64_PEAK_TOPS = FP64_LANES_PER_CLK_SM * GB300_SMS * GB300_MAX_MHZ * 1e6 / 1e12
 
 
 def workload_name(n=N, sr=SR):
     J = [2 * ((sr["A"] + sr["B"] * (sr["K"] - k)) // 2) for k in range(1, sr["K"] + 1)]
     nseg = (n // sr["seg"]) ** 3
+    nc = sr.get("n_coarse", 0) or 2
     return (f"SR-FMG FP64 {n}^3 cells, {nseg} segments of {sr['seg']}^3, K={sr['K']} SR levels, "
             f"buffers Eq.(eq:nb) A={sr['A']} B={sr['B']} (J={J}), F(1,2,2) Chebyshev, "
-            f"global levels {n >> sr['K']}^3..2^3"), J
+            f"global levels {n >> sr['K']}^3..{nc}^3, {nc}^3 solved exactly"), J
 
 
 def parse():
@@ -284,6 +289,11 @@ def run_ours(args):
         sr.solve_async(ft, ut)
     sr.check()
     u_sr = ut.cpu().numpy()
+    # measured FMA peaks of this device (the float64 one is the roofline's
+    # denominator for the float64-pipe-bound kernels)
+    fp64_peak = srfmg.probe_fma_rate(64) / 1e12
+    fp32_peak = srfmg.probe_fma_rate(32) / 1e12
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     sampler = ClockSampler(local)
     total_ms = timed(sr, args.steps, sampler)
     clocks = sampler.summary()
@@ -306,10 +316,15 @@ def run_ours(args):
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except (OSError, ValueError, KeyError):
         pass
+    max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    fp64_derived = FP64_LANES_PER_CLK_SM * sms * max_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved,
-                "peak": FP64_PEAK_TOPS, "unit": "TFP64op/s", "frac": achieved / FP64_PEAK_TOPS,
+                "peak": fp64_peak, "unit": "TFP64op/s", "frac": achieved / fp64_peak,
                 "traffic": ncu_traffic(dominant),
-                "peak_note": "float64 pipe: 2 lanes/clk/SM x 152 SMs x 2070 MHz (derived)",
+                "peak_note": (f"measured: sr_probe_fma_rate(64) on this GPU, {fp64_peak:.3f} T "
+                              f"FP64 FMA lane-op/s; derived 2 lanes/clk/SM x {sms} SMs x "
+                              f"{max_mhz:.0f} MHz = {fp64_derived:.3f}"),
+                "frac_of_derived": achieved / fp64_derived,
                 "launches": d["launches"] // args.steps,
                 "fp64_ops_per_launch": d["ops"] / d["launches"],
                 "ms_per_launch": d["ms"] / d["launches"],
@@ -330,7 +345,7 @@ def run_ours(args):
     direct.close()
 
     # the same solve without segmental refinement (plain FMG), same f
-    plain = srfmg.Solver(N, graph=True)
+    plain = srfmg.Solver(N, graph=True, **PLAIN)
     for _ in range(args.warmup):
         plain.solve_async(ft, ut)
     plain.check()
@@ -371,12 +386,23 @@ def run_ours(args):
     sr.close()
     del fh, uh
 
+    # the same segments at the paper's depth (2^3 coarsest grid, J = 8) and
+    # plain FMG there: far from discretisation error (comparison only)
+    depth2 = {}
+    for name, kw in (("sr", SR_DEPTH2), ("plain", {})):
+        with srfmg.Solver(N, graph=True, **kw) as s2:
+            for _ in range(args.warmup):
+                s2.solve_async(ft, ut)
+            s2.check()
+            depth2[name + "_u"] = ut.cpu().numpy()
+            depth2[name + "_ms"] = timed(s2, args.steps) / args.steps
+
     mixed = batch = None
     paper = adjoint = None
     if not args.no_extras:
         mixed = measure_mixed(args, timed_fn=ranks_max, world=world, rank=rank)
         batch = measure_batch(args, ranks_max, world)
-        paper = measure_paper(args, ranks_max, world)
+        paper = measure_paper(args, ranks_max, world, fp64_peak)
         adjoint = measure_adjoint(args, ranks_max, world, rank)
 
     if rank != 0:
@@ -396,11 +422,21 @@ def run_ours(args):
         acc["e_disc"] = float(np.abs(u_h - u_exact).max())
         acc["e_alg_sr"] = float(np.abs(u_sr - u_h).max())
         acc["e_alg_plain"] = float(np.abs(u_plain - u_h).max())
+        acc["e_alg_sr_over_e_disc"] = acc["e_alg_sr"] / acc["e_disc"]
+        acc["e_alg_plain_over_e_disc"] = acc["e_alg_plain"] / acc["e_disc"]
+        acc["sr_minus_plain_over_e_disc"] = float(np.abs(u_sr - u_plain).max()) / acc["e_disc"]
+        for name in ("sr", "plain"):
+            depth2["e_alg_" + name + "_over_e_disc"] = \
+                float(np.abs(depth2[name + "_u"] - u_h).max()) / acc["e_disc"]
     except ImportError:
         pass
     acc["e_sr"] = float(np.abs(u_sr - u_exact).max())
     acc["e_plain"] = float(np.abs(u_plain - u_exact).max())
     acc["e_r"] = acc["e_sr"] / acc["e_plain"]
+    e_d2 = {k: float(np.abs(depth2.pop(k + "_u") - u_exact).max()) for k in ("sr", "plain")}
+    depth2.update({"e_r": e_d2["sr"] / e_d2["plain"], "config": dict(SR_DEPTH2),
+                   "sr_dof_s": world * N ** 3 / (depth2["sr_ms"] / 1e3),
+                   "plain_dof_s": world * N ** 3 / (depth2["plain_ms"] / 1e3)})
     if vs is not None:
         vs["e_over_e_plain_fmg"] = vs["e"] / acc["e_plain"]
 
@@ -440,6 +476,7 @@ def run_ours(args):
                             "hbm_frac_of_measured": sr_bytes / (ms / 1e3) / 1e9 / hbm
                             if hbm else None},
         "vcycle_solve_fp64_256": vs,
+        "paper_depth_2cubed_fp64_256": depth2,
         "mixed_sr_512": mixed,
         "batched_mixed": batch,
         "adjoint_sr_fp64_256": adjoint,
@@ -455,12 +492,16 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2: f is 134 MB and each solve sweeps about 3 GB "
                          "of workspace",
+                   "n_coarse": SR["n_coarse"],
                    "plain_fmg_dof_s": world * N ** 3 / (plain_ms / 1e3),
                    "plain_fmg_ms_per_step": plain_ms},
         "e2e": {"value": world * N ** 3 / e2e_s, "unit": "DOF/s",
                 "h2d_bytes_per_step": N ** 3 * 8, "d2h_bytes_per_step": N ** 3 * 8},
         "gpu_launches": launches * args.steps,
         "roofline": roofline,
+        "peaks": {"fp64_fma_tops_measured": fp64_peak, "fp32_fma_tops_measured": fp32_peak,
+                  "fp64_fma_tops_derived": fp64_derived, "sms": sms,
+                  "hbm_gbs_measured": hbm_peak},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "accuracy": acc,
@@ -496,7 +537,7 @@ def _time_loop(step, steps, stream=None):
     return e0.elapsed_time(e1)
 
 
-def measure_paper(args, timed_fn, world):
+def measure_paper(args, timed_fn, world, fp64_peak):
     """The paper's own model problem (Sec. 5.1) at Table 2's N = 256 column:
     [0,2]x[0,1]^2 with 1024 x 512 x 512 cells, 27-point operator ((14,3,1)/30),
     4 x 2 x 2 segments of 256^3, K = 5, A = 8, B = 0; plain FMG on the same f.
@@ -536,7 +577,7 @@ def measure_paper(args, timed_fn, world):
                 out["dominant_kernel"] = {
                     "kind": top, "share": d["ms"] / sum(v["ms"] for v in prof.values()),
                     "tfp64ops": d["ops"] / (d["ms"] / 1e3) / 1e12,
-                    "frac_of_fp64_peak": d["ops"] / (d["ms"] / 1e3) / 1e12 / FP64_PEAK_TOPS}
+                    "frac_of_fp64_peak": d["ops"] / (d["ms"] / 1e3) / 1e12 / fp64_peak}
     out["e_sr"], out["e_conv"] = err["sr"], err["plain"]
     out["e_r"] = err["sr"] / err["plain"]
     return out

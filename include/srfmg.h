@@ -68,7 +68,15 @@ typedef struct sr_fmg_s* sr_fmg_t;
  *             the coarsest grid.
  *   n_coarse  cells per unit length of the coarsest grid, solved exactly
  *             (Sec. 3.1, the "else" branch of FASMGV); 0 = keep halving until
- *             2 or 3 remain.  At most 8.
+ *             2 or 3 remain.  At most 16.  Grids of up to 512 cells use a
+ *             dense inverse; larger ones, with at most 32 cells per axis, the
+ *             separable sine-transform solve (about 2 (nx + ny + nz) float64
+ *             operations per cell); other coarsest grids of up to 4096 cells
+ *             the dense inverse again, and anything larger is
+ *             SR_ERR_UNSUPPORTED_SIZE.  A deeper exact solve (16) lets FMG
+ *             reach an algebraic error well below the discretisation error
+ *             (Sec. 3.2: FMG is asymptotically exact once the coarsest
+ *             solve and the V-cycle are accurate enough).
  *   seg       genuine segment edge on the finest level (segments are cubes);
  *             0 = plain FMG (no segmental refinement).  n % seg == 0 and
  *             seg % 2^K == 0.
@@ -222,6 +230,20 @@ int sr_fmg_profile_kinds(void);
 int sr_fmg_profile_read(sr_fmg_t h, int kind, const char** name, long long* launches,
                         double* ms, double* ops, double* bytes);
 
+/*
+ * Measured peak fused multiply-add rate of the current device: bits = 64
+ * (float64) or 32 (float32).  *lane_ops_per_s receives the lane operations
+ * per second (one FMA on one lane counts one) of a kernel that keeps every
+ * SM's pipe busy with independent FMA chains, best of three event-timed
+ * launches on stream after one warm-up; the call waits for them.  It
+ * allocates and frees a small output buffer.  The solver's float64 kernels
+ * are bound by this rate, not by HBM (the roofline denominator of the
+ * stencil passes; the paper, which reports CPU results, has no
+ * counterpart).  Errors: SR_ERR_INVALID (bits, null output), SR_ERR_OOM,
+ * SR_ERR_CUDA, SR_ERR_NO_DEVICE.
+ */
+int sr_probe_fma_rate(int bits, double* lane_ops_per_s, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* sr_fmg_status_string(int status);
 
@@ -236,7 +258,7 @@ const char* sr_fmg_status_string(int status);
  *   sr_op_restrict     ac = 8-child average of a, (n/2)^3 result  (Sec. 5.1)
  *   sr_op_prolong      af = trilinear interpolation of the nc^3 grid ac onto
  *                      (2 nc)^3                                  (Sec. 5.1)
- *   sr_op_coarse_solve u = A^-1 f exactly, n <= 8                 (Sec. 3.1)
+ *   sr_op_coarse_solve u = A^-1 f exactly, n <= 32                (Sec. 3.1)
  *   sr_op_vcycle       one FAS V-cycle on u with right-hand side f, using
  *                      cfg's cycle parameters (seg and K ignored)  (Sec. 3.1)
  */

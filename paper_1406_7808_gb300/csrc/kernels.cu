@@ -564,6 +564,100 @@ __global__ void k_coarse_solve(LevelView L, const double* __restrict__ minv, Fie
   }
 }
 
+// Coarsest grid by the separable sine transform: the operator is diagonal
+// in the products of the per-axis bases P_d[k][i] = c_k sin(pi (k + 1)(i + 1/2) / N_d)
+// (rows orthonormal), so u = P^T (Lambda^-1 (P f)) with P = Px (x) Py (x) Pz.
+// Three passes, each a set of independent tasks of W lanes (W a power of two
+// covering every axis, 32 / W tasks per warp; lane l holds index l of its
+// line and the sums run over the line through shuffles within the task):
+//   fwd_xy  task (z, ky):   t[x] = sum_y Py[ky][y] f[z][y][x],  g[z][ky][kx] = sum_x Px[kx][x] t[x]
+//   z       task (ky, kx):  h[kz] = sum_z Pz[kz][z] g[z][ky][kx] / lambda,  q[z][ky][kx] = sum_kz Pz[kz][z] h[kz]
+//   inv_xy  task (z, y):    t[kx] = sum_ky Py[ky][y] q[z][ky][kx],  u[z][y][x] = sum_kx Px[kx][x] t[kx]
+// sep holds Px (nx^2), Py (ny^2), Pz (nz^2) and 1/lambda (indexed
+// (kz ny + ky) nx + kx); g and q are float64 scratch of nx ny nz values.
+struct SepTask {
+  int lane, task;  // lane within the task, task index (may be past the last task)
+};
+
+__device__ __forceinline__ SepTask sep_task(int W) {
+  const int gl = blockIdx.x * blockDim.x + threadIdx.x;
+  return SepTask{gl & (W - 1), gl / W};
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_sep_fwd_xy(LevelView L, FieldT<T> f,
+                                                   const double* __restrict__ sep,
+                                                   double* __restrict__ g, int W, Fk<double> k) {
+  grid_dep_wait();
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const SepTask q = sep_task(W);
+  const bool live = q.task < nz * ny;
+  const int z = live ? q.task / ny : 0, ky = live ? q.task - (q.task / ny) * ny : 0;
+  const BoxDesc FB = f.boxes[0];
+  const double* Px = sep;
+  const double* Py = sep + nx * nx;
+  double t = k.zero;
+  if (live && q.lane < nx)
+    for (int y = 0; y < ny; ++y) t = fma(Py[ky * ny + y], widen(f.p[at(FB, q.lane, y, z)]), t);
+  double o = k.zero;
+  for (int x = 0; x < nx; ++x) {
+    const double tx = __shfl_sync(0xffffffffu, t, x, W);
+    if (q.lane < nx) o = fma(Px[q.lane * nx + x], tx, o);
+  }
+  if (live && q.lane < nx) g[((long long)z * ny + ky) * nx + q.lane] = o;
+}
+
+__global__ void __launch_bounds__(64) k_sep_z(int nx, int ny, int nz,
+                                              const double* __restrict__ sep,
+                                              const double* __restrict__ g,
+                                              double* __restrict__ qo, int W, Fk<double> k) {
+  grid_dep_wait();
+  const SepTask q = sep_task(W);
+  const bool live = q.task < ny * nx;
+  const int ky = live ? q.task / nx : 0, kx = live ? q.task - (q.task / nx) * nx : 0;
+  const double* Pz = sep + nx * nx + ny * ny;
+  const double* il = Pz + nz * nz;
+  const long long pl = (long long)ny * nx;
+  const bool on = live && q.lane < nz;
+  const double v = on ? g[q.lane * pl + (long long)ky * nx + kx] : k.zero;
+  double h = k.zero;
+  for (int z = 0; z < nz; ++z) {
+    const double vz = __shfl_sync(0xffffffffu, v, z, W);
+    if (q.lane < nz) h = fma(Pz[q.lane * nz + z], vz, h);
+  }
+  if (on) h = fma(h, il[q.lane * pl + (long long)ky * nx + kx], k.zero);
+  double o = k.zero;
+  for (int kz = 0; kz < nz; ++kz) {
+    const double hz = __shfl_sync(0xffffffffu, h, kz, W);
+    if (q.lane < nz) o = fma(Pz[kz * nz + q.lane], hz, o);
+  }
+  if (on) qo[q.lane * pl + (long long)ky * nx + kx] = o;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_sep_inv_xy(LevelView L, const double* __restrict__ sep,
+                                                   const double* __restrict__ qi,
+                                                   T* __restrict__ u, int W, Fk<double> k) {
+  grid_dep_wait();
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const SepTask q = sep_task(W);
+  const bool live = q.task < nz * ny;
+  const int z = live ? q.task / ny : 0, y = live ? q.task - (q.task / ny) * ny : 0;
+  const BoxDesc B = L.boxes[0];
+  const double* Px = sep;
+  const double* Py = sep + nx * nx;
+  double t = k.zero;
+  if (live && q.lane < nx)
+    for (int ky = 0; ky < ny; ++ky)
+      t = fma(Py[ky * ny + y], qi[((long long)z * ny + ky) * nx + q.lane], t);
+  double o = k.zero;
+  for (int kx = 0; kx < nx; ++kx) {
+    const double tk = __shfl_sync(0xffffffffu, t, kx, W);
+    if (q.lane < nx) o = fma(Px[kx * nx + q.lane], tk, o);
+  }
+  if (live && q.lane < nx) u[at(B, q.lane, y, z)] = (T)o;
+}
+
 __device__ __forceinline__ bool not_finite(double v) {
   return ((__double_as_longlong(v) >> 52) & 0x7ff) == 0x7ff;
 }
@@ -1046,6 +1140,32 @@ cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldT<T
   return cudaGetLastError();
 }
 
+int sep_lanes(const LevelView& L) {
+  const int m = max(L.nx, max(L.ny, L.nz));
+  int W = 1;
+  while (W < m) W *= 2;
+  return W;
+}
+
+unsigned sep_blocks(int tasks, int W) {
+  const long long threads = (long long)tasks * W;
+  return (unsigned)((threads + 63) / 64);
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve_sep(const LevelView& L, const double* sep, double* g, double* q,
+                                    FieldT<T> f, T* u, cudaStream_t s) {
+  const int W = sep_lanes(L);
+  if (W > 32) return cudaErrorInvalidValue;
+  SRFMG_LAUNCH(pdl_launch(k_sep_fwd_xy<T>, sep_blocks(L.nz * L.ny, W), 64, 0, s, L, f, sep, g, W,
+                          fk<double>()));
+  SRFMG_LAUNCH(pdl_launch(k_sep_z, sep_blocks(L.ny * L.nx, W), 64, 0, s, L.nx, L.ny, L.nz, sep,
+                          (const double*)g, q, W, fk<double>()));
+  SRFMG_LAUNCH(pdl_launch(k_sep_inv_xy<T>, sep_blocks(L.nz * L.ny, W), 64, 0, s, L, sep,
+                          (const double*)q, u, W, fk<double>()));
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_restrict_global(Dims fd, const T* ff, T* fc, int check, unsigned int* status,
                                    cudaStream_t s) {
@@ -1112,6 +1232,8 @@ cudaError_t launch_accumulate(long long cells, const float* e, double* u, int ad
                                       int);                                                    \
   template cudaError_t launch_coarse_solve<T>(const LevelView&, const double*, FieldT<T>, T*,  \
                                               cudaStream_t);                                   \
+  template cudaError_t launch_coarse_solve_sep<T>(const LevelView&, const double*, double*,    \
+                                                  double*, FieldT<T>, T*, cudaStream_t);       \
   template cudaError_t launch_restrict_global<T>(Dims, const T*, T*, int, unsigned int*,       \
                                                  cudaStream_t);                                \
   template cudaError_t launch_gather_genuine<T>(const LevelView&, const T*, double*, int,      \

@@ -137,7 +137,9 @@ struct sr_fmg_s {
   Hier<double> h64;                // levels of the float64 solver
   Hier<float> h32;                 // levels of the float32 inner solver
   float* defect = nullptr;         // SR_MIXED: float32 defect, n^3
-  double* minv = nullptr;          // inverse of the coarsest operator
+  double* minv = nullptr;          // dense inverse of the coarsest operator (small grids)
+  double* sep = nullptr;           // separable coarsest solve: bases and 1/lambda
+  double *sep_g = nullptr, *sep_q = nullptr;  // its float64 scratch
   unsigned int* status = nullptr;  // device status bits
   Cheb pre, post, fmg;
   int len[3] = {1, 1, 1};          // domain lengths
@@ -278,6 +280,17 @@ int lengths_of(const sr_fmg_config* c, int len[3]) {
   return SR_OK;
 }
 
+// how the coarsest grid of nd cells is solved exactly (see build_coarse)
+enum CoarsePlan { kCoarseDense = 0, kCoarseSeparable = 1, kCoarseUnsupported = -1 };
+
+CoarsePlan coarse_plan(const int nd[3]) {
+  const long long m = (long long)nd[0] * nd[1] * nd[2];
+  const bool narrow = nd[0] <= 32 && nd[1] <= 32 && nd[2] <= 32;
+  if (m <= 512) return kCoarseDense;
+  if (narrow) return kCoarseSeparable;
+  return m <= 4096 ? kCoarseDense : kCoarseUnsupported;
+}
+
 int check_config(const sr_fmg_config* c) {
   if (!c) return SR_ERR_INVALID;
   if (c->precision != SR_FP64 && c->precision != SR_MIXED) return SR_ERR_INVALID;
@@ -294,9 +307,14 @@ int check_config(const sr_fmg_config* c) {
   if (c->alpha < 0 || c->nu1 < 0 || c->nu2 < 0 || c->alpha > 16 || c->nu1 > 16 || c->nu2 > 16)
     return SR_ERR_INVALID;
   if (!(c->cheb_lo > 0.0 && c->cheb_hi > c->cheb_lo && c->cheb_hi < 4.0)) return SR_ERR_INVALID;
-  if (c->n_coarse < 0 || c->n_coarse > 8 || c->n_coarse == 1) return SR_ERR_UNSUPPORTED_SIZE;
+  if (c->n_coarse < 0 || c->n_coarse > 16 || c->n_coarse == 1) return SR_ERR_UNSUPPORTED_SIZE;
   if (c->n < 2 || c->n > 2048) return SR_ERR_UNSUPPORTED_SIZE;
-  if (halvings_to_coarsest(c->n, c->n_coarse) < 0) return SR_ERR_UNSUPPORTED_SIZE;
+  const int halvings = halvings_to_coarsest(c->n, c->n_coarse);
+  if (halvings < 0) return SR_ERR_UNSUPPORTED_SIZE;
+  {
+    const int ncs = c->n >> halvings, nd[3] = {ncs * len[0], ncs * len[1], ncs * len[2]};
+    if (coarse_plan(nd) == kCoarseUnsupported) return SR_ERR_UNSUPPORTED_SIZE;
+  }
   if (c->seg < 0 || c->K < 0 || c->K > SR_FMG_MAXK) return SR_ERR_INVALID;
   if (c->seg == 0 || c->K == 0) return SR_OK;
   if (c->mbs && (c->A < 0 || c->A % 2 || c->A > 4096 >> c->K)) return SR_ERR_INVALID;
@@ -441,35 +459,43 @@ int finish_level(sr_fmg_s* h, Geom& L) {
   return SR_OK;
 }
 
-// dense inverse of the coarsest operator from its eigen-decomposition: on
-// each axis of N cells the factors sin(k pi (i + 1/2) / N), k = 1..N, are
-// orthogonal with squared norms N/2 (k < N) and N (k = N); the operator's
-// eigenvalue on their product is n^2 (w0 - 2 w1 sum c_d - 4 w2 sum c_d c_e
-// - 8 w3 c_0 c_1 c_2), c_d = cos(k_d pi / N_d) (7-point: w = (6, 1, 0, 0)).
+// Exact coarsest solves.  On each axis of N cells the factors
+// sin(k pi (i + 1/2) / N), k = 1..N, are orthogonal with squared norms N/2
+// (k < N) and N (k = N); the operator's eigenvalue on their product is
+// n^2 (w0 - 2 w1 sum c_d - 4 w2 sum c_d c_e - 8 w3 c_0 c_1 c_2),
+// c_d = cos(k_d pi / N_d) (7-point: w = (6, 1, 0, 0)).  Small grids use the
+// dense inverse built from that eigen-decomposition (one launch); larger
+// ones, with at most 32 cells per axis, apply it as separable transforms
+// (three launches, about 2 (nx + ny + nz) operations per cell instead of
+// nx ny nz).
+// orthonormal sine basis of an axis of N cells, row k - 1 = mode k, and the
+// mode cosines cos(k pi / N)
+void sine_basis(int N, std::vector<double>& phi, std::vector<double>& cs) {
+  const double pi = 3.14159265358979323846;
+  phi.assign((size_t)N * N, 0.0);
+  cs.assign(N, 0.0);
+  for (int k = 1; k <= N; ++k) {
+    const double norm = std::sqrt((k < N) ? 2.0 / N : 1.0 / N);
+    for (int i = 0; i < N; ++i) phi[(size_t)(k - 1) * N + i] = norm * std::sin(pi * k * (i + 0.5) / N);
+    cs[k - 1] = std::cos(pi * k / N);
+  }
+}
+
+double symbol_eig(const W27& w, double n2, double x, double y, double z) {
+  return n2 * (w.w0 - 2.0 * w.w1 * (x + y + z) - 4.0 * w.w2 * (x * y + x * z + y * z) -
+               8.0 * w.w3 * x * y * z);
+}
+
 std::vector<double> coarsest_inverse(const int nd[3], int n, const W27& w) {
   const int m = nd[0] * nd[1] * nd[2];
-  const double pi = 3.14159265358979323846;
   std::vector<double> phi[3], cs[3];
-  for (int d = 0; d < 3; ++d) {
-    const int N = nd[d];
-    phi[d].assign((size_t)N * N, 0.0);
-    cs[d].assign(N, 0.0);
-    for (int k = 1; k <= N; ++k) {
-      const double norm = std::sqrt((k < N) ? 2.0 / N : 1.0 / N);
-      for (int i = 0; i < N; ++i)
-        phi[d][(size_t)(k - 1) * N + i] = norm * std::sin(pi * k * (i + 0.5) / N);
-      cs[d][k - 1] = std::cos(pi * k / N);
-    }
-  }
+  for (int d = 0; d < 3; ++d) sine_basis(nd[d], phi[d], cs[d]);
   const double n2 = (double)n * n;
   std::vector<double> minv((size_t)m * m, 0.0), v(m);
   for (int k3 = 0; k3 < nd[2]; ++k3)
     for (int k2 = 0; k2 < nd[1]; ++k2)
       for (int k1 = 0; k1 < nd[0]; ++k1) {
-        const double x = cs[0][k1], y = cs[1][k2], z = cs[2][k3];
-        const double lam = n2 * (w.w0 - 2.0 * w.w1 * (x + y + z) -
-                                 4.0 * w.w2 * (x * y + x * z + y * z) - 8.0 * w.w3 * x * y * z);
-        const double il = 1.0 / lam;
+        const double il = 1.0 / symbol_eig(w, n2, cs[0][k1], cs[1][k2], cs[2][k3]);
         for (int zz = 0; zz < nd[2]; ++zz)
           for (int yy = 0; yy < nd[1]; ++yy)
             for (int xx = 0; xx < nd[0]; ++xx)
@@ -483,6 +509,47 @@ std::vector<double> coarsest_inverse(const int nd[3], int n, const W27& w) {
         }
       }
   return minv;
+}
+
+// [Px | Py | Pz | 1/lambda] for the separable solve
+std::vector<double> coarsest_separable(const int nd[3], int n, const W27& w) {
+  std::vector<double> phi[3], cs[3], out;
+  for (int d = 0; d < 3; ++d) {
+    sine_basis(nd[d], phi[d], cs[d]);
+    out.insert(out.end(), phi[d].begin(), phi[d].end());
+  }
+  const double n2 = (double)n * n;
+  for (int k3 = 0; k3 < nd[2]; ++k3)
+    for (int k2 = 0; k2 < nd[1]; ++k2)
+      for (int k1 = 0; k1 < nd[0]; ++k1)
+        out.push_back(1.0 / symbol_eig(w, n2, cs[0][k1], cs[1][k2], cs[2][k3]));
+  return out;
+}
+
+struct CoarseOp {
+  double* minv = nullptr;
+  double *sep = nullptr, *g = nullptr, *q = nullptr;
+};
+
+// device data of the exact solve on a coarsest grid of nd cells (allocated
+// through h, freed with it)
+int build_coarse(sr_fmg_s* h, const int nd[3], int n, const W27& w, CoarseOp* op) {
+  const CoarsePlan plan = coarse_plan(nd);
+  if (plan == kCoarseUnsupported) return SR_ERR_UNSUPPORTED_SIZE;
+  const std::vector<double> data = plan == kCoarseDense ? coarsest_inverse(nd, n, w)
+                                                        : coarsest_separable(nd, n, w);
+  double* dev = nullptr;
+  int rc = dalloc(h, &dev, data.size());
+  if (rc) return rc;
+  CK(cudaMemcpy(dev, data.data(), data.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (plan == kCoarseDense) {
+    op->minv = dev;
+    return SR_OK;
+  }
+  op->sep = dev;
+  const size_t m = (size_t)nd[0] * nd[1] * nd[2];
+  if ((rc = dalloc(h, &op->g, m))) return rc;
+  return dalloc(h, &op->q, m);
 }
 
 // global levels of ntop down to the coarsest grid; with top_user the finest
@@ -514,11 +581,14 @@ int build_global_levels(sr_fmg_s* h, Hier<T>& H, int ntop, bool top_user) {
     if ((rc = dalloc(h, &L.rho, cells))) return rc;
     if ((rc = dalloc(h, &L.f, cells))) return rc;
   }
-  if (!h->minv) {
-    std::vector<double> minv = coarsest_inverse(H.glev[0].nd, H.glev[0].n, h->w27);
-    int rc = dalloc(h, &h->minv, minv.size());
+  if (!h->minv && !h->sep) {
+    CoarseOp op;
+    int rc = build_coarse(h, H.glev[0].nd, H.glev[0].n, h->w27, &op);
     if (rc) return rc;
-    CK(cudaMemcpy(h->minv, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    h->minv = op.minv;
+    h->sep = op.sep;
+    h->sep_g = op.g;
+    h->sep_q = op.q;
   }
   return SR_OK;
 }
@@ -779,6 +849,23 @@ int fmg_step(sr_fmg_s* h, const Level<T>& L, T* u, FieldT<T> f, cudaStream_t s,
   return SR_OK;
 }
 
+// exact solve on the coarsest global level L: u = A^-1 f (dense inverse or
+// separable transforms, whichever the handle built)
+template <typename T>
+int coarse_solve(sr_fmg_s* h, const Level<T>& L, FieldT<T> f, T* u, cudaStream_t s) {
+  const double m = L.tot_cells;
+  if (h->minv) {
+    LAUNCH(h, kind_of<T>(kCoarseSolve), m * m, 1, 8, s,
+           launch_coarse_solve<T>(L.view, h->minv, f, u, s));
+    return SR_OK;
+  }
+  const double ops = 2.0 * (L.nd[0] + L.nd[1] + L.nd[2]) + 1.0;
+  LAUNCH(h, kind_of<T>(kCoarseSolve), m, ops, 40.0 + 2.0 * sizeof(T), s,
+         launch_coarse_solve_sep<T>(L.view, h->sep, h->sep_g, h->sep_q, f, u, s));
+  h->launches += 2;  // three kernels
+  return SR_OK;
+}
+
 // FASMGV on global level g (Fig. "FAS multigrid V-cycle"); u is the level's
 // u (or the caller's u on the finest plain FP64 level).
 template <typename T>
@@ -786,12 +873,7 @@ int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStrea
                   const T* r_first = nullptr) {
   Level<T>& L = H.glev[g];
   const double w = sizeof(T);
-  if (g == 0) {
-    const double m = L.tot_cells;
-    LAUNCH(h, kind_of<T>(kCoarseSolve), m * m, 1, 8, s,
-           launch_coarse_solve<T>(L.view, h->minv, rhs, u, s));
-    return SR_OK;
-  }
+  if (g == 0) return coarse_solve<T>(h, L, rhs, u, s);
   Level<T>& C = H.glev[g - 1];
   int rc = smooth(h, L, h->pre, u, rhs, s, r_first);
   if (rc) return rc;
@@ -820,10 +902,8 @@ int run_fmg_global(sr_fmg_s* h, Hier<T>& H, const T* ftop, T* utop, cudaStream_t
   auto fg = [&](int g) -> const T* { return (g == top && plain) ? ftop : H.glev[g].f; };
   auto ug = [&](int g) -> T* { return (g == top && plain) ? utop : H.glev[g].u; };
   {
-    const double m = H.glev[0].tot_cells;
-    LAUNCH(h, kind_of<T>(kCoarseSolve), m * m, 1, 8, s,
-           launch_coarse_solve<T>(H.glev[0].view, h->minv, view_global<T>(H.glev[0], fg(0)),
-                                  ug(0), s));
+    const int rc = coarse_solve<T>(h, H.glev[0], view_global<T>(H.glev[0], fg(0)), ug(0), s);
+    if (rc) return rc;
   }
   const double w = sizeof(T);
   for (int g = 1; g <= top; ++g) {
@@ -1481,15 +1561,13 @@ int sr_op_coarse_solve_ex(const sr_fmg_config* cfg, const double* f, double* u, 
   TmpLevel T;
   int rc = tmp_level(T, *cfg, cfg->n);
   if (rc) return rc;
-  if (cells_of(T.L) > 4096) return SR_ERR_UNSUPPORTED_SIZE;
-  std::vector<double> minv = coarsest_inverse(T.L.nd, T.L.n, T.h.w27);
-  double* dm = nullptr;
-  rc = dalloc(&T.h, &dm, minv.size());
-  if (rc) return rc;
-  CK(cudaMemcpy(dm, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice));
-  CK(launch_coarse_solve<double>(T.L.view, dm, view_global<double>(T.L, f), u,
-                                 (cudaStream_t)stream));
-  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  CoarseOp op;
+  if ((rc = build_coarse(&T.h, T.L.nd, T.L.n, T.h.w27, &op))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const FieldT<double> fv = view_global<double>(T.L, f);
+  CK(op.minv ? launch_coarse_solve<double>(T.L.view, op.minv, fv, u, s)
+             : launch_coarse_solve_sep<double>(T.L.view, op.sep, op.g, op.q, fv, u, s));
+  CK(cudaStreamSynchronize(s));
   return SR_OK;
 }
 
@@ -1522,7 +1600,7 @@ int sr_op_prolong(int nc, const double* ac, double* af, void* stream) {
 }
 
 int sr_op_coarse_solve(int n, const double* f, double* u, void* stream) {
-  if (n > 8) return SR_ERR_INVALID;
+  if (n > 32) return SR_ERR_INVALID;
   const sr_fmg_config c = cube7(n);
   return sr_op_coarse_solve_ex(&c, f, u, stream);
 }

@@ -188,6 +188,14 @@ cudaError_t launch_diff(const LevelView& C, const T* u, const T* t, T* e, cudaSt
 template <typename T>
 cudaError_t launch_coarse_solve(const LevelView& L, const double* minv, FieldT<T> f, T* u,
                                 cudaStream_t s);
+// Coarsest grid by the separable sine transform, u = P^T (Lambda^-1 (P f)),
+// every axis at most 32 cells; sep = [Px | Py | Pz | 1/lambda] (per-axis
+// orthonormal bases P_d[k][i], k, i < N_d, then nx ny nz inverse
+// eigenvalues indexed (kz ny + ky) nx + kx); g, q: float64 scratch of
+// nx ny nz values.  Three launches; float64 arithmetic.
+template <typename T>
+cudaError_t launch_coarse_solve_sep(const LevelView& L, const double* sep, double* g, double* q,
+                                    FieldT<T> f, T* u, cudaStream_t s);
 // f_c = 8-child average of f_f on whole global levels (fd: the fine grid's
 // cells per dimension); sets *status |= 1 if an input value is not finite
 // (check != 0).

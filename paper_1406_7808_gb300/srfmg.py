@@ -128,6 +128,7 @@ def load():
         getattr(lib, name).argtypes = [PC, _VP, _VP, _VP]
     lib.sr_op_residual_ex.argtypes = [PC, _VP, _VP, _VP, _VP]
     lib.sr_op_smooth_ex.argtypes = [PC, ctypes.c_int, _VP, _VP, _VP]
+    lib.sr_probe_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]
     _LIB = lib
     return lib
 
@@ -142,6 +143,14 @@ def status_string(status):
 def _check(status, what):
     if status != SR_OK:
         raise SRFMGError(status, what)
+
+
+def probe_fma_rate(bits=64):
+    """Measured peak FMA rate of the current device in lane operations per
+    second (bits = 64: float64, 32: float32); sr_probe_fma_rate."""
+    rate = ctypes.c_double(0.0)
+    _check(load().sr_probe_fma_rate(int(bits), ctypes.byref(rate), _stream()), "sr_probe_fma_rate")
+    return rate.value
 
 
 def mbs_schedule(J1, K):

@@ -2,10 +2,18 @@
 used by the benchmark, the smoke check and the tests.  Configuration only:
 no arithmetic of the method lives here."""
 
-# SR-FMG FP64: 256^3 cells, 512 segments of 32^3, K = 3, J = (8, 8, 8)
-SR256 = dict(n=256, seg=32, K=3, A=8, B=0)
-# plain FMG FP64 on the same grid
-PLAIN256 = dict(n=256)
+# SR-FMG FP64 at discretisation error: 256^3 cells, 512 segments of 32^3,
+# K = 3, buffers J = (12, 12, 10) (Eq. eq:nb with A = 11, B = 1), coarsest
+# grid 16^3 solved exactly.  Plain FMG on this hierarchy leaves an algebraic
+# error of about 0.13 e_disc, and these buffers keep the SR result within
+# 0.04 e_disc of it (e_r about 0.97).
+SR256 = dict(n=256, seg=32, K=3, A=11, B=1, n_coarse=16)
+# plain FMG FP64 on the same grid and hierarchy
+PLAIN256 = dict(n=256, n_coarse=16)
+# the same segments at the paper's depth (coarsest grid 2^3) with J = 8:
+# there FMG leaves about 10 e_disc of algebraic error in the smoothest mode
+SR256_DEPTH2 = dict(n=256, seg=32, K=3, A=8, B=0)
+PLAIN256_DEPTH2 = dict(n=256)
 # mixed-precision SR-FMG: 512^3 cells, 512 segments of 64^3, K = 4, J = 8
 MIXED512 = dict(n=512, seg=64, K=4, A=8, B=0, mixed=True, n_outer=2)
 

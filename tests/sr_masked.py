@@ -176,15 +176,17 @@ def box_mask(shape, lo, hi):
     return m
 
 
-def sr_fmg(f, seg, K, J, P):
-    """FASFMGSR with full-grid masks; returns u on the fine grid."""
+def sr_fmg(f, seg, K, J, P, coarsest=None):
+    """FASFMGSR with full-grid masks; returns u on the fine grid.  coarsest:
+    cells per unit length of the exactly solved grid (default: halve to 2
+    or 3)."""
     n = f.shape[2] // P.lengths[0]
     nk = [n >> (K - k) for k in range(K + 1)]
     dims = lambda k: [nk[k] * l for l in P.lengths]  # noqa: E731  (x, y, z)
     fsr = {K: f}
     for k in range(K, 0, -1):
         fsr[k - 1] = restrict(fsr[k])
-    coarsest = _coarsest(nk[0])
+    coarsest = _coarsest(nk[0]) if coarsest is None else coarsest
     u0 = fmg(fsr[0], P, coarsest, nk[0])
     rho0 = np.full(P.shape(nk[0]), np.nan)
     uhat0 = np.full(P.shape(nk[0]), np.nan)

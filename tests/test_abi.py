@@ -65,6 +65,9 @@ def _create(lib, **kw):
             c.use_J = 1
             for i, x in enumerate(v):
                 c.J[i] = x
+        elif k == "len":
+            for i, x in enumerate(v):
+                c.len[i] = x
         else:
             setattr(c, k, v)
     h = ctypes.c_void_p()
@@ -76,7 +79,8 @@ def _create(lib, **kw):
 @pytest.mark.parametrize("kw,expected", [
     (dict(n=20), -2),                                   # 20 -> 10 -> 5 never reaches 2 or 3
     (dict(n=64, n_coarse=5), -2),
-    (dict(n=64, n_coarse=16), -2),                      # coarsest grid larger than supported
+    (dict(n=64, n_coarse=32), -2),                      # coarsest grid larger than supported
+    (dict(n=64, n_coarse=16, len=(4, 1, 1)), -2),       # 64 x 16 x 16 coarsest cells: too many
     (dict(n=64, seg=24, K=2), -1),                      # seg does not divide n
     (dict(n=64, seg=16, K=5), -1),                      # seg not divisible by 2^K
     (dict(n=64, seg=16, K=2, J=[4, 3]), -1),            # odd buffer

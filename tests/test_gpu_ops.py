@@ -69,13 +69,33 @@ def test_prolong(gpu, oracle_mod, nc):
     assert rel(N(gpu.op_prolong(T(a))), oracle_mod.prolong(a)) < TOL
 
 
-@pytest.mark.parametrize("n", [2, 3, 4, 8])
+@pytest.mark.parametrize("n", [2, 3, 4, 8, 9, 12, 16])
 def test_coarse_solve(gpu, oracle_mod, n):
+    """Up to 8^3 the dense inverse, above it the separable sine-transform solve."""
     f = np.random.default_rng(n).standard_normal((n, n, n))
     assert rel(N(gpu.op_coarse_solve(T(f))), oracle_mod.coarse_solve(f)) < TOL
 
 
+def test_coarse_solve_32(gpu, oracle_mod):
+    """The separable solve at its largest size, 32^3: against the exact DST
+    solution and through its residual (the oracle's operator)."""
+    n = 32
+    f = np.random.default_rng(5).standard_normal((n, n, n))
+    u = N(gpu.op_coarse_solve(T(f)))
+    assert rel(u, exact.dst_solve(f)) < TOL
+    assert np.abs(oracle_mod.apply(u) - f).max() < 1e-10 * np.abs(f).max()
+
+
+def test_coarse_solve_separable_rectangle(gpu, oracle_mod):
+    """32 x 16 x 16 cells of [0,2] x [0,1]^2 with the 27-point operator: the
+    separable solve on unequal axes against the oracle's banded Cholesky."""
+    geo = dict(lengths=(2, 1, 1), stencil=27, weights=(14 / 30, 3 / 30, 1 / 30))
+    f = np.random.default_rng(7).standard_normal((16, 16, 32))
+    assert rel(N(gpu.op_coarse_solve(T(f), **geo)), oracle_mod.coarse_solve(f, **geo)) < TOL
+
+
 @pytest.mark.parametrize("n,kw", [(16, {}), (24, {}), (64, {}), (64, dict(n_coarse=8)),
+                                  (64, dict(n_coarse=16)), (32, dict(n_coarse=16)),
                                   (32, dict(nu1=3, nu2=1)), (32, dict(nu1=1, nu2=4))])
 def test_vcycle(gpu, oracle_mod, n, kw):
     rng = np.random.default_rng(n)

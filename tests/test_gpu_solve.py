@@ -5,7 +5,8 @@ benchmark times; plus the error behaviour of the boundary."""
 import numpy as np
 import pytest
 
-from paper_1406_7808_gb300 import inputs
+import exact
+from paper_1406_7808_gb300 import inputs, workloads
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -29,6 +30,8 @@ def gpu_solve(gpu, f, **kw):
     (2, {}), (3, {}), (4, {}), (8, {}), (16, {}), (24, {}), (32, {}), (48, {}), (64, {}),
     (96, {}), (128, {}),
     (32, dict(n_coarse=4)), (64, dict(n_coarse=8)), (32, dict(alpha=2, nu1=3, nu2=1)),
+    (16, dict(n_coarse=16)), (32, dict(n_coarse=16)), (128, dict(n_coarse=16)),
+    (48, dict(n_coarse=12)),
     (32, dict(cheb_lo=0.1, cheb_hi=1.1)),
 ])
 def test_plain_fmg_parity(gpu, oracle_mod, n, kw):
@@ -57,6 +60,11 @@ SR_CASES = [
     # with a degree-1 pre-smoother
     (32, dict(seg=8, K=2, J=[4, 4], alpha=2, nu1=3, nu2=1)),
     (32, dict(seg=16, K=2, J=[4, 4], nu1=1, nu2=2)),
+    # exact coarsest solve at 16^3 (separable transforms): the transition
+    # level is the coarsest grid, or one level above it
+    (64, dict(seg=16, K=2, J=[4, 4], n_coarse=16)),
+    (128, dict(seg=32, K=2, J=[12, 10], n_coarse=16)),
+    (128, dict(seg=32, K=3, J=[12, 12, 10], n_coarse=16)),
 ]
 
 
@@ -87,10 +95,33 @@ def test_mbs_flag_matches_explicit_schedule(gpu, oracle_mod):
 
 
 def test_sr_fmg_parity_full_size(gpu, oracle_mod):
-    """The benchmark's workload: 256^3, 32^3-cell segments (512), K = 3,
-    buffers A = 8, B = 0; every cell compared with the oracle."""
+    """The benchmark's workload, in the benchmark's launch configuration
+    (graph mode): 256^3, 512 segments of 32^3, K = 3, J = (12, 12, 10), the
+    coarsest grid 16^3 solved exactly; every cell compared with the oracle,
+    and the solve is at discretisation error: algebraic error below e_disc,
+    the SR result within 0.1 e_disc of plain FMG, e_r <= 1.1 (Sec. 5.2)."""
     n = 256
-    kw = dict(seg=32, K=3, A=8, B=0)
+    kw = workloads.config(workloads.SR256)
+    pkw = workloads.config(workloads.PLAIN256)
+    f, uex = inputs.manufactured(n, 0)
+    ref = oracle_mod.solve(f, **kw)
+    u = gpu_solve(gpu, f, graph=True, **kw)
+    assert rel(u, ref) < TOL
+    plain = gpu_solve(gpu, f, graph=True, **pkw)
+    assert rel(plain, oracle_mod.solve(f, **pkw)) < TOL
+    uh = exact.dst_solve(f)
+    e_disc = np.abs(uh - uex).max()
+    assert np.abs(u - uh).max() < 0.5 * e_disc
+    assert np.abs(u - plain).max() < 0.1 * e_disc
+    e_r = np.abs(u - uex).max() / np.abs(plain - uex).max()
+    assert e_r <= 1.1
+
+
+def test_sr_fmg_parity_full_size_paper_depth(gpu, oracle_mod):
+    """The same segments at the paper's depth (coarsest grid 2^3, J = 8),
+    every cell against the oracle."""
+    n = 256
+    kw = workloads.config(workloads.SR256_DEPTH2)
     f, uex = inputs.manufactured(n, 0)
     ref = oracle_mod.solve(f, **kw)
     u = gpu_solve(gpu, f, **kw)

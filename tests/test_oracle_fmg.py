@@ -7,13 +7,22 @@ and full multigrid (Sec. 3.2, Fig. "Full multigrid").
   solve;
 - FMG's total error against the manufactured solution falls at second order
   and, with a 16^3 coarsest grid, its algebraic error is below the
-  discretisation error; at the paper's depth (2^3 coarsest) the ratio r of
-  algebraic to discretisation error stays bounded.
+  discretisation error;
+- the ratio r of algebraic to discretisation error equals, to 1e-9, the
+  ratio the independent masked implementation (tests/sr_masked.py: its own
+  transfers, smoother and a DST coarsest solve) gives, at the paper's depth
+  (2^3 coarsest) and with a 16^3 coarsest grid.  At the paper's depth r is
+  4.5 to 9.5 (16^3 to 128^3), above the bound 3 Gamma / (1 - 4 Gamma) ~ 2.4 that the measured
+  V-cycle contraction Gamma ~ 0.19 would suggest (Sec. 3.2): the 2^3 grid's
+  smoothest eigenvalue is 8 per dimension against pi^2 for the continuous
+  operator, so each coarse correction of the smoothest mode is off by ~20 %
+  and that mode carries almost all of FMG's algebraic error.
 """
 import numpy as np
 import pytest
 
 import exact
+import sr_masked
 from paper_1406_7808_gb300 import inputs
 
 
@@ -57,7 +66,28 @@ def test_fmg_second_order_and_bounded_ratio(oracle_mod):
     assert all(x > 2.5 for x in q)
     assert all(b > a for a, b in zip(q, q[1:]))  # the order climbs towards 2 (ratio 4)
     assert q[-1] > 3.3
-    assert max(ratios) < 12.0
+    assert 4.0 < min(ratios) and max(ratios) < 10.5
+
+
+@pytest.mark.parametrize("n,nc", [(16, None), (32, None), (64, None), (32, 16), (64, 16),
+                                  (64, 8)])
+def test_fmg_error_ratio_matches_masked_implementation(oracle_mod, n, nc):
+    """r = |u_FMG - u_h| / |u_h - u| from the oracle equals the masked
+    implementation's to 1e-9 (a dropped term, a wrong Chebyshev coefficient
+    or transfer weight in either changes r by far more)."""
+    f, uex = inputs.manufactured(n, 0)
+    uh = exact.dst_solve(f)
+    e_disc = np.abs(uh - uex).max()
+    a = oracle_mod.solve(f, n_coarse=nc or 0)
+    b = sr_masked.inner(sr_masked.fmg(f, sr_masked.Params(), coarsest=nc))
+    ra = np.abs(a - uh).max() / e_disc
+    rb = np.abs(b - uh).max() / e_disc
+    assert abs(ra - rb) <= 1e-9
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+    if nc == 16:
+        assert ra < 0.3  # a 16^3 exact solve: FMG well below the discretisation error
+    elif nc is None:
+        assert ra > 4.0  # the paper's depth: the smoothest mode dominates
 
 
 @pytest.mark.parametrize("n", [32, 64, 128])

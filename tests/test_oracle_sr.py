@@ -15,8 +15,9 @@ Figs. "FMG segmental refinement" and "FAS V-cycle segmental refinement").
 import numpy as np
 import pytest
 
+import exact
 import sr_masked
-from paper_1406_7808_gb300 import inputs
+from paper_1406_7808_gb300 import inputs, workloads
 
 
 def test_buffer_schedule_eq_nb(oracle_mod):
@@ -141,3 +142,38 @@ def test_rejects_inconsistent_geometry(oracle_mod):
     assert oracle_mod.check_config(n=32, seg=8, K=2, J=[3, 4]) != 0    # odd buffer
     assert oracle_mod.check_config(n=32, seg=8, K=2, J=[2, 8]) != 0    # J_1 < J_2 / 2
     assert oracle_mod.check_config(n=32, seg=8, K=2, J=[4, 8]) == 0
+
+
+@pytest.mark.parametrize("nc,J", [(8, [4, 4]), (16, [4, 4]), (16, [4, 6])])
+def test_deep_coarse_solve_matches_masked_implementation(oracle_mod, nc, J):
+    """SR with an exact coarsest solve at 8^3 (global V-cycle on 16^3) or at
+    16^3 (the transition level itself) against the masked implementation."""
+    n, seg, K = 64, 32, 2
+    f, _ = inputs.manufactured(n, 2)
+    a = oracle_mod.solve(f, seg=seg, K=K, J=J, n_coarse=nc)
+    b = sr_masked.sr_fmg(f, seg, K, J, sr_masked.Params(), coarsest=nc)
+    assert not np.isnan(b).any()
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_benchmark_configuration_at_discretisation_error(oracle_mod):
+    """The benchmarked SR configuration on the oracle: 256^3, 512 segments of
+    32^3, K = 3, J = (12, 12, 10), coarsest grid 16^3.  Plain FMG on that
+    hierarchy is well below the discretisation error, the SR result stays
+    within 0.05 e_disc of it (so e_r <= 1.1, the paper's acceptability
+    threshold, Sec. 5.2, whatever the signs), while J = 8 adds about half an
+    e_disc of its own."""
+    n = 256
+    kw = workloads.config(workloads.SR256)
+    assert oracle_mod.buffer_schedule(kw["A"], kw["B"], kw["K"]) == [12, 12, 10]
+    f, uex = inputs.manufactured(n, 0)
+    uh = exact.dst_solve(f)
+    e_disc = np.abs(uh - uex).max()
+    plain = oracle_mod.solve(f, **workloads.config(workloads.PLAIN256))
+    sr = oracle_mod.solve(f, **kw)
+    assert np.abs(plain - uh).max() < 0.2 * e_disc
+    assert np.abs(sr - uh).max() < 0.25 * e_disc
+    assert np.abs(sr - plain).max() < 0.05 * e_disc
+    assert np.abs(sr - uex).max() / np.abs(plain - uex).max() <= 1.1
+    sr8 = oracle_mod.solve(f, seg=32, K=3, J=[8, 8, 8], n_coarse=16)
+    assert np.abs(sr8 - plain).max() > 0.3 * e_disc
