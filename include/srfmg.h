@@ -244,6 +244,35 @@ int sr_fmg_profile_read(sr_fmg_t h, int kind, const char** name, long long* laun
  */
 int sr_probe_fma_rate(int bits, double* lane_ops_per_s, void* stream);
 
+/*
+ * Allocation-failure injection and bookkeeping, for testing the error paths
+ * (the paper has no counterpart).  Every device allocation the library makes
+ * for a handle (workspace, plan, staging buffers) is counted.
+ *   sr_debug_fail_alloc(n)  n > 0: the n-th such allocation from now fails
+ *                           as if the device had run out of memory (the
+ *                           entry point that made it returns SR_ERR_OOM and
+ *                           releases what it had allocated); 0 turns the
+ *                           injection off.  SR_ERR_INVALID for n < 0.
+ *   sr_debug_alloc_count()  allocations attempted since the library loaded
+ *   sr_debug_live_bytes()   bytes of device memory the library's handles
+ *                           hold now
+ * Process-wide; not meant for concurrent use with other threads creating
+ * handles.
+ */
+int sr_debug_fail_alloc(int nth);
+long long sr_debug_alloc_count(void);
+long long sr_debug_live_bytes(void);
+
+/*
+ * Last-stage trimming switch, for testing (the paper has no counterpart).
+ * By default (enable = 1) the last stage's correction, residual and update
+ * on every SR level run only on the cells the finest genuine cells still
+ * depend on; every value kept is computed by the same arithmetic as on the
+ * full box, so the result is bitwise the same either way.  enable = 0 runs
+ * them on the full regions.  Drops the handle's captured graphs.
+ */
+int sr_debug_last_stage_trim(sr_fmg_t h, int enable);
+
 /* Human-readable name of a status code (static string). */
 const char* sr_fmg_status_string(int status);
 

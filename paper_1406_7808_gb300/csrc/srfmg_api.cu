@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -74,13 +75,13 @@ struct Hier {
   // (the post-smoother's update) and U_j as prolongation range (the cells
   // of w - t formed); ctrim_r[j] has U_j grown by one as compute region (the
   // residual) and by two as prolongation range (the correction onto level j).
+  // Box i of every one of these views is segment i, as on every SR level.
+  // Invariant: after a solve with trimming, slev[j].u and slev[j].r of the
+  // levels j < K hold the final values only on ctrim_u[j] (and slev[K] on
+  // trim_u); elsewhere they are stale.  Every solve (and every pass of the
+  // mixed mode) rebuilds the SR levels from the FMG prolongation before it
+  // reads them, so nothing reads the stale cells.
   std::vector<Geom> ctrim_r, ctrim_u;
-};
-
-struct Cheb {
-  int nu = 0;
-  double a = 0, b = 0, c2 = 0;      // degree-2 polynomial form
-  std::vector<double> alpha, beta;  // recurrence steps
 };
 
 // kernel kinds for the per-kernel profile: float64 storage and arithmetic;
@@ -128,6 +129,55 @@ struct Profile {
 
 }  // namespace
 
+// Chebyshev coefficients (declared in srfmg_internal.cuh)
+Cheb srfmg::chebyshev(int nu, double lo_frac, double hi_frac, double lmax) {
+  Cheb c;
+  c.nu = nu;
+  const double lo = lmax * lo_frac, hi = lmax * hi_frac;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  // three-term recurrence: d_0 = r_0/theta, d_m = rho_m rho_{m-1} d_{m-1} + (2 rho_m/delta) r_m
+  double rho_old = delta / theta;
+  for (int m = 0; m < nu; ++m) {
+    if (m == 0) {
+      c.alpha.push_back(0.0);
+      c.beta.push_back(1.0 / theta);
+    } else {
+      const double rho = 1.0 / (2.0 * theta / delta - rho_old);
+      c.alpha.push_back(rho * rho_old);
+      c.beta.push_back(2.0 * rho / delta);
+      rho_old = rho;
+    }
+  }
+  if (nu == 2) {
+    // x2 = x0 + c1 r0 + c2 B r0 with B r0 = D^-1 A r0 = r0 - W r0, W the
+    // neighbour part (7-point: the sum of the 6 neighbours of r0 over 6)
+    const double r0 = delta / theta;
+    const double r1 = 1.0 / (2.0 * theta / delta - r0);
+    const double c1 = (1.0 + r1 * r0) / theta + 2.0 * r1 / delta;
+    const double c2 = -2.0 * r1 / (delta * theta);
+    c.a = c1 + c2;
+    c.b = -c2 / 6.0;
+    c.c2 = c2;
+  }
+  return c;
+}
+
+// Allocation bookkeeping of the whole library (every handle): device
+// allocations made, bytes currently held, and the failure-injection
+// countdown of sr_debug_fail_alloc (0: off; n > 0: the n-th allocation from
+// now fails as if cudaMalloc had run out of memory).
+std::atomic<long long> g_allocs{0}, g_live_bytes{0}, g_fail_countdown{0};
+
+bool injected_failure() {
+  long long c = g_fail_countdown.load();
+  while (c > 0) {
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+  }
+  return false;
+}
+
+// Every device allocation of a handle goes through here; h->allocs owns it
+// (freed by free_all).
 struct sr_fmg_s {
   sr_fmg_config cfg{};
   int device = 0;
@@ -148,6 +198,7 @@ struct sr_fmg_s {
   double lmax = 2.0;               // lambda_max(D^-1 A)
   size_t bytes = 0;
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;  // size of each entry of allocs
   double* hbuf_f = nullptr;        // device staging for sr_fmg_solve_host
   double* hbuf_u = nullptr;
   unsigned long long* norms = nullptr;  // sr_fmg_vsolve: ||f||, ||f - A u|| as double bits
@@ -167,6 +218,7 @@ struct sr_fmg_s {
   int pslot = 0;
   bool pused[2] = {false, false};
   int launches = 0;                // kernel launches queued by the last solve
+  bool trim = true;                // last-stage trimming (sr_debug_last_stage_trim)
   Profile prof;
 
   Hier<double>& hier(double*) { return h64; }
@@ -251,7 +303,7 @@ void schedule(const sr_fmg_config& c, int* J) {
 int op_weights(const sr_fmg_config* c, W27* w, double* lmax) {
   if (c->stencil == 0 || c->stencil == 7) {
     *w = W27{6.0, 1.0, 0.0, 0.0};
-    *lmax = 2.0;
+    *lmax = kLambdaMax7;
     return SR_OK;
   }
   if (c->stencil != 27) return SR_ERR_INVALID;
@@ -332,48 +384,20 @@ int check_config(const sr_fmg_config* c) {
   return SR_OK;
 }
 
-Cheb chebyshev(int nu, double lo_frac, double hi_frac, double lmax) {
-  Cheb c;
-  c.nu = nu;
-  const double lo = lmax * lo_frac, hi = lmax * hi_frac;
-  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
-  // three-term recurrence: d_0 = r_0/theta, d_m = rho_m rho_{m-1} d_{m-1} + (2 rho_m/delta) r_m
-  double rho_old = delta / theta;
-  for (int m = 0; m < nu; ++m) {
-    if (m == 0) {
-      c.alpha.push_back(0.0);
-      c.beta.push_back(1.0 / theta);
-    } else {
-      const double rho = 1.0 / (2.0 * theta / delta - rho_old);
-      c.alpha.push_back(rho * rho_old);
-      c.beta.push_back(2.0 * rho / delta);
-      rho_old = rho;
-    }
-  }
-  if (nu == 2) {
-    // x2 = x0 + c1 r0 + c2 B r0 with B r0 = D^-1 A r0 = r0 - W r0, W the
-    // neighbour part (7-point: the sum of the 6 neighbours of r0 over 6)
-    const double r0 = delta / theta;
-    const double r1 = 1.0 / (2.0 * theta / delta - r0);
-    const double c1 = (1.0 + r1 * r0) / theta + 2.0 * r1 / delta;
-    const double c2 = -2.0 * r1 / (delta * theta);
-    c.a = c1 + c2;
-    c.b = -c2 / 6.0;
-    c.c2 = c2;
-  }
-  return c;
-}
-
 template <typename T>
 int dalloc(sr_fmg_s* h, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return SR_OK;
   void* q = nullptr;
+  ++g_allocs;
+  if (injected_failure()) return SR_ERR_OOM;
   if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     return SR_ERR_OOM;
   }
   h->allocs.push_back(q);
+  h->alloc_bytes.push_back(count * sizeof(T));
+  g_live_bytes += (long long)(count * sizeof(T));
   h->bytes += count * sizeof(T);
   if (cudaMemset(q, 0, count * sizeof(T)) != cudaSuccess) return SR_ERR_CUDA;
   *p = static_cast<T*>(q);
@@ -690,6 +714,14 @@ int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
     R.n = U.n = L.n;
     for (int d = 0; d < 3; ++d) R.nd[d] = U.nd[d] = L.nd[d];
     R.hboxes = U.hboxes = L.hboxes;
+    // box i of both levels must be the same segment: the fine box's genuine
+    // region is the coarse one's doubled
+    if (F.hboxes.size() != L.hboxes.size()) return SR_ERR_INVALID;
+    for (size_t i = 0; i < L.hboxes.size(); ++i)
+      for (int d = 0; d < 3; ++d)
+        if (F.hboxes[i].glo[d] != 2 * L.hboxes[i].glo[d] ||
+            F.hboxes[i].ghi[d] != 2 * L.hboxes[i].ghi[d])
+          return SR_ERR_INVALID;
     for (size_t i = 0; i < L.hboxes.size(); ++i) {
       const BoxDesc& c = L.hboxes[i];
       const BoxDesc& f = F.hboxes[i];
@@ -1013,7 +1045,7 @@ int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t
       // down the SR levels.  In the last stage the correction, the residual
       // and the update of every SR level therefore run on those regions only
       // (every value they keep is computed exactly as on the full box).
-      const bool last = k == K && h->post.nu == 2;
+      const bool last = k == K && h->post.nu == 2 && h->trim;
       if (last && j >= 2) {
         const Geom& D = H.ctrim_u[j - 1];
         LAUNCH(h, kind_of<T>(kDiff), D.tot_prolong, 1, 3 * w, s,
@@ -1104,8 +1136,12 @@ struct DeviceGuard {
 };
 
 void free_all(sr_fmg_s* h) {
-  for (void* p : h->allocs) cudaFree(p);
+  for (size_t i = 0; i < h->allocs.size(); ++i) {
+    cudaFree(h->allocs[i]);
+    g_live_bytes -= (long long)h->alloc_bytes[i];
+  }
   h->allocs.clear();
+  h->alloc_bytes.clear();
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   for (ProfRec& r : h->prof.recs) {
     cudaEventDestroy(r.e0);
@@ -1283,10 +1319,11 @@ int sr_fmg_solve_host_async(sr_fmg_t h, const double* f_host, double* u_host, vo
   const size_t cells = (size_t)srfmg::handle_cells(h);
   const size_t bytes = cells * sizeof(double);
   if (!h->cin) {
+    // staging slots (a retry after a failed allocation keeps what it got)
     int rc = SR_OK;
     for (int k = 0; k < 2 && !rc; ++k) {
-      rc = dalloc(h, &h->pf[k], cells);
-      if (!rc) rc = dalloc(h, &h->pu[k], cells);
+      if (!h->pf[k]) rc = dalloc(h, &h->pf[k], cells);
+      if (!rc && !h->pu[k]) rc = dalloc(h, &h->pu[k], cells);
     }
     if (rc) return rc;
     CK(cudaStreamCreateWithFlags(&h->cin, cudaStreamNonBlocking));
@@ -1338,9 +1375,9 @@ int sr_fmg_solve_host(sr_fmg_t h, const double* f_host, double* u_host, void* st
   DeviceGuard g(h->device);
   const size_t cells = (size_t)srfmg::handle_cells(h);
   const size_t bytes = cells * sizeof(double);
-  if (!h->hbuf_f) {
-    int rc = dalloc(h, &h->hbuf_f, cells);
-    if (!rc) rc = dalloc(h, &h->hbuf_u, cells);
+  {
+    int rc = h->hbuf_f ? SR_OK : dalloc(h, &h->hbuf_f, cells);
+    if (!rc && !h->hbuf_u) rc = dalloc(h, &h->hbuf_u, cells);
     if (rc) return rc;
   }
   cudaStream_t s = (cudaStream_t)stream;
@@ -1446,6 +1483,26 @@ int sr_fmg_profile_read(sr_fmg_t h, int kind, const char** name, long long* laun
   if (bytes) *bytes = h->prof.bytes[kind];
   return SR_OK;
 }
+
+int sr_debug_fail_alloc(int nth) {
+  if (nth < 0) return SR_ERR_INVALID;
+  g_fail_countdown.store(nth);
+  return SR_OK;
+}
+
+long long sr_debug_alloc_count(void) { return g_allocs.load(); }
+
+int sr_debug_last_stage_trim(sr_fmg_t h, int enable) {
+  if (!h) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  // captured graphs hold the previous launch sequence
+  for (const sr_fmg_s::GraphEntry& e : h->graphs) sr_fmg_batch_destroy(e.b);
+  h->graphs.clear();
+  h->trim = enable != 0;
+  return SR_OK;
+}
+
+long long sr_debug_live_bytes(void) { return g_live_bytes.load(); }
 
 const char* sr_fmg_status_string(int status) {
   switch (status) {

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 struct sr_fmg_s;  // solver handle (srfmg_api.cu)
 
 namespace srfmg {
@@ -114,6 +116,22 @@ inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   } while (0)
 
 enum Region { kCompute = 0, kProlong = 1, kRestrict = 2, kGenuine = 3 };
+
+// lambda_max(D^-1 A) of the 7-point operator (D = 6 n^2): the DST mode with
+// every wavenumber N has eigenvalue 12 n^2, i.e. 2 after D^-1
+constexpr double kLambdaMax7 = 2.0;
+
+// Chebyshev smoother S^nu on D^-1 A over [lo_frac, hi_frac] * lmax (Sec. 5.1):
+// the three-term recurrence d_m = alpha_m d_{m-1} + beta_m r_m, u += d_m,
+// and for nu = 2 the equivalent polynomial x2 = x0 + c1 r0 + c2 (D^-1 A) r0,
+// stored as a = c1 + c2 and b = -c2 / 6 (7-point: (D^-1 A) r = r - S(r) / 6,
+// S the neighbour sum) and c2 (srfmg_api.cu)
+struct Cheb {
+  int nu = 0;
+  double a = 0, b = 0, c2 = 0;      // degree-2 polynomial form
+  std::vector<double> alpha, beta;  // recurrence steps
+};
+Cheb chebyshev(int nu, double lo_frac, double hi_frac, double lmax);
 
 // ---- launchers; all enqueue on stream and return the launch status.  T is
 // ---- the storage and arithmetic type, except where noted.

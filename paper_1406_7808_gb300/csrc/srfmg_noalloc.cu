@@ -103,32 +103,20 @@ extern "C" int sr_op_smooth_noalloc(int n, int nu, double cheb_lo, double cheb_h
   L.max_ex = L.max_ey = L.max_ez = n;
   const FieldView fv{f, desc, 1};
 
-  // Chebyshev iteration on D^-1 A over [cheb_lo, cheb_hi] * 2 (the same
-  // coefficients as the allocating path); every scratch cell is written
+  // Chebyshev iteration on D^-1 A over [cheb_lo, cheb_hi] * lambda_max, the
+  // coefficients of the allocating path; every scratch cell is written
   // before it is read, so nothing has to be cleared between calls
-  const double lo = 2.0 * cheb_lo, hi = 2.0 * cheb_hi;
-  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  const Cheb c = chebyshev(nu, cheb_lo, cheb_hi, kLambdaMax7);
   if (nu == 2) {
-    const double r0 = delta / theta;
-    const double r1 = 1.0 / (2.0 * theta / delta - r0);
-    const double c1 = (1.0 + r1 * r0) / theta + 2.0 * r1 / delta;
-    const double c2 = -2.0 * r1 / (delta * theta);
     if (launch_cheb_residual(L, u, r, fv, s) != cudaSuccess) return SR_ERR_CUDA;
-    if (launch_cheb2_update(L, u, r, c1 + c2, -c2 / 6.0, s) != cudaSuccess) return SR_ERR_CUDA;
+    if (launch_cheb2_update(L, u, r, c.a, c.b, s) != cudaSuccess) return SR_ERR_CUDA;
     return SR_OK;
   }
-  double rho_old = delta / theta;
   for (int m = 0; m < nu; ++m) {
-    double alpha = 0.0, beta = 1.0 / theta;
-    if (m > 0) {
-      const double rho = 1.0 / (2.0 * theta / delta - rho_old);
-      alpha = rho * rho_old;
-      beta = 2.0 * rho / delta;
-      rho_old = rho;
-    }
     const int write_d = (nu > 1 && m < nu - 1) ? 1 : 0;
     if (launch_cheb_residual(L, u, r, fv, s) != cudaSuccess) return SR_ERR_CUDA;
-    if (launch_cheb_step(L, u, d, r, alpha, beta, write_d, s) != cudaSuccess) return SR_ERR_CUDA;
+    if (launch_cheb_step(L, u, d, r, c.alpha[m], c.beta[m], write_d, s) != cudaSuccess)
+      return SR_ERR_CUDA;
   }
   return SR_OK;
 }

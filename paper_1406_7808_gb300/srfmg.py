@@ -129,6 +129,12 @@ def load():
     lib.sr_op_residual_ex.argtypes = [PC, _VP, _VP, _VP, _VP]
     lib.sr_op_smooth_ex.argtypes = [PC, ctypes.c_int, _VP, _VP, _VP]
     lib.sr_probe_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]
+    lib.sr_debug_fail_alloc.argtypes = [ctypes.c_int]
+    lib.sr_debug_alloc_count.argtypes = []
+    lib.sr_debug_alloc_count.restype = ctypes.c_longlong
+    lib.sr_debug_live_bytes.argtypes = []
+    lib.sr_debug_live_bytes.restype = ctypes.c_longlong
+    lib.sr_debug_last_stage_trim.argtypes = [_VP, ctypes.c_int]
     _LIB = lib
     return lib
 
@@ -151,6 +157,22 @@ def probe_fma_rate(bits=64):
     rate = ctypes.c_double(0.0)
     _check(load().sr_probe_fma_rate(int(bits), ctypes.byref(rate), _stream()), "sr_probe_fma_rate")
     return rate.value
+
+
+def debug_fail_alloc(nth):
+    """Make the nth device allocation of the library from now fail as out of
+    memory (0: off); for testing the error paths."""
+    _check(load().sr_debug_fail_alloc(int(nth)), "sr_debug_fail_alloc")
+
+
+def debug_alloc_count():
+    """Device allocations the library has attempted since it was loaded."""
+    return int(load().sr_debug_alloc_count())
+
+
+def debug_live_bytes():
+    """Bytes of device memory the library's handles hold now."""
+    return int(load().sr_debug_live_bytes())
 
 
 def mbs_schedule(J1, K):
@@ -263,6 +285,11 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+    def debug_last_stage_trim(self, enable):
+        """Turn the last stage's trimming on (default) or off (same result)."""
+        _check(load().sr_debug_last_stage_trim(self._h, int(bool(enable))),
+               "sr_debug_last_stage_trim")
 
     @property
     def workspace_bytes(self):

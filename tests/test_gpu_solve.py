@@ -131,6 +131,26 @@ def test_sr_fmg_parity_full_size_paper_depth(gpu, oracle_mod):
     assert 0.99 < e_r < 1.2
 
 
+@pytest.mark.parametrize("n,kw", [
+    (128, dict(seg=32, K=3, A=8, B=0)),
+    (128, dict(seg=32, K=3, A=11, B=1, n_coarse=16)),
+    (128, dict(seg=32, K=3, A=8, B=0, mixed=True)),
+    (96, dict(seg=24, K=3, A=6, B=0, graph=True)),
+])
+def test_last_stage_trimming_is_bitwise(gpu, n, kw):
+    """The last stage run on the trimmed regions returns exactly the values
+    of the full-region run (every kept value takes the same arithmetic)."""
+    f, _ = inputs.manufactured(n, 2)
+    with gpu.Solver(n, **kw) as s:
+        a = s.solve(T(f)).cpu().numpy()
+        s.debug_last_stage_trim(False)
+        b = s.solve(T(f)).cpu().numpy()
+        s.debug_last_stage_trim(True)
+        c = s.solve(T(f)).cpu().numpy()
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, c)
+
+
 def test_repeated_solves_identical(gpu):
     n = 64
     f, _ = inputs.manufactured(n, 3)
