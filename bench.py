@@ -61,6 +61,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the mixed-precision and batched measurements")
+    p.add_argument("--shard", action="store_true",
+                   help="split one problem's segments among the ranks (redundant coarse "
+                        "solves, one all-reduce of the transition level per SR stage) "
+                        "instead of one replica per rank")
     return p.parse_args()
 
 
@@ -513,6 +517,101 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_sharded(args):
+    """One 256^3 problem, its 512 segments split into contiguous ranges, one
+    per rank; every rank holds the whole f and solves the transition level and
+    below redundantly; per SR stage one all-reduce (sum) of the two
+    transition-level arrays (32^3 doubles each) over NCCL.  value = n^3 /
+    the slowest rank's time per solve (strong scaling of one problem)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1406_7808_gb300 import build, inputs, srfmg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def allreduce(ts):
+        for t in ts:
+            dist.all_reduce(t)
+
+    reduce_sum = allreduce if world > 1 else None
+    nsegs = srfmg.segment_count(N, SR["seg"])
+    first, count = srfmg.segment_range(nsegs, rank, world)
+    f, u_exact = inputs.manufactured(N, SEED)
+    ft = torch.from_numpy(f).cuda()
+    ut = torch.zeros_like(ft)
+    stream = torch.cuda.current_stream()
+    solver = srfmg.Solver(N, segments=(first, count), **SR)
+
+    def step():
+        srfmg.solve_staged([solver], ft, ut, reduce_sum)
+
+    for _ in range(args.warmup):
+        step()
+    solver.check()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    sampler = ClockSampler(local)
+    with sampler:
+        ms = _time_loop(step, args.steps, stream) / args.steps
+    solver.check()
+    launches = solver.launches_per_solve * args.steps
+    ms = max_over_ranks(ms, world)
+    clocks = sampler.summary()
+    # end to end: f in from pinned host memory and this rank's u out, every step
+    fh = torch.from_numpy(f).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ft.copy_(fh, non_blocking=True)
+        step()
+        uh.copy_(ut, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world) / args.steps
+    # the whole solution (each cell written by one rank, the others zero)
+    # and its error ratio against plain FMG on the same f
+    if world > 1:
+        dist.all_reduce(ut)
+    u = ut.cpu().numpy()
+    with srfmg.Solver(N, **PLAIN) as p:
+        up = p.solve(ft).cpu().numpy()
+    e_r = float(np.abs(u - u_exact).max() / np.abs(up - u_exact).max())
+    solver.close()
+    if rank == 0:
+        name, J = workload_name()
+        line = {"metric": METRIC, "value": N ** 3 / (ms / 1e3), "unit": "DOF/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": name, "n": N, **SR, "J": J,
+                           "parallelism": f"segments split over {world} ranks, transition "
+                                          f"level all-reduced per stage",
+                           "l2": "inputs larger than L2: f is 134 MB"},
+                "e2e": {"value": N ** 3 / e2e_s, "unit": "DOF/s",
+                        "h2d_bytes_per_step": N ** 3 * 8, "d2h_bytes_per_step": N ** 3 * 8},
+                "gpu_launches": launches, "clocks": clocks,
+                "accuracy": {"e_r": e_r},
+                "exchange_bytes_per_stage": 2 * (N >> SR["K"]) ** 3 * 8}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def profiled_bytes(solver, ft, ut, reps=2):
     """Algorithmic bytes of one solve, from the library's per-kernel profile."""
     solver.profile(True)
@@ -676,6 +775,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.shard:
+        run_sharded(args)
     else:
         run_ours(args)
 

@@ -119,6 +119,15 @@ typedef struct sr_fmg_s* sr_fmg_t;
  *             profiler is on launch kernel by kernel.  Not for use inside
  *             the caller's own stream capture.  0 (default): kernel by
  *             kernel.
+ *   seg_first, seg_count  segment range (SR_FP64 with seg > 0, K > 0): the
+ *             handle holds and processes only segments seg_first ..
+ *             seg_first + seg_count - 1, numbered x fastest over the grid of
+ *             segments (n len[0] / seg of them along x), and solves through
+ *             the stage entry points below, one handle per process or GPU
+ *             sharing the segments of one problem; the global levels (the
+ *             transition level and below) are solved redundantly by every
+ *             handle (Sec. 7: redundant coarse-grid solves instead of idle
+ *             processes).  seg_count = 0 (default): all segments.
  */
 typedef struct {
   int n;
@@ -137,6 +146,7 @@ typedef struct {
   int stencil;
   double w[3];
   int graph;
+  int seg_first, seg_count;
 } sr_fmg_config;
 
 /* Fill cfg with the defaults for an n^3 grid: unit cube, 7-point operator,
@@ -208,6 +218,42 @@ int sr_fmg_vsolve(sr_fmg_t h, const double* f_dev, double* u_dev, double rtol, i
  */
 int sr_fmg_solve_host_async(sr_fmg_t h, const double* f_host, double* u_host, void* stream);
 int sr_fmg_check_host(sr_fmg_t h);
+
+/*
+ * Stage-by-stage SR-FMG solve, for sharing the segments of one problem among
+ * several handles (segment ranges; any FP64 SR handle works, one handle then
+ * solving alone).  Each SR stage k = 1..K (Fig. "FMG segmental refinement")
+ * is split at the transition level, the one step of the method where
+ * segments exchange data (Sec. 4):
+ *   sr_fmg_stage_down(h, f, k)   k = 1 first runs the f hierarchy and the
+ *                       global FMG up to the transition level; then the FMG
+ *                       prolongation onto level k, S^alpha, and the down-leg
+ *                       of the SR V-cycle on the handle's segments, which
+ *                       owner-write their genuine transition-level cells of
+ *                       \hat I u_1 and of the restricted residual into the
+ *                       two exchange arrays (all other cells zero).
+ *   sr_fmg_stage_buffers(h, &uhat0, &rho0, &count)   device pointers of the
+ *                       two exchange arrays, count doubles each (the
+ *                       transition level's cells, C order); owned by h.
+ *   (the caller)        replaces both arrays, on every handle, by their sum
+ *                       over all handles of the problem (an all-reduce): as
+ *                       every cell has one owner the sum is exact, and every
+ *                       handle then holds the whole transition level.
+ *   sr_fmg_stage_up(h, f, k, u)  the transition-level right-hand side, the
+ *                       global V-cycle (redundant on every handle) and the
+ *                       up-leg on the handle's segments; after k = K the
+ *                       genuine finest cells of the handle's segments go to
+ *                       u (n^3 doubles; the other cells are not written).
+ * f: the whole right-hand side on every handle (device, n^3 doubles).  The
+ * calls queue work on stream and return launch errors; sr_fmg_check reports
+ * a non-finite f.  Handles with a segment range refuse sr_fmg_solve and the
+ * other whole-solve entry points (SR_ERR_INVALID).  SR_MIXED handles and
+ * plain FMG handles are refused too.  Stage calls on one handle run in
+ * order: down(1), exchange, up(1), down(2), ..., up(K).
+ */
+int sr_fmg_stage_down(sr_fmg_t h, const double* f_dev, int k, void* stream);
+int sr_fmg_stage_buffers(sr_fmg_t h, double** uhat0, double** rho0, size_t* count);
+int sr_fmg_stage_up(sr_fmg_t h, const double* f_dev, int k, double* u_dev, void* stream);
 
 /* Number of kernel launches the handle's last queued solve made. */
 int sr_fmg_launches_per_solve(sr_fmg_t h, int* launches);

@@ -219,6 +219,7 @@ struct sr_fmg_s {
   bool pused[2] = {false, false};
   int launches = 0;                // kernel launches queued by the last solve
   bool trim = true;                // last-stage trimming (sr_debug_last_stage_trim)
+  bool sharded = false;            // the handle owns a range of the segments only
   Profile prof;
 
   Hier<double>& hier(double*) { return h64; }
@@ -368,13 +369,18 @@ int check_config(const sr_fmg_config* c) {
     if (coarse_plan(nd) == kCoarseUnsupported) return SR_ERR_UNSUPPORTED_SIZE;
   }
   if (c->seg < 0 || c->K < 0 || c->K > SR_FMG_MAXK) return SR_ERR_INVALID;
-  if (c->seg == 0 || c->K == 0) return SR_OK;
+  if (c->seg == 0 || c->K == 0) return (c->seg_count || c->seg_first) ? SR_ERR_INVALID : SR_OK;
   if (c->mbs && (c->A < 0 || c->A % 2 || c->A > 4096 >> c->K)) return SR_ERR_INVALID;
   if (c->n % c->seg) return SR_ERR_INVALID;
   if (c->seg % (1 << c->K)) return SR_ERR_INVALID;
   if (halvings_to_coarsest(c->n >> c->K, c->n_coarse) < 0) return SR_ERR_UNSUPPORTED_SIZE;
   const long long nseg1 = c->n / c->seg;
-  if (nseg1 * nseg1 * nseg1 * len[0] * len[1] * len[2] > 65535) return SR_ERR_UNSUPPORTED_SIZE;
+  const long long nsegs = nseg1 * nseg1 * nseg1 * len[0] * len[1] * len[2];
+  if (nsegs > 65535) return SR_ERR_UNSUPPORTED_SIZE;
+  if (c->seg_count < 0 || c->seg_first < 0) return SR_ERR_INVALID;
+  if (c->seg_count > 0 &&
+      ((long long)c->seg_first + c->seg_count > nsegs || c->precision != SR_FP64))
+    return SR_ERR_INVALID;
   int J[SR_FMG_MAXK];
   schedule(*c, J);
   for (int k = 1; k <= c->K; ++k) {
@@ -625,6 +631,9 @@ int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
   schedule(c, J);
   int nsd[3];
   for (int d = 0; d < 3; ++d) nsd[d] = c.n * h->len[d] / c.seg;  // segments per dimension
+  // the segments this handle owns: [seg_lo, seg_hi) in x-fastest order
+  const int seg_lo = c.seg_count > 0 ? c.seg_first : 0;
+  const int seg_hi = c.seg_count > 0 ? c.seg_first + c.seg_count : nsd[0] * nsd[1] * nsd[2];
   const bool need_d = c.alpha > 2 || c.nu1 > 2 || c.nu2 > 2 || fused_fmg_step<T>(h);
   H.slev.resize(K + 1);
   for (int k = 1; k <= K; ++k) {
@@ -634,9 +643,12 @@ int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
     const int s0 = c.seg >> K;
     std::vector<BoxDesc> boxes;
     long long slot = 0;
+    int index = -1;  // segment number, x fastest over the segment grid
     for (int pz = 0; pz < nsd[2]; ++pz)
       for (int py = 0; py < nsd[1]; ++py)
         for (int px = 0; px < nsd[0]; ++px) {
+          ++index;
+          if (index < seg_lo || index >= seg_hi) continue;  // another handle's segment
           const int q[3] = {px, py, pz};
           BoxDesc b;
           std::memset(&b, 0, sizeof(b));
@@ -977,104 +989,135 @@ int f_hierarchy(sr_fmg_s* h, Hier<T>& H, const T* f, int check, cudaStream_t s) 
   return SR_OK;
 }
 
+// SR stage k, first half: the FMG prolongation onto level k and S^alpha,
+// then the down-leg of FASMGVSR(k) to the transition level, where every
+// segment owner-writes its genuine level-0 cells of \hat I u_1 (into t_0) and
+// of the restricted residual (rho_0)
+template <typename T>
+int sr_stage_down(sr_fmg_s* h, Hier<T>& H, const T* f, int k, cudaStream_t s) {
+  const int K = h->K;
+  Level<T>& L0 = H.glev[h->G - 1];
+  const double w = sizeof(T);
+  auto fview = [&](int j) -> FieldT<T> {
+    return view_global<T>(H.slev[j], j == K ? f : H.slev[j].f);
+  };
+  Level<T>& Lk = H.slev[k];
+  // u_k <- Pi u_{k-1} on Omega^C_k u Omega^GSR_k, then S^alpha on Omega^C_k
+  const T* r_first = nullptr;
+  {
+    const Level<T>& C = (k == 1) ? L0 : H.slev[k - 1];
+    LAUNCH(h, kind_of<T>(kProlongSet), Lk.tot_prolong, 3.75, 1.125 * w, s,
+           launch_prolong<T>(C.view, C.u, Lk.view, Lk.u, 0, s));
+    int rc = fmg_step(h, Lk, Lk.u, fview(k), s, &r_first);
+    if (rc) return rc;
+  }
+  // FASMGVSR(k): down-leg
+  for (int j = k; j >= 1; --j) {
+    Level<T>& Lj = H.slev[j];
+    const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
+    // at the stage's top level the first residual may come from the fused
+    // FMG step; below it, with the level's right-hand side (float64)
+    const T* rf = (j == k) ? r_first : (kFirstResidual<T> ? Lj.r : nullptr);
+    int rc = smooth(h, Lj, h->pre, Lj.u, rhs, s, rf);
+    if (rc) return rc;
+    if (j > 1) {
+      Level<T>& C = H.slev[j - 1];
+      rc = resid_restrict<T>(h, Lj, Lj.u, rhs, C, C.u, C.rho, s);
+      if (rc) return rc;
+      const bool cr = kFirstResidual<T>;
+      LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h) + (cr ? 1 : 0), (cr ? 5 : 4) * w,
+             s,
+             op_coarse_rhs<T>(h, C.view, Lj.view, C.u, C.rho, C.rhs, C.t, cr ? C.r : nullptr, s));
+      if (!h->op27)
+        LAUNCH(h, kind_of<T>(kShellCopy), C.tot_cells / 4, 0, 2 * w, s,
+               launch_shell_copy<T>(C.view, C.u, C.t, s));
+    } else {
+      rc = resid_restrict<T>(h, Lj, Lj.u, rhs, L0, L0.t, L0.rho, s);
+      if (rc) return rc;
+    }
+  }
+  return SR_OK;
+}
+
+// SR stage k, second half (t_0 and rho_0 complete on the whole transition
+// level): u_0 <- t_0, r_0 = rho_0 + L_0 u_0, the global FASMGV, then the
+// up-leg (corrections onto Omega^C u Omega^GSR and S^nu2) back to level k
+template <typename T>
+int sr_stage_up(sr_fmg_s* h, Hier<T>& H, const T* f, int k, cudaStream_t s) {
+  const int K = h->K;
+  Level<T>& L0 = H.glev[h->G - 1];
+  const double w = sizeof(T);
+  auto fview = [&](int j) -> FieldT<T> {
+    return view_global<T>(H.slev[j], j == K ? f : H.slev[j].f);
+  };
+  // level 0 is solved directly and needs no residual
+  const bool cr = kFirstResidual<T> && h->G - 1 >= 1;
+  LAUNCH(h, kind_of<T>(kTransitionRhs), L0.tot_cells, ops_rhs(h) + (cr ? 1 : 0), (cr ? 5 : 4) * w,
+         s, op_transition_rhs<T>(h, L0.view, L0.t, L0.rho, L0.u, L0.rhs, cr ? L0.r : nullptr, s));
+  int rc = vcycle_global(h, H, h->G - 1, L0.u, view_global<T>(L0, L0.rhs), s, cr ? L0.r : nullptr);
+  if (rc) return rc;
+  // up-leg
+  for (int j = 1; j <= k; ++j) {
+    Level<T>& Lj = H.slev[j];
+    const Level<T>& C = (j == 1) ? L0 : H.slev[j - 1];
+    // The solve's last operations: only the finest level's genuine cells
+    // are returned.  After its correction they depend on u within two
+    // cells and on r within one cell of them; the correction reads the
+    // level below on the cells U its prolongation touches, which depend
+    // on that level's u and r within two and one cells of U, and so on
+    // down the SR levels.  In the last stage the correction, the residual
+    // and the update of every SR level therefore run on those regions only
+    // (every value they keep is computed exactly as on the full box).
+    const bool last = k == K && h->post.nu == 2 && h->trim;
+    if (last && j >= 2) {
+      const Geom& D = H.ctrim_u[j - 1];
+      LAUNCH(h, kind_of<T>(kDiff), D.tot_prolong, 1, 3 * w, s,
+             launch_diff<T>(D.view, C.u, C.t, C.rho, s, 1));
+    } else {
+      LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
+             launch_diff<T>(C.view, C.u, C.t, C.rho, s));
+    }
+    const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
+    if (last) {
+      const Geom& TR = (j == K) ? H.trim_r : H.ctrim_r[j];
+      const Geom& TU = (j == K) ? H.trim_u : H.ctrim_u[j];
+      LAUNCH(h, kind_of<T>(kProlongAdd), TR.tot_prolong, 3.75, 2.125 * w, s,
+             launch_prolong<T>(C.view, C.rho, TR.view, Lj.u, 1, s));
+      LAUNCH(h, kind_of<T>(kChebResidual), TR.tot_cells, ops_smooth(h), 3 * w, s,
+             op_cheb_residual<T>(h, TR.view, Lj.u, Lj.r, rhs, s));
+      LAUNCH(h, kind_of<T>(kCheb2Update), TU.tot_cells, ops_smooth(h), 3 * w, s,
+             op_cheb2_update<T>(h, TU.view, Lj.u, Lj.r, h->post, s));
+      continue;
+    }
+    LAUNCH(h, kind_of<T>(kProlongAdd), Lj.tot_prolong, 3.75, 2.125 * w, s,
+           launch_prolong<T>(C.view, C.rho, Lj.view, Lj.u, 1, s));
+    rc = smooth(h, Lj, h->post, Lj.u, rhs, s);
+    if (rc) return rc;
+  }
+  return SR_OK;
+}
+
+// genuine finest cells of the handle's segments into u (add == 0) or added
+// to it (add == 1)
+template <typename T>
+int sr_gather(sr_fmg_s* h, Hier<T>& H, double* u, int add, cudaStream_t s) {
+  const double w = sizeof(T);
+  const int K = h->K;
+  LAUNCH(h, kind_of<T>(kGather), H.slev[K].tot_genuine, add ? 1 : 0, w + (add ? 16 : 8), s,
+         launch_gather_genuine<T>(H.slev[K].view, H.slev[K].u, u, add, s));
+  return SR_OK;
+}
+
 // the SR stages k = 1..K after the global FMG; the genuine finest cells go to
 // u (add == 0) or are added to it (add == 1)
 template <typename T>
 int run_sr(sr_fmg_s* h, Hier<T>& H, const T* f, double* u, int add, cudaStream_t s) {
-  const int K = h->K;
-  Level<T>& L0 = H.glev[h->G - 1];
-  const double w = sizeof(T);
-  auto fview = [&](int k) -> FieldT<T> {
-    return view_global<T>(H.slev[k], k == K ? f : H.slev[k].f);
-  };
-  for (int k = 1; k <= K; ++k) {
-    Level<T>& Lk = H.slev[k];
-    // u_k <- Pi u_{k-1} on Omega^C_k u Omega^GSR_k, then S^alpha on Omega^C_k
-    const T* r_first = nullptr;
-    {
-      const Level<T>& C = (k == 1) ? L0 : H.slev[k - 1];
-      LAUNCH(h, kind_of<T>(kProlongSet), Lk.tot_prolong, 3.75, 1.125 * w, s,
-             launch_prolong<T>(C.view, C.u, Lk.view, Lk.u, 0, s));
-      int rc = fmg_step(h, Lk, Lk.u, fview(k), s, &r_first);
-      if (rc) return rc;
-    }
-    // FASMGVSR(k): down-leg
-    for (int j = k; j >= 1; --j) {
-      Level<T>& Lj = H.slev[j];
-      const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
-      // at the stage's top level the first residual may come from the fused
-      // FMG step; below it, with the level's right-hand side (float64)
-      const T* rf = (j == k) ? r_first : (kFirstResidual<T> ? Lj.r : nullptr);
-      int rc = smooth(h, Lj, h->pre, Lj.u, rhs, s, rf);
-      if (rc) return rc;
-      if (j > 1) {
-        Level<T>& C = H.slev[j - 1];
-        rc = resid_restrict<T>(h, Lj, Lj.u, rhs, C, C.u, C.rho, s);
-        if (rc) return rc;
-        const bool cr = kFirstResidual<T>;
-        LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h) + (cr ? 1 : 0),
-               (cr ? 5 : 4) * w, s,
-               op_coarse_rhs<T>(h, C.view, Lj.view, C.u, C.rho, C.rhs, C.t, cr ? C.r : nullptr,
-                                s));
-        if (!h->op27)
-          LAUNCH(h, kind_of<T>(kShellCopy), C.tot_cells / 4, 0, 2 * w, s,
-                 launch_shell_copy<T>(C.view, C.u, C.t, s));
-      } else {
-        rc = resid_restrict<T>(h, Lj, Lj.u, rhs, L0, L0.t, L0.rho, s);
-        if (rc) return rc;
-      }
-    }
-    // transition level: u_0 <- \hat I u_1, t_0 = u_0, r_0 = rho_0 + L_0 u_0, FASMGV
-    // level 0 is solved directly and needs no residual
-    const bool cr = kFirstResidual<T> && h->G - 1 >= 1;
-    LAUNCH(h, kind_of<T>(kTransitionRhs), L0.tot_cells, ops_rhs(h) + (cr ? 1 : 0),
-           (cr ? 5 : 4) * w, s,
-           op_transition_rhs<T>(h, L0.view, L0.t, L0.rho, L0.u, L0.rhs, cr ? L0.r : nullptr, s));
-    int rc = vcycle_global(h, H, h->G - 1, L0.u, view_global<T>(L0, L0.rhs), s,
-                           cr ? L0.r : nullptr);
+  for (int k = 1; k <= h->K; ++k) {
+    int rc = sr_stage_down<T>(h, H, f, k, s);
+    if (!rc) rc = sr_stage_up<T>(h, H, f, k, s);
     if (rc) return rc;
-    // up-leg
-    for (int j = 1; j <= k; ++j) {
-      Level<T>& Lj = H.slev[j];
-      const Level<T>& C = (j == 1) ? L0 : H.slev[j - 1];
-      // The solve's last operations: only the finest level's genuine cells
-      // are returned.  After its correction they depend on u within two
-      // cells and on r within one cell of them; the correction reads the
-      // level below on the cells U its prolongation touches, which depend
-      // on that level's u and r within two and one cells of U, and so on
-      // down the SR levels.  In the last stage the correction, the residual
-      // and the update of every SR level therefore run on those regions only
-      // (every value they keep is computed exactly as on the full box).
-      const bool last = k == K && h->post.nu == 2 && h->trim;
-      if (last && j >= 2) {
-        const Geom& D = H.ctrim_u[j - 1];
-        LAUNCH(h, kind_of<T>(kDiff), D.tot_prolong, 1, 3 * w, s,
-               launch_diff<T>(D.view, C.u, C.t, C.rho, s, 1));
-      } else {
-        LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
-               launch_diff<T>(C.view, C.u, C.t, C.rho, s));
-      }
-      const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
-      if (last) {
-        const Geom& TR = (j == K) ? H.trim_r : H.ctrim_r[j];
-        const Geom& TU = (j == K) ? H.trim_u : H.ctrim_u[j];
-        LAUNCH(h, kind_of<T>(kProlongAdd), TR.tot_prolong, 3.75, 2.125 * w, s,
-               launch_prolong<T>(C.view, C.rho, TR.view, Lj.u, 1, s));
-        LAUNCH(h, kind_of<T>(kChebResidual), TR.tot_cells, ops_smooth(h), 3 * w, s,
-               op_cheb_residual<T>(h, TR.view, Lj.u, Lj.r, rhs, s));
-        LAUNCH(h, kind_of<T>(kCheb2Update), TU.tot_cells, ops_smooth(h), 3 * w, s,
-               op_cheb2_update<T>(h, TU.view, Lj.u, Lj.r, h->post, s));
-        continue;
-      }
-      LAUNCH(h, kind_of<T>(kProlongAdd), Lj.tot_prolong, 3.75, 2.125 * w, s,
-             launch_prolong<T>(C.view, C.rho, Lj.view, Lj.u, 1, s));
-      rc = smooth(h, Lj, h->post, Lj.u, rhs, s);
-      if (rc) return rc;
-    }
   }
-  LAUNCH(h, kind_of<T>(kGather), H.slev[K].tot_genuine, add ? 1 : 0, w + (add ? 16 : 8), s,
-         launch_gather_genuine<T>(H.slev[K].view, H.slev[K].u, u, add, s));
-  return SR_OK;
+  return sr_gather<T>(h, H, u, add, s);
 }
 
 // one FMG / SR-FMG solve of A x = f in storage type T.  With T = double and
@@ -1099,6 +1142,7 @@ int solve_once(sr_fmg_s* h, const T* f, double* out, int add, int check, cudaStr
 }
 
 int enqueue_solve(sr_fmg_s* h, const double* f, double* u, cudaStream_t s) {
+  if (h->sharded) return SR_ERR_INVALID;  // a segment range solves stage by stage
   h->launches = 0;
   if (!h->mixed) return solve_once<double>(h, f, u, 0, 1, s);
   // float64 defect correction around the float32 solve
@@ -1248,6 +1292,7 @@ int sr_fmg_create(sr_fmg_t* out, const sr_fmg_config* cfg) {
   }
   h->mixed = cfg->precision == SR_MIXED;
   h->K = (cfg->seg > 0) ? cfg->K : 0;
+  h->sharded = cfg->seg_count > 0;
   lengths_of(cfg, h->len);
   op_weights(cfg, &h->w27, &h->lmax);
   h->op27 = cfg->stencil == 27;
@@ -1444,6 +1489,46 @@ int sr_fmg_vsolve(sr_fmg_t h, const double* f_dev, double* u_dev, double rtol, i
     if ((rc = norm(u_dev, 1, &r))) return rc;
   }
   return SR_OK;
+}
+
+int sr_fmg_stage_down(sr_fmg_t h, const double* f_dev, int k, void* stream) {
+  if (!h || !f_dev || h->mixed || h->K == 0 || k < 1 || k > h->K) return SR_ERR_INVALID;
+  if (!is_device_ptr(f_dev)) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Hier<double>& H = h->h64;
+  if (k == 1) {  // the f hierarchy and the global FMG up to the transition level
+    h->launches = 0;
+    int rc = f_hierarchy<double>(h, H, f_dev, 1, s);
+    if (!rc) rc = run_fmg_global<double>(h, H, f_dev, nullptr, s);
+    if (rc) return rc;
+  }
+  // the exchange arrays hold this handle's genuine cells only: clear them
+  const Level<double>& L0 = H.glev[h->G - 1];
+  const size_t bytes = (size_t)cells_of(L0) * sizeof(double);
+  CK(cudaMemsetAsync(L0.t, 0, bytes, s));
+  CK(cudaMemsetAsync(L0.rho, 0, bytes, s));
+  return sr_stage_down<double>(h, H, f_dev, k, s);
+}
+
+int sr_fmg_stage_buffers(sr_fmg_t h, double** uhat0, double** rho0, size_t* count) {
+  if (!h || !uhat0 || !rho0 || !count || h->mixed || h->K == 0) return SR_ERR_INVALID;
+  const Level<double>& L0 = h->h64.glev[h->G - 1];
+  *uhat0 = L0.t;
+  *rho0 = L0.rho;
+  *count = (size_t)cells_of(L0);
+  return SR_OK;
+}
+
+int sr_fmg_stage_up(sr_fmg_t h, const double* f_dev, int k, double* u_dev, void* stream) {
+  if (!h || !f_dev || h->mixed || h->K == 0 || k < 1 || k > h->K) return SR_ERR_INVALID;
+  if (k == h->K && (!u_dev || !is_device_ptr(u_dev))) return SR_ERR_INVALID;
+  if (!is_device_ptr(f_dev)) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = sr_stage_up<double>(h, h->h64, f_dev, k, s);
+  if (!rc && k == h->K) rc = sr_gather<double>(h, h->h64, u_dev, 0, s);
+  return rc;
 }
 
 int sr_fmg_launches_per_solve(sr_fmg_t h, int* launches) {

@@ -58,6 +58,8 @@ class Config(ctypes.Structure):
         ("stencil", ctypes.c_int),
         ("w", ctypes.c_double * 3),
         ("graph", ctypes.c_int),
+        ("seg_first", ctypes.c_int),
+        ("seg_count", ctypes.c_int),
     ]
 
 
@@ -135,6 +137,10 @@ def load():
     lib.sr_debug_live_bytes.argtypes = []
     lib.sr_debug_live_bytes.restype = ctypes.c_longlong
     lib.sr_debug_last_stage_trim.argtypes = [_VP, ctypes.c_int]
+    lib.sr_fmg_stage_down.argtypes = [_VP, _VP, ctypes.c_int, _VP]
+    lib.sr_fmg_stage_buffers.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                         ctypes.POINTER(ctypes.c_size_t)]
+    lib.sr_fmg_stage_up.argtypes = [_VP, _VP, ctypes.c_int, _VP, _VP]
     _LIB = lib
     return lib
 
@@ -187,11 +193,13 @@ def buffer_schedule(A, B, K):
 
 def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, nu2=2,
                 cheb_lo=1.0 / 6.0, cheb_hi=1.0, precision=SR_FP64, n_outer=2, mixed=False,
-                mbs=False, lengths=(1, 1, 1), stencil=7, weights=None, graph=False):
+                mbs=False, lengths=(1, 1, 1), stencil=7, weights=None, graph=False,
+                segments=None):
     """sr_fmg_config with n cells per unit length (mixed=True selects SR_MIXED;
     mbs=True the maximum buffer schedule J_k = 2^(k-1) A; lengths the domain
     [0, l0] x [0, l1] x [0, l2]; stencil 7 or 27 with weights (faces, edges,
-    corners); graph=True queues each solve as one captured CUDA graph)."""
+    corners); graph=True queues each solve as one captured CUDA graph;
+    segments=(first, count) a segment range, solved stage by stage)."""
     c = Config()
     load().sr_fmg_default_config(ctypes.byref(c), int(n))
     c.n_coarse, c.seg, c.K, c.A, c.B = n_coarse, seg, K, A, B
@@ -209,6 +217,8 @@ def make_config(n, *, seg=0, K=0, A=8, B=0, J=None, n_coarse=0, alpha=1, nu1=2, 
         c.len[d] = int(lengths[d])
     c.stencil = int(stencil)
     c.graph = int(bool(graph))
+    if segments is not None:
+        c.seg_first, c.seg_count = int(segments[0]), int(segments[1])
     if weights is None and int(stencil) == 27:
         weights = W27_DEFAULT
     if weights is not None:
@@ -285,6 +295,38 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+    # ---- stage-by-stage solve (segment ranges shared among handles) ----
+
+    @property
+    def K(self):
+        return int(self.config.K) if self.config.seg else 0
+
+    def stage_down(self, f, k):
+        """SR stage k up to the transition level (k = 1 also runs the f
+        hierarchy and the global FMG); the handle's genuine transition-level
+        cells land in the exchange arrays, zeros elsewhere."""
+        _check(load().sr_fmg_stage_down(self._h, _dev(f, self.shape, "f"), int(k), _stream()),
+               "sr_fmg_stage_down")
+
+    def stage_buffers(self):
+        """The two exchange arrays (\\hat I u_1 and the restricted residual
+        on the transition level) as torch float64 CUDA tensors that alias the
+        handle's memory: the caller sums them over all handles in place."""
+        import torch
+        a, b, count = _VP(), _VP(), ctypes.c_size_t()
+        _check(load().sr_fmg_stage_buffers(self._h, ctypes.byref(a), ctypes.byref(b),
+                                           ctypes.byref(count)), "sr_fmg_stage_buffers")
+        return tuple(torch.as_tensor(_DeviceArray(p.value, count.value), device="cuda")
+                     for p in (a, b))
+
+    def stage_up(self, f, k, out):
+        """Transition level, global V-cycle and the up-leg of stage k; after
+        the last stage the handle's genuine finest cells go to out."""
+        _check(load().sr_fmg_stage_up(self._h, _dev(f, self.shape, "f"), int(k),
+                                      _dev(out, self.shape, "out"), _stream()),
+               "sr_fmg_stage_up")
+        return out
 
     def debug_last_stage_trim(self, enable):
         """Turn the last stage's trimming on (default) or off (same result)."""
@@ -383,6 +425,74 @@ class Solver:
             ctypes.c_void_p(out.data_ptr())
         _check(load().sr_fmg_solve_host(self._h, fp, up, _stream()), "sr_fmg_solve_host")
         return out
+
+
+class _DeviceArray:
+    """A float64 vector in device memory the library owns, exposed through
+    the CUDA array interface (torch.as_tensor wraps it without a copy)."""
+
+    def __init__(self, ptr, count):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+def segment_range(nsegs, rank, world):
+    """(first, count) of the contiguous share of nsegs segments that rank
+    `rank` of `world` owns (shares differ by at most one segment)."""
+    first = rank * nsegs // world
+    return first, (rank + 1) * nsegs // world - first
+
+
+def segment_count(n, seg, lengths=(1, 1, 1)):
+    """Segments of an SR configuration: (n l0 / seg)(n l1 / seg)(n l2 / seg)."""
+    out = 1
+    for l in lengths:
+        out *= n * int(l) // seg
+    return out
+
+
+def solve_staged(solvers, f, out, reduce_sum=None):
+    """SR-FMG of one problem through the stage entry points.  solvers: the
+    handles this process drives (segment ranges of the same problem, or one
+    handle with all segments); f: each handle's copy of the whole right-hand
+    side (one tensor, or one per handle); out: the output tensor(s), each
+    handle writing its own segments' genuine cells.  reduce_sum(tensors)
+    sums the exchange arrays in place over all handles of the problem that
+    other processes drive (None: this process drives them all); the arrays
+    of the local handles are summed here first.  Every step of the solve
+    runs in the library; this loop only moves the two transition-level
+    arrays between handles (Sec. 4: the transition level is the one
+    exchange of the method)."""
+    solvers = list(solvers)
+    fs = f if isinstance(f, (list, tuple)) else [f] * len(solvers)
+    outs = out if isinstance(out, (list, tuple)) else [out] * len(solvers)
+    K = solvers[0].K
+    for k in range(1, K + 1):
+        for s, fk in zip(solvers, fs):
+            s.stage_down(fk, k)
+        bufs = [s.stage_buffers() for s in solvers]
+        exchange_sum(bufs, reduce_sum)
+        for s, fk, o in zip(solvers, fs, outs):
+            s.stage_up(fk, k, o)
+    return outs
+
+
+def exchange_sum(bufs, reduce_sum=None):
+    """bufs: per local handle, a tuple of arrays; afterwards every handle's
+    arrays hold the sum over all handles (the local ones, then reduce_sum
+    across processes).  Works on any torch tensors (CUDA or CPU).  Every
+    cell has one owner, so the sum is exact whatever its order."""
+    total = [t.clone() for t in bufs[0]]
+    for b in bufs[1:]:
+        for acc, x in zip(total, b):
+            acc.add_(x)
+    if reduce_sum is not None:
+        reduce_sum(total)
+    for b in bufs:
+        for dst, src in zip(b, total):
+            dst.copy_(src)
+    return total
 
 
 def _host_ptr(a, shape, name):
