@@ -319,6 +319,15 @@ long long sr_debug_live_bytes(void);
  */
 int sr_debug_last_stage_trim(sr_fmg_t h, int enable);
 
+/*
+ * Testing hook for the float64 -> float32 rounding the mixed mode's
+ * float64-arithmetic kernels store their results with (a round-to-nearest-
+ * even conversion on the integer pipe): out[i] = in[i] rounded, device
+ * arrays of n values; waits for stream.  Results must equal the IEEE 754
+ * conversion bit for bit.
+ */
+int sr_debug_narrow(const double* in, float* out, long long n, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* sr_fmg_status_string(int status);
 

@@ -89,6 +89,52 @@ __device__ __forceinline__ double widen(float x) {
 }
 __device__ __forceinline__ double widen(double x) { return x; }
 
+// double -> float rounded to nearest (ties to even), on the integer pipe
+// (the conversion instruction would take a float64-pipe slot, and the
+// float64-arithmetic kernels of the mixed mode are bound by that pipe).
+// Built from the IEEE 754 binary64 / binary32 formats: keep the leading 24
+// significant bits, round on the bits dropped, renormalise on a carry;
+// results below the smallest normal float become subnormal floats (rounded
+// the same way), results beyond the largest float become infinity, NaN
+// stays a (quiet) NaN.
+__device__ __forceinline__ float narrow(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long frac = b & 0xfffffffffffffull;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (frac ? 0x400000u : 0u));
+  if (e < 1023 - 150) return __uint_as_float(sign);  // below half the smallest subnormal
+  // significand with its leading one, and the number of low bits to drop:
+  // 29 for a normal float result, more for a subnormal one (exponent < -126)
+  const unsigned long long sig = frac | (1ull << 52);
+  const int fe = e - 1023 + 127;  // biased float exponent of a normal result
+  const int drop = fe >= 1 ? 29 : 29 + (1 - fe);
+  unsigned long long keep = sig >> drop;
+  const unsigned long long rest = sig & ((1ull << drop) - 1), half = 1ull << (drop - 1);
+  if (rest > half || (rest == half && (keep & 1ull))) ++keep;
+  if (fe >= 1) {
+    // keep holds 1.m (24 bits) or, after a carry, 2^24
+    int ex = fe;
+    if (keep >> 24) {
+      keep >>= 1;
+      ++ex;
+    }
+    if (ex >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)ex << 23) | ((unsigned)keep & 0x7fffffu));
+  }
+  // subnormal result (a carry into bit 23 gives the smallest normal, which
+  // the same bit pattern encodes)
+  return __uint_as_float(sign | (unsigned)keep);
+}
+
+// a float64 result stored in T: unchanged for double, narrow() for float
+__device__ __forceinline__ double store_as(double v, double*) { return v; }
+__device__ __forceinline__ float store_as(double v, float*) { return narrow(v); }
+template <typename T>
+__device__ __forceinline__ T stored(double v) {
+  return store_as(v, (T*)nullptr);
+}
+
 __device__ __forceinline__ void region_of(const BoxDesc& b, int which, int lo[3], int hi[3]) {
   const int* l = b.lo;
   const int* h = b.hi;
@@ -505,8 +551,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_coarse_rhs(LevelView C, LevelVi
     double v[6];
     neighbours<double>(u, c, B, C, q.x, q.y, q.z, uc, v);
     const double rh = inF ? widen(rho[c]) : k.zero;
-    rhs[c] = (T)fma6(cn, v, fma(c6, widen(uc), rh));
-    if (r) r[c] = (T)(cr * rh);
+    rhs[c] = stored<T>(fma6(cn, v, fma(c6, widen(uc), rh)));
+    if (r) r[c] = stored<T>(cr * rh);
   }
 }
 
@@ -535,8 +581,8 @@ __global__ void __launch_bounds__(kThreads) k_transition_rhs(LevelView C,
     neighbours<double>(t, c, B, C, q.x, q.y, q.z, tc, v);
     u[c] = tc;
     const double rh = widen(rho[c]);
-    rhs[c] = (T)fma6(cn, v, fma(c6, widen(tc), rh));
-    if (r) r[c] = (T)(cr * rh);
+    rhs[c] = stored<T>(fma6(cn, v, fma(c6, widen(tc), rh)));
+    if (r) r[c] = stored<T>(cr * rh);
   }
 }
 
@@ -560,7 +606,7 @@ __global__ void k_coarse_solve(LevelView L, const double* __restrict__ minv, Fie
   for (int o = 16; o > 0; o >>= 1) s = fma(__shfl_xor_sync(0xffffffffu, s, o), k.one, s);
   if (lane == 0) {
     const int x = warp % nx, y = (warp / nx) % ny, z = warp / (nx * ny);
-    u[at(B, x, y, z)] = (T)s;
+    u[at(B, x, y, z)] = stored<T>(s);
   }
 }
 
@@ -655,7 +701,7 @@ __global__ void __launch_bounds__(64) k_sep_inv_xy(LevelView L, const double* __
     const double tk = __shfl_sync(0xffffffffu, t, kx, W);
     if (q.lane < nx) o = fma(Px[kx * nx + q.lane], tk, o);
   }
-  if (live && q.lane < nx) u[at(B, q.lane, y, z)] = (T)o;
+  if (live && q.lane < nx) u[at(B, q.lane, y, z)] = stored<T>(o);
 }
 
 __device__ __forceinline__ bool not_finite(double v) {
@@ -707,7 +753,7 @@ __global__ void __launch_bounds__(kThreads) k_defect(Dims g, const double* __res
     const double fv = f[i];
     bad |= not_finite(fv);
     if (!u) {
-      d[i] = (float)fv;
+      d[i] = narrow(fv);
       continue;
     }
     int x, y, z;
@@ -721,7 +767,7 @@ __global__ void __launch_bounds__(kThreads) k_defect(Dims g, const double* __res
     v[3] = (y < g.y - 1) ? u[i + sy] : m;
     v[4] = (z > 0) ? u[i - sz] : m;
     v[5] = (z < g.z - 1) ? u[i + sz] : m;
-    d[i] = (float)fma6(cn, v, fma(c6, uc, fv));
+    d[i] = narrow(fma6(cn, v, fma(c6, uc, fv)));
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
 }
@@ -976,8 +1022,18 @@ __global__ void __launch_bounds__(kZThreads) k_gather_zm(LevelView L, const T* _
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_narrow(const double* __restrict__ in,
+                                                      float* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = narrow(in[i]);
+}
+
+// per-cell kernels: blocks of kThreads per box, each thread taking two cells
+// of the grid-stride loop (amortises the box descriptor fetch and the block
+// barrier; measured 1-8 % faster than one cell per thread)
 dim3 grid_for(const LevelView& L, int cells) {
-  int bx = (cells + kThreads - 1) / kThreads;
+  int bx = (cells + 2 * kThreads - 1) / (2 * kThreads);
   if (bx < 1) bx = 1;
   return dim3((unsigned)bx, (unsigned)L.nbox, 1);
 }
@@ -1204,6 +1260,11 @@ cudaError_t launch_accumulate(long long cells, const float* e, double* u, int ad
                               cudaStream_t s) {
   SRFMG_LAUNCH(pdl_launch(k_accumulate, flat_blocks(cells), kThreads, 0, s, cells, e, u, add,
                           fk<double>()));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_narrow(const double* in, float* out, long long n, cudaStream_t s) {
+  k_narrow<<<flat_blocks(n), kThreads, 0, s>>>(in, out, n);
   return cudaGetLastError();
 }
 

@@ -1168,6 +1168,8 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+bool dev_ok_any(const void* p) { return p && is_device_ptr(p); }
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -1576,6 +1578,14 @@ int sr_debug_fail_alloc(int nth) {
 }
 
 long long sr_debug_alloc_count(void) { return g_allocs.load(); }
+
+int sr_debug_narrow(const double* in, float* out, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!dev_ok_any(in) || !dev_ok_any(out)))) return SR_ERR_INVALID;
+  if (n == 0) return SR_OK;
+  CK(launch_narrow(in, out, n, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return SR_OK;
+}
 
 int sr_debug_last_stage_trim(sr_fmg_t h, int enable) {
   if (!h) return SR_ERR_INVALID;

@@ -238,6 +238,9 @@ cudaError_t launch_defect(Dims g, int n, const double* f, const double* u, float
 // Sets *status |= 1 if a value is not finite.
 cudaError_t launch_resid_norm(Dims g, int n, const double* f, const double* u,
                               unsigned long long* norm, unsigned int* status, cudaStream_t s);
+// out[i] = in[i] rounded to float by the solver's integer-pipe conversion
+// (the one its float64-arithmetic kernels store float32 results with).
+cudaError_t launch_narrow(const double* in, float* out, long long n, cudaStream_t s);
 // u = e (add == 0) or u += e (add == 1) on `cells` cells, e float32.
 cudaError_t launch_accumulate(long long cells, const float* e, double* u, int add,
                               cudaStream_t s);

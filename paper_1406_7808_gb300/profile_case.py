@@ -5,9 +5,10 @@ captures (ncu): each case runs a fixed, seeded workload once and exits.
       one Chebyshev degree-2 smoothing of a whole n^3 grid (two kernels:
       cheb_residual, cheb2_update)
   python -m paper_1406_7808_gb300.profile_case solve --n 256 [--plain] [--mixed] [--warmup 1]
-      warm-up solves then one solve of the benchmark configuration (SR,
-      32^3 segments, K = 3, J = 8; --plain without segments; --mixed in the
-      mixed-precision mode)
+          [--seg 32 --K 3 --A 11 --B 1 --n-coarse 16]
+      warm-up solves then one solve of an SR configuration (default: the
+      benchmark's segments, buffers and coarsest grid; --plain without
+      segments; --mixed in the mixed-precision mode)
   python -m paper_1406_7808_gb300.profile_case smooth27 --n 256
       one degree-2 smoothing with the 27-point operator ((14,3,1)/30) on the
       paper's domain [0,2]x[0,1]^2 with n cells per unit length (two
@@ -25,14 +26,20 @@ if ROOT not in sys.path:
 def main():
     import torch
 
-    from paper_1406_7808_gb300 import build, inputs, srfmg
+    from paper_1406_7808_gb300 import build, inputs, srfmg, workloads
 
+    sr = workloads.SR256
     p = argparse.ArgumentParser()
     p.add_argument("case", choices=["smooth", "solve", "smooth27"])
     p.add_argument("--n", type=int, default=256)
     p.add_argument("--plain", action="store_true")
     p.add_argument("--mixed", action="store_true")
     p.add_argument("--warmup", type=int, default=1)
+    p.add_argument("--seg", type=int, default=sr["seg"])
+    p.add_argument("--K", type=int, default=sr["K"])
+    p.add_argument("--A", type=int, default=sr["A"])
+    p.add_argument("--B", type=int, default=sr["B"])
+    p.add_argument("--n-coarse", type=int, default=sr["n_coarse"])
     a = p.parse_args()
     build.build()
     torch.cuda.set_device(0)
@@ -49,7 +56,9 @@ def main():
         u = torch.zeros_like(ft)
         srfmg.op_smooth(u, ft, 2)
     else:
-        kw = {} if a.plain else dict(seg=32, K=3, A=8, B=0)
+        kw = dict(n_coarse=a.n_coarse)
+        if not a.plain:
+            kw.update(seg=a.seg, K=a.K, A=a.A, B=a.B)
         if a.mixed:
             kw["mixed"] = True
         with srfmg.Solver(a.n, **kw) as s:

@@ -137,6 +137,7 @@ def load():
     lib.sr_debug_live_bytes.argtypes = []
     lib.sr_debug_live_bytes.restype = ctypes.c_longlong
     lib.sr_debug_last_stage_trim.argtypes = [_VP, ctypes.c_int]
+    lib.sr_debug_narrow.argtypes = [_VP, _VP, ctypes.c_longlong, _VP]
     lib.sr_fmg_stage_down.argtypes = [_VP, _VP, ctypes.c_int, _VP]
     lib.sr_fmg_stage_buffers.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                          ctypes.POINTER(ctypes.c_size_t)]
@@ -169,6 +170,16 @@ def debug_fail_alloc(nth):
     """Make the nth device allocation of the library from now fail as out of
     memory (0: off); for testing the error paths."""
     _check(load().sr_debug_fail_alloc(int(nth)), "sr_debug_fail_alloc")
+
+
+def debug_narrow(x):
+    """float64 CUDA tensor -> float32 through the library's integer-pipe
+    rounding (sr_debug_narrow)."""
+    import torch
+    out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    _check(load().sr_debug_narrow(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  x.numel(), _stream()), "sr_debug_narrow")
+    return out
 
 
 def debug_alloc_count():

@@ -14,8 +14,9 @@ PLAIN256 = dict(n=256, n_coarse=16)
 # there FMG leaves about 10 e_disc of algebraic error in the smoothest mode
 SR256_DEPTH2 = dict(n=256, seg=32, K=3, A=8, B=0)
 PLAIN256_DEPTH2 = dict(n=256)
-# mixed-precision SR-FMG: 512^3 cells, 512 segments of 64^3, K = 4, J = 8
-MIXED512 = dict(n=512, seg=64, K=4, A=8, B=0, mixed=True, n_outer=2)
+# mixed-precision SR-FMG: 512^3 cells, 512 segments of 64^3, K = 4, J = 8,
+# coarsest grid 16^3 solved exactly (float64 arithmetic)
+MIXED512 = dict(n=512, seg=64, K=4, A=8, B=0, mixed=True, n_outer=2, n_coarse=16)
 
 # batched: 16 right-hand sides each of 64^3, 128^3, 192^3, 256^3 cells,
 # mixed precision, manufactured f with seeds 100 + i

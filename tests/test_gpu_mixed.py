@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import exact
-from paper_1406_7808_gb300 import inputs
+from paper_1406_7808_gb300 import inputs, workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -57,14 +57,18 @@ def test_mixed_against_float64_defect_correction(gpu, oracle_mod, n, kw):
 
 
 def test_mixed_full_size_512(gpu, oracle_mod):
-    """The mixed-precision configuration: 512^3, 64^3-cell segments, K = 4."""
+    """The benchmark's mixed-precision configuration, in its launch
+    configuration (graph mode): 512^3, 64^3-cell segments, K = 4, coarsest
+    grid 16^3; and the same segments at the paper's depth (2^3)."""
     n = 512
-    kw = dict(seg=64, K=4, A=8, B=0)
     f, uex = inputs.manufactured(n, 1)
-    u = gpu_solve(gpu, f, mixed=True, n_outer=2, **kw)
-    ref = oracle_mod.solve_refined(f, 2, **kw)
     e_disc = exact.e_disc_main(n)  # the main mode dominates u; closed form
-    assert np.abs(u - ref).max() <= 0.1 * e_disc
+    for kw in (workloads.config(workloads.MIXED512), dict(seg=64, K=4, A=8, B=0, n_outer=2)):
+        kw = {k: v for k, v in kw.items() if k != "mixed"}
+        u = gpu_solve(gpu, f, mixed=True, graph=True, **kw)
+        okw = {k: v for k, v in kw.items() if k != "n_outer"}
+        ref = oracle_mod.solve_refined(f, kw["n_outer"], **okw)
+        assert np.abs(u - ref).max() <= 0.1 * e_disc
 
 
 def test_more_passes_approach_the_discrete_solution(gpu):
@@ -85,3 +89,34 @@ def test_mixed_nonfinite_rhs(gpu):
         with pytest.raises(gpu.SRFMGError) as e:
             s.solve(T(f))
         assert e.value.status == gpu.SR_ERR_NONFINITE
+
+
+def test_integer_pipe_rounding_matches_ieee(gpu):
+    """The mixed mode's float64-arithmetic kernels store float32 results
+    through an integer-pipe round-to-nearest-even conversion; it must equal
+    the IEEE 754 conversion (torch's .float() on the device) bit for bit, on
+    every exponent range: normal, the float subnormal range, ties, carries
+    into the exponent, overflow, zeros, infinities (NaN stays NaN)."""
+    import torch
+    rng = np.random.default_rng(11)
+    parts = [
+        rng.standard_normal(200000) * 10.0 ** rng.uniform(-45, 39, 200000),
+        rng.uniform(-1, 1, 50000) * 2.0 ** -126,                      # float subnormal range
+        rng.uniform(-1, 1, 50000) * 2.0 ** -149,                      # around the smallest one
+    ]
+    # exact ties and near-ties of the 29 dropped bits, and carries into the exponent
+    mant = rng.integers(0, 1 << 23, 20000, dtype=np.int64)
+    ex = rng.integers(-140, 120, 20000)
+    tie = (mant.astype(np.float64) * 2 + 1) * 2.0 ** (ex.astype(np.float64) - 24)
+    parts += [tie, np.nextafter(tie, np.inf), np.nextafter(tie, -np.inf)]
+    specials = [0.0, -0.0, np.inf, -np.inf, 3.4028234663852886e38, 3.4028235677973366e38,
+                3.402823669209385e38, 1.1754943508222875e-38, 1.1754942807573643e-38,
+                1.401298464324817e-45, 7.006492321624085e-46, 7.006492321624087e-46,
+                2.8e-45, 1e-320, -1e-320, 1.0 - 2.0 ** -25, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24]
+    x = torch.from_numpy(np.concatenate(parts + [np.array(specials)])).cuda()
+    got = gpu.debug_narrow(x)
+    ref = x.float()
+    assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
+    nan = gpu.debug_narrow(torch.tensor([float("nan"), -float("nan")], dtype=torch.float64,
+                                        device="cuda"))
+    assert torch.isnan(nan).all()
