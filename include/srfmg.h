@@ -64,8 +64,8 @@ typedef struct sr_fmg_s* sr_fmg_t;
 /*
  * Solver configuration.  sr_fmg_default_config fills it for a given n.
  *   n         fine cells per unit length (h = 1/n); the fine grid has
- *             n len[0] x n len[1] x n len[2] cells.  n must halve down to
- *             the coarsest grid.
+ *             n len[0] x n len[1] x n len[2] cells, fewer than 2^31.  n must
+ *             halve down to the coarsest grid.
  *   n_coarse  cells per unit length of the coarsest grid, solved exactly
  *             (Sec. 3.1, the "else" branch of FASMGV); 0 = keep halving until
  *             2 or 3 remain.  At most 16.  Grids of up to 512 cells use a

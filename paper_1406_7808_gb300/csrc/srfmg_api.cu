@@ -353,8 +353,10 @@ int check_config(const sr_fmg_config* c) {
   if (lengths_of(c, len) || op_weights(c, &w, &lmax)) return SR_ERR_INVALID;
   if (c->stencil == 27 && c->precision != SR_FP64) return SR_ERR_INVALID;
   {
+    // the kernels index the cells of a box (up to the whole finest grid)
+    // with 32-bit integers
     const long long cells = (long long)c->n * c->n * c->n * len[0] * len[1] * len[2];
-    if (c->n > 0 && cells > (1LL << 34)) return SR_ERR_UNSUPPORTED_SIZE;
+    if (c->n > 0 && cells >= (1LL << 31)) return SR_ERR_UNSUPPORTED_SIZE;
   }
   if (c->precision == SR_MIXED && (c->n_outer < 0 || c->n_outer > 16)) return SR_ERR_INVALID;
   if (c->alpha < 0 || c->nu1 < 0 || c->nu2 < 0 || c->alpha > 16 || c->nu1 > 16 || c->nu2 > 16)

@@ -80,6 +80,7 @@ def _create(lib, **kw):
     (dict(n=20), -2),                                   # 20 -> 10 -> 5 never reaches 2 or 3
     (dict(n=64, n_coarse=5), -2),
     (dict(n=64, n_coarse=32), -2),                      # coarsest grid larger than supported
+    (dict(n=1024, len=(2, 1, 1)), -2),                  # 2^31 cells: beyond 32-bit cell indices
     (dict(n=64, n_coarse=16, len=(4, 1, 1)), -2),       # 64 x 16 x 16 coarsest cells: too many
     (dict(n=64, seg=24, K=2), -1),                      # seg does not divide n
     (dict(n=64, seg=16, K=5), -1),                      # seg not divisible by 2^K
