@@ -320,6 +320,29 @@ long long sr_debug_live_bytes(void);
 int sr_debug_last_stage_trim(sr_fmg_t h, int enable);
 
 /*
+ * Segment-resident legs (the float32 inner solver of SR_MIXED, 7-point,
+ * degree-2 smoothers): on every SR level below a stage's top level whose
+ * boxes fit, the down-leg (coarse right-hand side, pre-smoother, residual and
+ * restriction) and the up-leg (correction, post-smoother, w - t) of each
+ * segment run as one launch of a thread-block cluster per segment that
+ * holds the segment's box in shared memory (Sec. 4; the near-memory
+ * residency of a segment, Sec. 6), with the same results bit for bit as the
+ * separate kernels.  sr_debug_segment_legs(h, 1, ...) runs the legs;
+ * 0 (the default) the separate kernels, which are faster on GB300 (the
+ * mixed 512^3 solve: 24.2 ms against 30 to 32 ms with the legs).  *levels (may
+ * be NULL) receives a bit mask of the SR levels j (bit j) that have a leg.
+ * Drops the handle's captured graphs.
+ *
+ * sr_debug_force_wait_timeout(h, 1) makes every bounded device-side wait of
+ * the legs (when they run) expect data that never arrives, so each wait
+ * runs out (after about a second) and the solve reports SR_ERR_TIMEOUT; 0
+ * turns it off.
+ * For testing that path: nothing faults or hangs, the handle stays usable.
+ */
+int sr_debug_segment_legs(sr_fmg_t h, int enable, int* levels);
+int sr_debug_force_wait_timeout(sr_fmg_t h, int enable);
+
+/*
  * Testing hook for the float64 -> float32 rounding the mixed mode's
  * float64-arithmetic kernels store their results with (a round-to-nearest-
  * even conversion on the integer pipe): out[i] = in[i] rounded, device

@@ -93,7 +93,7 @@ enum Kind {
   kChebResidualF32, kCheb2UpdateF32, kChebStepF32, kResidRestrictF32, kCoarseRhsMixed,
   kTransitionRhsMixed, kProlongSetF32, kProlongAddF32, kCoarseSolveMixed, kRestrictFF32,
   kGatherMixed, kDefect, kAccumulate, kDiff, kDiffF32, kResidNorm, kShellCopy, kShellCopyF32,
-  kKinds
+  kLegDownF32, kLegUpF32, kKinds
 };
 const char* const kKindName[kKinds] = {
   "cheb_residual", "cheb2_update", "cheb_step", "resid_restrict", "coarse_rhs",
@@ -102,7 +102,8 @@ const char* const kKindName[kKinds] = {
   "cheb_residual_f32", "cheb2_update_f32", "cheb_step_f32", "resid_restrict_f32",
   "coarse_rhs_mixed", "transition_rhs_mixed", "prolong_f32", "prolong_correct_f32",
   "coarse_solve_mixed", "restrict_f_f32", "gather_genuine_mixed", "defect", "accumulate",
-  "correction", "correction_f32", "resid_norm", "shell_copy", "shell_copy_f32"};
+  "correction", "correction_f32", "resid_norm", "shell_copy", "shell_copy_f32",
+  "leg_down_f32", "leg_up_f32"};
 
 // kind of a kernel for storage type T: float64 kinds shift to their float32
 // counterparts (same order)
@@ -220,6 +221,16 @@ struct sr_fmg_s {
   int launches = 0;                // kernel launches queued by the last solve
   bool trim = true;                // last-stage trimming (sr_debug_last_stage_trim)
   bool sharded = false;            // the handle owns a range of the segments only
+  // segment-resident legs of the float32 SR levels j < K (segment_leg.cu):
+  // cluster size, planes per CTA and shared memory per level; C = 0: the
+  // level runs the separate kernels
+  struct Leg {
+    int C = 0, max_planes = 0;
+    size_t smem = 0;
+  };
+  std::vector<Leg> legs;
+  bool legs_on = false;            // sr_debug_segment_legs (measured slower: off)
+  int force_timeout = 0;           // sr_debug_force_wait_timeout
   Profile prof;
 
   Hier<double>& hier(double*) { return h64; }
@@ -765,6 +776,50 @@ int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
   return SR_OK;
 }
 
+// Segment-resident legs for the float32 SR levels j = 1 .. K-1 (the
+// levels below a stage's top): a level qualifies when its boxes' stored
+// planes can be split over a cluster of at most 16 CTAs whose shared memory
+// holds two arrays of a slab, when every box row and plane keeps the
+// 16-byte alignment of the bulk copies, and the operator, smoothers and
+// precision are those the fused legs implement (7-point, degree-2 pre- and
+// post-smoother, float32).
+int plan_legs(sr_fmg_s* h) {
+  h->legs.assign(h->K + 1, sr_fmg_s::Leg{});
+  if (!h->mixed || h->op27 || h->pre.nu != 2 || h->post.nu != 2 || h->K < 2) return SR_OK;
+  constexpr size_t kMaxSmem = 232448 - 1024;  // dynamic shared memory per CTA on sm_103a
+  if (leg_prepare(kMaxSmem) != cudaSuccess) {
+    cudaGetLastError();
+    return SR_OK;  // no fused legs on this device
+  }
+  for (int j = 1; j < h->K; ++j) {
+    const Level<float>& L = h->h32.slev[j];
+    int e0 = 0, e1 = 0, e2 = 0;
+    bool aligned = L.slot % 4 == 0 && L.nbox <= 65535;
+    for (const BoxDesc& b : L.hboxes) {
+      const int a0 = b.hi[0] - b.lo[0] + 2, a1 = b.hi[1] - b.lo[1] + 2, a2 = b.hi[2] - b.lo[2] + 2;
+      aligned = aligned && (a0 * a1) % 4 == 0 && b.base % 4 == 0;
+      e0 = std::max(e0, a0);
+      e1 = std::max(e1, a1);
+      e2 = std::max(e2, a2);
+    }
+    if (!aligned) continue;
+    sr_fmg_s::Leg best;
+    for (size_t cap : {(size_t)113 * 1024, kMaxSmem}) {  // two CTAs per SM if possible
+      for (int C = 1; C <= 16 && !best.C; C *= 2) {
+        const int planes = (e2 + C - 1) / C;
+        const size_t smem = leg_smem_bytes(e0, e1, planes);
+        if (planes < 1 || smem > cap || leg_max_clusters(C, smem) < 1) continue;
+        best.C = C;
+        best.max_planes = planes;
+        best.smem = smem;
+      }
+      if (best.C) break;
+    }
+    h->legs[j] = best;
+  }
+  return SR_OK;
+}
+
 // ---------------------------------------------------------------------------
 // launch sequence, for storage type T
 
@@ -991,6 +1046,22 @@ int f_hierarchy(sr_fmg_s* h, Hier<T>& H, const T* f, int check, cudaStream_t s) 
   return SR_OK;
 }
 
+// level j (below stage k's top) runs as a segment-resident leg in this solve
+template <typename T>
+bool leg_on(const sr_fmg_s* h, int j, int k) {
+  if constexpr (sizeof(T) == 4) {
+    return h->legs_on && j >= 1 && j < k && j < (int)h->legs.size() && h->legs[j].C > 0;
+  }
+  return false;
+}
+
+// algorithmic counts of a leg per compute cell: floating-point operations
+// (smoother 14, restriction 42 per coarse cell / prolongation about 3.75,
+// correction 1) and bytes (down: u read and written, rhs, the coarse uhat
+// and rho; up: u read and written, rhs, t, e, the coarse e)
+constexpr double kLegDownOps = 14.0 + 42.0 / 8, kLegDownBytes = 12.0 + 1.0;
+constexpr double kLegUpOps = 14.0 + 3.75 + 1.0, kLegUpBytes = 20.0 + 0.5;
+
 // SR stage k, first half: the FMG prolongation onto level k and S^alpha,
 // then the down-leg of FASMGVSR(k) to the transition level, where every
 // segment owner-writes its genuine level-0 cells of \hat I u_1 (into t_0) and
@@ -1016,16 +1087,30 @@ int sr_stage_down(sr_fmg_s* h, Hier<T>& H, const T* f, int k, cudaStream_t s) {
   // FASMGVSR(k): down-leg
   for (int j = k; j >= 1; --j) {
     Level<T>& Lj = H.slev[j];
-    const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
-    // at the stage's top level the first residual may come from the fused
-    // FMG step; below it, with the level's right-hand side (float64)
-    const T* rf = (j == k) ? r_first : (kFirstResidual<T> ? Lj.r : nullptr);
-    int rc = smooth(h, Lj, h->pre, Lj.u, rhs, s, rf);
-    if (rc) return rc;
-    if (j > 1) {
-      Level<T>& C = H.slev[j - 1];
-      rc = resid_restrict<T>(h, Lj, Lj.u, rhs, C, C.u, C.rho, s);
+    Level<T>& C = (j > 1) ? H.slev[j - 1] : L0;
+    T* uhat = (j > 1) ? C.u : L0.t;  // the transition level owner-writes into t_0
+    bool leg = false;
+    if constexpr (sizeof(T) == 4) leg = leg_on<T>(h, j, k);
+    if (leg) {
+      // the pre-smoother and the restriction of level j in one cluster launch
+      // per segment box (float32 only)
+      if constexpr (sizeof(T) == 4) {
+        const sr_fmg_s::Leg& g = h->legs[j];
+        LAUNCH(h, kLegDownF32, Lj.tot_cells, kLegDownOps, kLegDownBytes, s,
+               launch_leg_down(Lj.view, C.view, Lj.u, Lj.rhs, uhat, C.rho, h->pre.a, h->pre.b,
+                               g.C, g.max_planes, g.smem, h->status, h->force_timeout, s));
+      }
+    } else {
+      const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
+      // at the stage's top level the first residual may come from the fused
+      // FMG step; below it, with the level's right-hand side (float64)
+      const T* rf = (j == k) ? r_first : (kFirstResidual<T> ? Lj.r : nullptr);
+      int rc = smooth(h, Lj, h->pre, Lj.u, rhs, s, rf);
       if (rc) return rc;
+      rc = resid_restrict<T>(h, Lj, Lj.u, rhs, C, uhat, C.rho, s);
+      if (rc) return rc;
+    }
+    if (j > 1) {
       const bool cr = kFirstResidual<T>;
       LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h) + (cr ? 1 : 0), (cr ? 5 : 4) * w,
              s,
@@ -1033,9 +1118,6 @@ int sr_stage_down(sr_fmg_s* h, Hier<T>& H, const T* f, int k, cudaStream_t s) {
       if (!h->op27)
         LAUNCH(h, kind_of<T>(kShellCopy), C.tot_cells / 4, 0, 2 * w, s,
                launch_shell_copy<T>(C.view, C.u, C.t, s));
-    } else {
-      rc = resid_restrict<T>(h, Lj, Lj.u, rhs, L0, L0.t, L0.rho, s);
-      if (rc) return rc;
     }
   }
   return SR_OK;
@@ -1062,6 +1144,45 @@ int sr_stage_up(sr_fmg_s* h, Hier<T>& H, const T* f, int k, cudaStream_t s) {
   for (int j = 1; j <= k; ++j) {
     Level<T>& Lj = H.slev[j];
     const Level<T>& C = (j == 1) ? L0 : H.slev[j - 1];
+    if constexpr (sizeof(T) == 4) {
+      // level j-1's leg has formed e_{j-1} = w - t already
+      const bool have_e = j > 1 && leg_on<T>(h, j - 1, k);
+      if (leg_on<T>(h, j, k)) {
+        if (!have_e)
+          LAUNCH(h, kind_of<T>(kDiff), C.tot_cells, 1, 3 * w, s,
+                 launch_diff<T>(C.view, C.u, C.t, C.rho, s));
+        // correction, post-smoother and level j's own w - t in one cluster
+        // launch per segment box
+        const sr_fmg_s::Leg& g = h->legs[j];
+        LAUNCH(h, kLegUpF32, Lj.tot_cells, kLegUpOps, kLegUpBytes, s,
+               launch_leg_up(Lj.view, C.view, Lj.u, Lj.t, Lj.rhs, C.rho, Lj.rho, h->post.a,
+                             h->post.b, g.C, g.max_planes, g.smem, h->status, h->force_timeout,
+                             s));
+        continue;
+      }
+      if (have_e) {
+        // the correction onto level j (a separate-kernel level) from the
+        // leg's e_{j-1}
+        const FieldT<T> rhs = (j == k) ? fview(k) : view_boxes<T>(Lj, Lj.rhs);
+        const bool last = k == K && h->post.nu == 2 && h->trim;
+        if (last) {
+          const Geom& TR = (j == K) ? H.trim_r : H.ctrim_r[j];
+          const Geom& TU = (j == K) ? H.trim_u : H.ctrim_u[j];
+          LAUNCH(h, kind_of<T>(kProlongAdd), TR.tot_prolong, 3.75, 2.125 * w, s,
+                 launch_prolong<T>(C.view, C.rho, TR.view, Lj.u, 1, s));
+          LAUNCH(h, kind_of<T>(kChebResidual), TR.tot_cells, ops_smooth(h), 3 * w, s,
+                 op_cheb_residual<T>(h, TR.view, Lj.u, Lj.r, rhs, s));
+          LAUNCH(h, kind_of<T>(kCheb2Update), TU.tot_cells, ops_smooth(h), 3 * w, s,
+                 op_cheb2_update<T>(h, TU.view, Lj.u, Lj.r, h->post, s));
+          continue;
+        }
+        LAUNCH(h, kind_of<T>(kProlongAdd), Lj.tot_prolong, 3.75, 2.125 * w, s,
+               launch_prolong<T>(C.view, C.rho, Lj.view, Lj.u, 1, s));
+        rc = smooth(h, Lj, h->post, Lj.u, rhs, s);
+        if (rc) return rc;
+        continue;
+      }
+    }
     // The solve's last operations: only the finest level's genuine cells
     // are returned.  After its correction they depend on u within two
     // cells and on r within one cell of them; the correction reads the
@@ -1312,6 +1433,7 @@ int sr_fmg_create(sr_fmg_t* out, const sr_fmg_config* cfg) {
     if (!rc) rc = dalloc(h, &h->defect, cells);
     if (!rc) rc = build_global_levels<float>(h, h->h32, cfg->n >> h->K, false);
     if (!rc && h->K) rc = build_sr_levels<float>(h, h->h32);
+    if (!rc && h->K) rc = plan_legs(h);
   }
   if (rc) {
     free_all(h);
@@ -1586,6 +1708,29 @@ int sr_debug_narrow(const double* in, float* out, long long n, void* stream) {
   if (n == 0) return SR_OK;
   CK(launch_narrow(in, out, n, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return SR_OK;
+}
+
+int sr_debug_segment_legs(sr_fmg_t h, int enable, int* levels) {
+  if (!h) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  for (const sr_fmg_s::GraphEntry& e : h->graphs) sr_fmg_batch_destroy(e.b);
+  h->graphs.clear();
+  h->legs_on = enable != 0;
+  if (levels) {
+    *levels = 0;
+    for (size_t j = 1; j < h->legs.size(); ++j)
+      if (h->legs[j].C > 0) *levels |= 1 << j;
+  }
+  return SR_OK;
+}
+
+int sr_debug_force_wait_timeout(sr_fmg_t h, int enable) {
+  if (!h) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  for (const sr_fmg_s::GraphEntry& e : h->graphs) sr_fmg_batch_destroy(e.b);
+  h->graphs.clear();
+  h->force_timeout = enable != 0;
   return SR_OK;
 }
 

@@ -281,6 +281,27 @@ cudaError_t launch27_resid_norm(const LevelView& L, const double* f, const doubl
                                 unsigned long long* norm, unsigned int* status, W27 w,
                                 cudaStream_t s);
 
+// ---- segment-resident legs of the float32 SR V-cycle (segment_leg.cu): one
+// thread-block cluster of C CTAs per segment box of level L, the box's
+// stored planes split into z-slabs of at most max_planes planes whose u and
+// smoother residual are held in shared memory (smem bytes, leg_smem_bytes).
+// down: the degree-2 pre-smoother (a, b) with the level's right-hand side
+// rhs, then residual + restriction into uhat_dst / rho_dst of Cv.
+cudaError_t launch_leg_down(const LevelView& L, const LevelView& Cv, float* u, const float* rhs,
+                            float* uhat_dst, float* rho_dst, double a, double b, int C,
+                            int max_planes, size_t smem, unsigned* status, int force_timeout,
+                            cudaStream_t s);
+// up: u += P ec (ec on Cv), the degree-2 post-smoother (a, b), e_out = u - t.
+cudaError_t launch_leg_up(const LevelView& L, const LevelView& Cv, float* u, const float* t,
+                          const float* rhs, const float* ec, float* e_out, double a, double b,
+                          int C, int max_planes, size_t smem, unsigned* status,
+                          int force_timeout, cudaStream_t s);
+size_t leg_smem_bytes(int e0, int e1, int planes);
+// clusters of C CTAs with smem bytes each that fit on the device at once
+int leg_max_clusters(int C, size_t smem);
+// allow smem bytes of dynamic shared memory for the leg kernels
+cudaError_t leg_prepare(size_t smem);
+
 // Queue one solve of handle h on stream without validating the pointers
 // (the batch path validates them before stream capture); srfmg_api.cu.
 int enqueue_solve_unchecked(::sr_fmg_s* h, const double* f, double* u, cudaStream_t s);

@@ -138,6 +138,8 @@ def load():
     lib.sr_debug_live_bytes.restype = ctypes.c_longlong
     lib.sr_debug_last_stage_trim.argtypes = [_VP, ctypes.c_int]
     lib.sr_debug_narrow.argtypes = [_VP, _VP, ctypes.c_longlong, _VP]
+    lib.sr_debug_segment_legs.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.sr_debug_force_wait_timeout.argtypes = [_VP, ctypes.c_int]
     lib.sr_fmg_stage_down.argtypes = [_VP, _VP, ctypes.c_int, _VP]
     lib.sr_fmg_stage_buffers.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                          ctypes.POINTER(ctypes.c_size_t)]
@@ -338,6 +340,20 @@ class Solver:
                                       _dev(out, self.shape, "out"), _stream()),
                "sr_fmg_stage_up")
         return out
+
+    def debug_segment_legs(self, enable):
+        """Segment-resident legs on or off (default: off, the separate kernels
+        are faster on GB300); returns the levels that have one (a list of j)."""
+        levels = ctypes.c_int(0)
+        _check(load().sr_debug_segment_legs(self._h, int(bool(enable)), ctypes.byref(levels)),
+               "sr_debug_segment_legs")
+        return [j for j in range(1, 31) if levels.value >> j & 1]
+
+    def debug_force_wait_timeout(self, enable):
+        """Make the legs' bounded waits run out (the solve reports
+        SR_ERR_TIMEOUT); for testing."""
+        _check(load().sr_debug_force_wait_timeout(self._h, int(bool(enable))),
+               "sr_debug_force_wait_timeout")
 
     def debug_last_stage_trim(self, enable):
         """Turn the last stage's trimming on (default) or off (same result)."""
