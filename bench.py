@@ -735,8 +735,9 @@ def measure_adjoint(args, timed_fn, world, rank):
 
 def measure_batch(args, timed_fn, world):
     """64 right-hand sides (16 each of 64^3, 128^3, 192^3, 256^3), mixed
-    precision, one CUDA graph launch per batch, autotuned segment shapes and
-    graph branches."""
+    precision, one CUDA graph launch per batch, the deepest exact coarsest
+    grid each size allows, autotuned segment shapes, launch shapes and graph
+    branches."""
     import torch
     from paper_1406_7808_gb300 import autotune, inputs, srfmg, workloads
     problems = workloads.batch_problems()
@@ -759,8 +760,14 @@ def measure_batch(args, timed_fn, world):
     return {"problems": len(problems), "sizes": list(workloads.BATCH_SIZES),
             "dof_per_batch": dof, "ms_per_batch": ms, "dof_s": world * dof / (ms / 1e3),
             "graph_branches": branches, "timed_batches": steps,
-            "segment_choice": {str(n): {k: v for k, v in c[0].items() if k in ("seg", "K")}
-                               for n, c in choices.items()}}
+            "choice": {str(n): {"seg": c[0].get("seg"), "K": c[0].get("K"),
+                                "n_coarse": c[0].get("n_coarse"), "zchunk": c[2][0],
+                                "cells_per_thread": c[2][1],
+                                "segment_table": [[t[0], round(t[1], 3), round(t[2], 3)]
+                                                  for t in c[1]],
+                                "shape_ms": {f"{z},{p}": round(v, 3)
+                                             for (z, p), v in c[3].items()}}
+                       for n, c in choices.items()}}
 
 
 class _Null:

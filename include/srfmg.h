@@ -255,6 +255,18 @@ int sr_fmg_stage_down(sr_fmg_t h, const double* f_dev, int k, void* stream);
 int sr_fmg_stage_buffers(sr_fmg_t h, double** uhat0, double** rho0, size_t* count);
 int sr_fmg_stage_up(sr_fmg_t h, const double* f_dev, int k, double* u_dev, void* stream);
 
+/*
+ * Launch shape of the handle's kernels (results do not depend on it, bit
+ * for bit): zchunk = cells in z that a thread of the z-column kernels walks
+ * (1..256, default 16), cells_per_thread = cells a thread of the per-cell
+ * kernels takes (1..16, default 2).  Drops the handle's captured graphs;
+ * batches holding the handle re-capture theirs at their next solve.  The
+ * batch autotuner (paper_1406_7808_gb300/autotune.py) picks both per grid
+ * size by timing.  The paper has no counterpart.
+ */
+int sr_fmg_set_launch_shape(sr_fmg_t h, int zchunk, int cells_per_thread);
+int sr_fmg_launch_shape(sr_fmg_t h, int* zchunk, int* cells_per_thread);
+
 /* Number of kernel launches the handle's last queued solve made. */
 int sr_fmg_launches_per_solve(sr_fmg_t h, int* launches);
 

@@ -197,12 +197,13 @@ __device__ __forceinline__ Cell cell_of(int i, const int lo[3], int ex, int ey) 
 // neighbours)/6 and u += a r + b (sum of the neighbours of r), in column
 // (z-marching) form: the threads of a block take consecutive cells of the
 // box's flattened (x, y) plane (so warps stay full whatever the box width),
-// and each thread walks a chunk of kZChunk cells in z, carrying the
+// and each thread walks a chunk of L.zchunk cells in z, carrying the
 // z-neighbours in registers.  blockIdx.x enumerates (plane block, z chunk).
-constexpr int kZThreads = 256, kZChunk = 16;
+constexpr int kZThreads = 256;
 
 struct ZTiles {
   int nplane, nzc;  // plane blocks, z chunks
+  int zc;           // cells per z chunk
 };
 
 __device__ __forceinline__ bool ztile(const BoxDesc& B, ZTiles t, int& x, int& y, int& z0,
@@ -213,8 +214,8 @@ __device__ __forceinline__ bool ztile(const BoxDesc& B, ZTiles t, int& x, int& y
   const int iy = i / ex;
   x = B.lo[0] + (i - iy * ex);
   y = B.lo[1] + iy;
-  z0 = B.lo[2] + tz * kZChunk;
-  z1 = min(z0 + kZChunk, B.hi[2]);
+  z0 = B.lo[2] + tz * t.zc;
+  z1 = min(z0 + t.zc, B.hi[2]);
   return iy < ey && z0 < z1;
 }
 
@@ -832,14 +833,14 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(long long cells, const 
 
 // ---------------------------------------------------------------------------
 // The transfer and pointwise passes walk z-columns: a thread owns an (x, y)
-// of the region and kZChunk cells in z, which keeps many independent loads
+// of the region and zc cells in z, which keeps many independent loads
 // in flight per thread (these passes are memory- or latency-bound in both
 // precisions) and amortises the index arithmetic.
 
 // region [lo, hi) of box B as z-columns: thread -> (x, y) of the flattened
 // region plane, blockIdx.x -> (plane block, z chunk)
-__device__ __forceinline__ bool zcolumn(const int lo[3], const int hi[3], int nplane, int& x,
-                                        int& y, int& z0, int& z1) {
+__device__ __forceinline__ bool zcolumn(const int lo[3], const int hi[3], int nplane, int zc,
+                                        int& x, int& y, int& z0, int& z1) {
   const int tz = blockIdx.x / nplane, pb = blockIdx.x - tz * nplane;
   const int ex = hi[0] - lo[0], ey = hi[1] - lo[1];
   if (ex <= 0 || ey <= 0) return false;
@@ -847,13 +848,13 @@ __device__ __forceinline__ bool zcolumn(const int lo[3], const int hi[3], int np
   const int iy = i / ex;
   x = lo[0] + (i - iy * ex);
   y = lo[1] + iy;
-  z0 = lo[2] + tz * kZChunk;
-  z1 = min(z0 + kZChunk, hi[2]);
+  z0 = lo[2] + tz * zc;
+  z1 = min(z0 + zc, hi[2]);
   return iy < ey && z0 < z1;
 }
 
 // trilinear prolongation in fine z-columns: a thread owns a fine (x, y) of
-// the box's prolongation range and walks kZChunk fine cells in z.  Its two
+// the box's prolongation range and walks F.zchunk fine cells in z.  Its two
 // coarse columns per dimension are the fine cell's own coarse cell and the
 // neighbour on its side (mirrored with a sign flip outside the domain); for
 // every coarse plane it meets it forms the bilinear (x, y) value once
@@ -875,7 +876,7 @@ __global__ void __launch_bounds__(kZThreads, 6) k_prolong_zcol(LevelView C, cons
   int lo[3], hi[3];
   region_of(B, kProlong, lo, hi);
   int x, y, z0, z1;
-  if (!zcolumn(lo, hi, nplane, x, y, z0, z1)) return;
+  if (!zcolumn(lo, hi, nplane, F.zchunk, x, y, z0, z1)) return;
   // coarse columns and their offsets within the coarse box
   const int X0 = x >> 1, Y0 = y >> 1;
   int Xo = (x & 1) ? X0 + 1 : X0 - 1, Yo = (y & 1) ? Y0 + 1 : Y0 - 1;
@@ -925,7 +926,7 @@ __global__ void __launch_bounds__(kZThreads, 8) k_cheb_step_zm(LevelView L, T* _
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
   int x, y, z0, z1;
-  if (!zcolumn(B.lo, B.hi, nplane, x, y, z0, z1)) return;
+  if (!zcolumn(B.lo, B.hi, nplane, L.zchunk, x, y, z0, z1)) return;
   const bool use_d = alpha != T(0);
   long long c = at(B, x, y, z0);
 #pragma unroll 4
@@ -962,7 +963,7 @@ __global__ void __launch_bounds__(kZThreads, 8) k_diff_zm(LevelView C, const T* 
     }
   }
   int x, y, z0, z1;
-  if (!zcolumn(lo, hi, nplane, x, y, z0, z1)) return;
+  if (!zcolumn(lo, hi, nplane, C.zchunk, x, y, z0, z1)) return;
   long long c = at(B, x, y, z0);
 #pragma unroll 4
   for (int z = z0; z < z1; ++z, c += B.sz) e[c] = fma(t[c], mone, u[c]);
@@ -987,7 +988,7 @@ __global__ void __launch_bounds__(kZThreads) k_shell_copy(LevelView C, const T* 
     hi[d] = min(B.hi[d] + 1, nd[d]);
   }
   int x, y, z0, z1;
-  if (!zcolumn(lo, hi, nplane, x, y, z0, z1)) return;
+  if (!zcolumn(lo, hi, nplane, C.zchunk, x, y, z0, z1)) return;
   const bool ring = x < B.lo[0] || x >= B.hi[0] || y < B.lo[1] || y >= B.hi[1];
   if (!ring) {  // only the cells outside the compute region in z
     if (z0 >= B.lo[2]) z0 = max(z0, B.hi[2]);
@@ -1011,7 +1012,7 @@ __global__ void __launch_bounds__(kZThreads) k_gather_zm(LevelView L, const T* _
   if (threadIdx.x == 0) B = L.boxes[blockIdx.y];
   __syncthreads();
   int x, y, z0, z1;
-  if (!zcolumn(B.glo, B.ghi, nplane, x, y, z0, z1)) return;
+  if (!zcolumn(B.glo, B.ghi, nplane, L.zchunk, x, y, z0, z1)) return;
   const long long pz = (long long)L.nx * L.ny;
   long long c = at(B, x, y, z0);
   long long o = (long long)z0 * pz + (long long)y * L.nx + x;
@@ -1029,11 +1030,12 @@ __global__ void __launch_bounds__(kThreads) k_narrow(const double* __restrict__ 
     out[i] = narrow(in[i]);
 }
 
-// per-cell kernels: blocks of kThreads per box, each thread taking two cells
-// of the grid-stride loop (amortises the box descriptor fetch and the block
-// barrier; measured 1-8 % faster than one cell per thread)
+// per-cell kernels: blocks of kThreads per box, each thread taking L.cpt
+// cells of the grid-stride loop (two by default: amortises the box
+// descriptor fetch and the block barrier, measured 1-8 % faster than one)
 dim3 grid_for(const LevelView& L, int cells) {
-  int bx = (cells + 2 * kThreads - 1) / (2 * kThreads);
+  const int per = kThreads * L.cpt;
+  int bx = (cells + per - 1) / per;
   if (bx < 1) bx = 1;
   return dim3((unsigned)bx, (unsigned)L.nbox, 1);
 }
@@ -1051,7 +1053,8 @@ double sq(int n) { return (double)n * (double)n; }
 
 ZTiles ztiles(const LevelView& L) {
   const int plane = L.max_ex * L.max_ey;  // bounds every box's (x, y) plane
-  return ZTiles{(plane + kZThreads - 1) / kZThreads, (L.max_ez + kZChunk - 1) / kZChunk};
+  return ZTiles{(plane + kZThreads - 1) / kZThreads, (L.max_ez + L.zchunk - 1) / L.zchunk,
+                L.zchunk};
 }
 
 dim3 zgrid(const LevelView& L, ZTiles t) {
@@ -1062,7 +1065,8 @@ dim3 zgrid(const LevelView& L, ZTiles t) {
 // one cell on every side (the stored region)
 ZTiles ztiles_stored(const LevelView& L) {
   const int plane = (L.max_ex + 2) * (L.max_ey + 2);
-  return ZTiles{(plane + kZThreads - 1) / kZThreads, (L.max_ez + 2 + kZChunk - 1) / kZChunk};
+  return ZTiles{(plane + kZThreads - 1) / kZThreads, (L.max_ez + 2 + L.zchunk - 1) / L.zchunk,
+                L.zchunk};
 }
 
 // float64: per-cell form; float32: column form

@@ -230,6 +230,8 @@ struct sr_fmg_s {
   };
   std::vector<Leg> legs;
   bool legs_on = false;            // sr_debug_segment_legs (measured slower: off)
+  int zchunk = kDefaultZChunk, cpt = kDefaultCellsPerThread;  // launch shape
+  long long generation = 0;        // bumped when the launch sequence changes
   int force_timeout = 0;           // sr_debug_force_wait_timeout
   Profile prof;
 
@@ -472,6 +474,8 @@ int finish_level(sr_fmg_s* h, Geom& L) {
   if (rc) return rc;
   CK(cudaMemcpy(L.dglobal, &g, sizeof(BoxDesc), cudaMemcpyHostToDevice));
   LevelView v{};
+  v.zchunk = kDefaultZChunk;
+  v.cpt = kDefaultCellsPerThread;
   v.boxes = L.dboxes;
   v.nbox = L.nbox;
   v.n = L.n;
@@ -1373,6 +1377,31 @@ int srfmg::enqueue_solve_unchecked(sr_fmg_s* h, const double* f, double* u, cuda
   return enqueue_solve(h, f, u, s);
 }
 
+long long srfmg::handle_generation(const sr_fmg_s* h) { return h->generation; }
+
+// the handle's launch sequence changes: its captured graphs go, and batches
+// holding it re-capture theirs
+static void sequence_changed(sr_fmg_s* h) {
+  for (const sr_fmg_s::GraphEntry& e : h->graphs) sr_fmg_batch_destroy(e.b);
+  h->graphs.clear();
+  ++h->generation;
+}
+
+template <typename T>
+static void set_shape(Hier<T>& H, int zchunk, int cpt) {
+  auto apply = [&](Geom& g) {
+    g.view.zchunk = zchunk;
+    g.view.cpt = cpt;
+  };
+  for (Geom& g : H.glev) apply(g);
+  for (Geom& g : H.slev) apply(g);
+  apply(H.trim_r);
+  apply(H.trim_u);
+  for (Geom& g : H.ctrim_r) apply(g);
+  for (Geom& g : H.ctrim_u) apply(g);
+}
+
+
 long long srfmg::handle_cells(const sr_fmg_s* h) {
   return (long long)h->cfg.n * h->cfg.n * h->cfg.n * h->len[0] * h->len[1] * h->len[2];
 }
@@ -1711,11 +1740,29 @@ int sr_debug_narrow(const double* in, float* out, long long n, void* stream) {
   return SR_OK;
 }
 
+int sr_fmg_set_launch_shape(sr_fmg_t h, int zchunk, int cells_per_thread) {
+  if (!h || zchunk < 1 || zchunk > 256 || cells_per_thread < 1 || cells_per_thread > 16)
+    return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  h->zchunk = zchunk;
+  h->cpt = cells_per_thread;
+  set_shape(h->h64, zchunk, cells_per_thread);
+  set_shape(h->h32, zchunk, cells_per_thread);
+  sequence_changed(h);
+  return SR_OK;
+}
+
+int sr_fmg_launch_shape(sr_fmg_t h, int* zchunk, int* cells_per_thread) {
+  if (!h || !zchunk || !cells_per_thread) return SR_ERR_INVALID;
+  *zchunk = h->zchunk;
+  *cells_per_thread = h->cpt;
+  return SR_OK;
+}
+
 int sr_debug_segment_legs(sr_fmg_t h, int enable, int* levels) {
   if (!h) return SR_ERR_INVALID;
   DeviceGuard g(h->device);
-  for (const sr_fmg_s::GraphEntry& e : h->graphs) sr_fmg_batch_destroy(e.b);
-  h->graphs.clear();
+  sequence_changed(h);
   h->legs_on = enable != 0;
   if (levels) {
     *levels = 0;
@@ -1728,8 +1775,7 @@ int sr_debug_segment_legs(sr_fmg_t h, int enable, int* levels) {
 int sr_debug_force_wait_timeout(sr_fmg_t h, int enable) {
   if (!h) return SR_ERR_INVALID;
   DeviceGuard g(h->device);
-  for (const sr_fmg_s::GraphEntry& e : h->graphs) sr_fmg_batch_destroy(e.b);
-  h->graphs.clear();
+  sequence_changed(h);
   h->force_timeout = enable != 0;
   return SR_OK;
 }
@@ -1737,9 +1783,7 @@ int sr_debug_force_wait_timeout(sr_fmg_t h, int enable) {
 int sr_debug_last_stage_trim(sr_fmg_t h, int enable) {
   if (!h) return SR_ERR_INVALID;
   DeviceGuard g(h->device);
-  // captured graphs hold the previous launch sequence
-  for (const sr_fmg_s::GraphEntry& e : h->graphs) sr_fmg_batch_destroy(e.b);
-  h->graphs.clear();
+  sequence_changed(h);
   h->trim = enable != 0;
   return SR_OK;
 }

@@ -34,6 +34,7 @@ struct sr_fmg_batch_s {
   cudaGraphExec_t exec = nullptr;
   std::vector<const double*> f_cached;   // pointers the graph was captured with
   std::vector<double*> u_cached;
+  std::vector<long long> gen_cached;     // the handles' generations at capture
   int captured_streams = 0;
 };
 
@@ -124,6 +125,8 @@ int capture(sr_fmg_batch_s* b, const double* const* f, double* const* u, int str
   }
   b->f_cached.assign(f, f + b->hs.size());
   b->u_cached.assign(u, u + b->hs.size());
+  b->gen_cached.clear();
+  for (sr_fmg_t h : b->hs) b->gen_cached.push_back(srfmg::handle_generation(h));
   b->captured_streams = streams;
   return SR_OK;
 }
@@ -145,7 +148,8 @@ int validate(const sr_fmg_batch_s* b, const double* const* f, double* const* u) 
 int launch_graph(sr_fmg_batch_s* b, const double* const* f, double* const* u, cudaStream_t s) {
   bool same = b->exec && b->captured_streams == b->streams;
   for (size_t i = 0; same && i < b->hs.size(); ++i)
-    same = b->f_cached[i] == f[i] && b->u_cached[i] == u[i];
+    same = b->f_cached[i] == f[i] && b->u_cached[i] == u[i] &&
+           b->gen_cached[i] == srfmg::handle_generation(b->hs[i]);
   if (!same) {
     int rc = capture(b, f, u, b->streams);
     if (rc) return rc;

@@ -50,7 +50,13 @@ struct LevelView {
   int max_genuine;       // largest genuine-region cell count
   int max_ex, max_ey, max_ez;  // largest compute-region extents
   int shell;             // 1: the boxes are stored with a one-cell shell (SR levels)
+  // launch shape (results do not depend on it): cells in z a thread of a
+  // z-column kernel walks, and cells a thread of a per-cell kernel takes
+  int zchunk;            // default kDefaultZChunk
+  int cpt;               // default kDefaultCellsPerThread
 };
+
+constexpr int kDefaultZChunk = 16, kDefaultCellsPerThread = 2;
 
 // A field read with a possibly different layout than the level's boxes (the
 // caller's global f on the finest SR level): single != 0 means every box
@@ -307,5 +313,8 @@ cudaError_t leg_prepare(size_t smem);
 int enqueue_solve_unchecked(::sr_fmg_s* h, const double* f, double* u, cudaStream_t s);
 // cells of the handle's fine grid
 long long handle_cells(const ::sr_fmg_s* h);
+// changes whenever the handle's launch sequence changes (launch shape,
+// debug modes): a batch re-captures its graph when it does
+long long handle_generation(const ::sr_fmg_s* h);
 
 }  // namespace srfmg

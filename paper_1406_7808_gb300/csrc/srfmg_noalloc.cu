@@ -94,6 +94,8 @@ extern "C" int sr_op_smooth_noalloc(int n, int nu, double cheb_lo, double cheb_h
   k_store_desc<<<1, 32, 0, s>>>(b, desc);
   if (cudaGetLastError() != cudaSuccess) return SR_ERR_CUDA;
   LevelView L{};
+  L.zchunk = kDefaultZChunk;
+  L.cpt = kDefaultCellsPerThread;
   L.boxes = desc;
   L.nbox = 1;
   L.n = n;

@@ -140,6 +140,9 @@ def load():
     lib.sr_debug_narrow.argtypes = [_VP, _VP, ctypes.c_longlong, _VP]
     lib.sr_debug_segment_legs.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.sr_debug_force_wait_timeout.argtypes = [_VP, ctypes.c_int]
+    lib.sr_fmg_set_launch_shape.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+    lib.sr_fmg_launch_shape.argtypes = [_VP, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]
     lib.sr_fmg_stage_down.argtypes = [_VP, _VP, ctypes.c_int, _VP]
     lib.sr_fmg_stage_buffers.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                          ctypes.POINTER(ctypes.c_size_t)]
@@ -340,6 +343,20 @@ class Solver:
                                       _dev(out, self.shape, "out"), _stream()),
                "sr_fmg_stage_up")
         return out
+
+    @property
+    def launch_shape(self):
+        """(zchunk, cells_per_thread) of the handle's kernels."""
+        z, c = ctypes.c_int(), ctypes.c_int()
+        _check(load().sr_fmg_launch_shape(self._h, ctypes.byref(z), ctypes.byref(c)),
+               "sr_fmg_launch_shape")
+        return z.value, c.value
+
+    def set_launch_shape(self, zchunk, cells_per_thread):
+        """Cells in z per thread of the column kernels and cells per thread of
+        the per-cell kernels (results do not depend on them)."""
+        _check(load().sr_fmg_set_launch_shape(self._h, int(zchunk), int(cells_per_thread)),
+               "sr_fmg_set_launch_shape")
 
     def debug_segment_legs(self, enable):
         """Segment-resident legs on or off (default: off, the separate kernels

@@ -23,12 +23,12 @@ MIXED512 = dict(n=512, seg=64, K=4, A=8, B=0, mixed=True, n_outer=2, n_coarse=16
 BATCH_SIZES = (64, 128, 192, 256)
 BATCH_PER_SIZE = 16
 
-# segment shapes the autotuner may choose from, per grid size: every
-# candidate keeps 4 genuine cells per segment side on the transition level
-# and J = 8 buffer cells per side (Eq. eq:nb with A = 8, B = 0)
+# segment shapes the autotuner may choose from, per grid size (J = 8 buffer
+# cells per side, Eq. eq:nb with A = 8, B = 0); a candidate whose
+# transition level would lie below the exact coarsest grid is skipped
 SEGMENT_CANDIDATES = {
-    64: [dict(seg=16, K=2), dict(seg=32, K=3), dict(seg=64, K=4)],
-    128: [dict(seg=16, K=2), dict(seg=32, K=3), dict(seg=64, K=4)],
+    64: [dict(seg=16, K=2), dict(seg=32, K=2), dict(seg=32, K=3), dict(seg=64, K=4)],
+    128: [dict(seg=16, K=2), dict(seg=32, K=3), dict(seg=64, K=3), dict(seg=64, K=4)],
     192: [dict(seg=32, K=3), dict(seg=64, K=4)],
     256: [dict(seg=32, K=3), dict(seg=64, K=4)],
 }

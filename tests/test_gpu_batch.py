@@ -50,6 +50,35 @@ def test_batch_equals_individual_solves(gpu):
         s.close()
 
 
+@pytest.mark.parametrize("n,kw", [(64, dict(seg=16, K=2, A=8, B=0)),
+                                  (96, dict(seg=24, K=3, A=6, B=0, mixed=True)),
+                                  (64, dict(seg=32, K=3, A=11, B=1, n_coarse=8))])
+def test_launch_shape_does_not_change_results(gpu, n, kw):
+    """The launch shape (cells in z per column-kernel thread, cells per
+    per-cell-kernel thread) is a pure performance choice: every shape gives
+    the same bits, in a single solve and inside a batch graph, which
+    re-captures when a handle's shape changes."""
+    import torch
+    f = T(inputs.manufactured(n, 7)[0])
+    with gpu.Solver(n, **kw) as s:
+        assert s.launch_shape == (16, 2)
+        ref = s.solve(f).cpu().numpy()
+        for shape in [(1, 1), (7, 3), (8, 1), (32, 4), (256, 16)]:
+            s.set_launch_shape(*shape)
+            assert s.launch_shape == shape
+            assert np.array_equal(s.solve(f).cpu().numpy(), ref)
+        u = torch.empty_like(f)
+        with gpu.Batch([s]) as b:
+            b.solve([f], [u])
+            assert np.array_equal(u.cpu().numpy(), ref)
+            s.set_launch_shape(8, 4)
+            u.zero_()
+            b.solve([f], [u])
+            assert np.array_equal(u.cpu().numpy(), ref)
+        with pytest.raises(gpu.SRFMGError):
+            s.set_launch_shape(0, 2)
+
+
 def test_batch_rejects_repeated_outputs(gpu):
     import torch
     s1, s2 = gpu.Solver(16), gpu.Solver(16)
@@ -83,6 +112,7 @@ def test_full_batch_workload(gpu, oracle_mod):
         f, uex = inputs.manufactured(n, seed)
         kw = workloads.config(choices[n][0])
         okw = {k: v for k, v in kw.items() if k not in ("mixed", "n_outer")}
+        assert kw["n_coarse"] == (12 if n == 192 else 16)
         ref = oracle_mod.solve_refined(f, kw["n_outer"], **okw)
         e_disc = np.abs(exact.dst_solve(f) - uex).max()
         assert np.abs(us[i].cpu().numpy() - ref).max() <= 0.1 * e_disc
