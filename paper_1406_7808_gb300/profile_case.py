@@ -8,7 +8,8 @@ captures (ncu): each case runs a fixed, seeded workload once and exits.
           [--seg 32 --K 3 --A 11 --B 1 --n-coarse 16]
       warm-up solves then one solve of an SR configuration (default: the
       benchmark's segments, buffers and coarsest grid; --plain without
-      segments; --mixed in the mixed-precision mode)
+      segments; --mixed in the mixed-precision mode; --legs with the
+      segment-resident legs)
   python -m paper_1406_7808_gb300.profile_case smooth27 --n 256
       one degree-2 smoothing with the 27-point operator ((14,3,1)/30) on the
       paper's domain [0,2]x[0,1]^2 with n cells per unit length (two
@@ -40,6 +41,8 @@ def main():
     p.add_argument("--A", type=int, default=sr["A"])
     p.add_argument("--B", type=int, default=sr["B"])
     p.add_argument("--n-coarse", type=int, default=sr["n_coarse"])
+    p.add_argument("--legs", action="store_true",
+                   help="segment-resident legs on (mixed mode; off by default)")
     a = p.parse_args()
     build.build()
     torch.cuda.set_device(0)
@@ -62,6 +65,8 @@ def main():
         if a.mixed:
             kw["mixed"] = True
         with srfmg.Solver(a.n, **kw) as s:
+            if a.legs:
+                s.debug_segment_legs(True)
             ut = torch.empty_like(ft)
             for _ in range(a.warmup):
                 s.solve_async(ft, ut)
