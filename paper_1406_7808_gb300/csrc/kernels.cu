@@ -741,33 +741,37 @@ __global__ void __launch_bounds__(kThreads) k_restrict_global(Dims fd, const T* 
 }
 
 // d = float(f - A u) with float64 arithmetic, or d = float(f) without u
-__global__ void __launch_bounds__(kThreads) k_defect(Dims g, const double* __restrict__ f,
-                                                     const double* __restrict__ u,
-                                                     float* __restrict__ d, unsigned int* status,
-                                                     double c6, double cn) {
+__global__ void __launch_bounds__(kThreads, 6) k_defect(Dims g, const double* __restrict__ f,
+                                                        const double* __restrict__ u,
+                                                        float* __restrict__ d,
+                                                        unsigned int* status, double c6,
+                                                        double cn) {
   grid_dep_wait();
-  const long long ncell = (long long)g.x * g.y * g.z;
-  const long long sy = g.x, sz = (long long)g.x * g.y;
+  // 32-bit cell indices (grids hold fewer than 2^31 cells): fewer registers
+  // and index instructions than the 64-bit loop, more resident warps to
+  // cover the neighbour loads of this float64-pipe-bound pass
+  const unsigned nx = (unsigned)g.x, ny = (unsigned)g.y;
+  const unsigned ncell = nx * ny * (unsigned)g.z;
+  const unsigned sy = nx, sz = nx * ny;
   bool bad = false;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
     const double fv = f[i];
     bad |= not_finite(fv);
     if (!u) {
       d[i] = narrow(fv);
       continue;
     }
-    int x, y, z;
-    split3(i, g.x, g.y, x, y, z);
+    const unsigned t = i / nx;
+    const unsigned x = i - t * nx, y = t % ny, z = t / ny;
     const double uc = u[i];
     const double m = negx(uc);
     double v[6];
     v[0] = (x > 0) ? u[i - 1] : m;
-    v[1] = (x < g.x - 1) ? u[i + 1] : m;
+    v[1] = (x < nx - 1) ? u[i + 1] : m;
     v[2] = (y > 0) ? u[i - sy] : m;
-    v[3] = (y < g.y - 1) ? u[i + sy] : m;
+    v[3] = (y < ny - 1) ? u[i + sy] : m;
     v[4] = (z > 0) ? u[i - sz] : m;
-    v[5] = (z < g.z - 1) ? u[i + sz] : m;
+    v[5] = (z < (unsigned)g.z - 1) ? u[i + sz] : m;
     d[i] = narrow(fma6(cn, v, fma(c6, uc, fv)));
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);

@@ -150,19 +150,6 @@ __device__ __forceinline__ int sidx(const Slab& s, int x, int y) {
   return (y - s.oy) * s.sy + (x - s.ox);
 }
 
-struct Cell3 {
-  int x, y, z;
-};
-// cell i of the region [lo, hi) with z restricted to [zl, zh)
-__device__ __forceinline__ Cell3 cell_in(int i, const int lo[3], int ex, int ey, int zl) {
-  Cell3 c;
-  c.x = lo[0] + i % ex;
-  const int t = i / ex;
-  c.y = lo[1] + t % ey;
-  c.z = zl + t / ey;
-  return c;
-}
-
 __device__ __forceinline__ void slab_setup(Slab& s, const BoxDesc& B, int C) {
   s.ox = B.ox;
   s.oy = B.oy;
@@ -432,7 +419,6 @@ __global__ void __launch_bounds__(kLegThreads, 2) k_leg_up(
   Slab s;
   slab_setup(s, B, C);
   LegArrays A = leg_arrays(s, max_planes);
-  const int nx = L.nx, ny = L.ny, nz = L.nz;
   if (threadIdx.x == 0) mbar_init(A.bar, 1);
   for (int i = threadIdx.x; i < (s.p1 - s.p0) * s.sz; i += blockDim.x) A.r[i] = 0.f;
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -491,8 +477,6 @@ __global__ void __launch_bounds__(kLegThreads, 2) k_leg_up(
     }
   }
   cl.sync();
-  (void)nx;
-  (void)ny;
 }
 
 }  // namespace
