@@ -132,16 +132,17 @@ def ncu_traffic(kernel):
     """DRAM traffic per launch of `kernel` from the committed ncu summary, if
     the kernel source is unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", f"ncu_{kernel}.md")
-    src = os.path.join(ROOT, "paper_1406_7808_gb300", "csrc", "kernels.cu")
-    if not os.path.exists(path) or not os.path.exists(src):
+    csrc = os.path.join(ROOT, "paper_1406_7808_gb300", "csrc")
+    srcs = [os.path.join(csrc, "kernels.cu"), os.path.join(csrc, "srfmg_device.cuh")]
+    if not os.path.exists(path) or not all(os.path.exists(x) for x in srcs):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = hashlib.sha256(b"".join(open(x, "rb").read() for x in srcs)).hexdigest()[:16]
     vals = {}
     for line in open(path):
         if ": " in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(": ", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernels.cu sha256[:16]") != sha:
+    if vals.get("kernels.cu + srfmg_device.cuh sha256[:16]") != sha:
         return None
     try:
         return float(vals["dram bytes per launch (scaled to the bench workload)"])

@@ -355,6 +355,21 @@ int sr_debug_segment_legs(sr_fmg_t h, int enable, int* levels);
 int sr_debug_force_wait_timeout(sr_fmg_t h, int enable);
 
 /*
+ * The global V-cycle in one persistent launch (float64 handles, 7-point
+ * operator, degree-2 smoothers; Sec. 3.1, Fig. "FAS multigrid V-cycle"):
+ * from the first global level of at most 64^3 cells down to the coarsest
+ * grid, every pass of the cycle runs inside one cooperative launch whose
+ * blocks meet at a grid barrier between passes, with the same results bit
+ * for bit as the separate kernels.  Its barrier waits are bounded (about a
+ * second each; SR_ERR_TIMEOUT on expiry; sr_debug_force_wait_timeout makes
+ * them run out).  sr_debug_persistent_vcycle(h, 0, ...) runs the separate
+ * kernels instead (for comparisons); 1 (the default) the persistent cycle.
+ * *available (may be NULL) receives 1 if the handle can use it.  Drops the
+ * handle's captured graphs.
+ */
+int sr_debug_persistent_vcycle(sr_fmg_t h, int enable, int* available);
+
+/*
  * Testing hook for the float64 -> float32 rounding the mixed mode's
  * float64-arithmetic kernels store their results with (a round-to-nearest-
  * even conversion on the integer pipe): out[i] = in[i] rounded, device

@@ -36,6 +36,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include "srfmg_device.cuh"
 #include "srfmg_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -46,21 +47,8 @@ namespace {
 constexpr int kLegThreads = 512;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bound on an mbarrier wait
 
-__device__ __forceinline__ long long at(const BoxDesc& b, int x, int y, int z) {
-  return b.base + (long long)(z - b.oz) * b.sz + (long long)(y - b.oy) * b.sy + (x - b.ox);
-}
+using namespace dev;
 
-__device__ __forceinline__ float negx(float v) {
-  unsigned b = __float_as_uint(v);
-  asm("xor.b32 %0, %0, 0x80000000;" : "+r"(b));
-  return __uint_as_float(b);
-}
-__device__ __forceinline__ float neg_if(float v, bool flip) {
-  unsigned b = __float_as_uint(v);
-  const unsigned m = (unsigned)flip << 31;
-  asm("xor.b32 %0, %0, %1;" : "+r"(b) : "r"(m));
-  return __uint_as_float(b);
-}
 // ---- mbarrier and bulk copies (inline PTX)
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {

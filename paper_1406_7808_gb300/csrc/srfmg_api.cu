@@ -93,7 +93,7 @@ enum Kind {
   kChebResidualF32, kCheb2UpdateF32, kChebStepF32, kResidRestrictF32, kCoarseRhsMixed,
   kTransitionRhsMixed, kProlongSetF32, kProlongAddF32, kCoarseSolveMixed, kRestrictFF32,
   kGatherMixed, kDefect, kAccumulate, kDiff, kDiffF32, kResidNorm, kShellCopy, kShellCopyF32,
-  kLegDownF32, kLegUpF32, kKinds
+  kLegDownF32, kLegUpF32, kVcyclePersistent, kKinds
 };
 const char* const kKindName[kKinds] = {
   "cheb_residual", "cheb2_update", "cheb_step", "resid_restrict", "coarse_rhs",
@@ -103,7 +103,7 @@ const char* const kKindName[kKinds] = {
   "coarse_rhs_mixed", "transition_rhs_mixed", "prolong_f32", "prolong_correct_f32",
   "coarse_solve_mixed", "restrict_f_f32", "gather_genuine_mixed", "defect", "accumulate",
   "correction", "correction_f32", "resid_norm", "shell_copy", "shell_copy_f32",
-  "leg_down_f32", "leg_up_f32"};
+  "leg_down_f32", "leg_up_f32", "vcycle_persistent"};
 
 // kind of a kernel for storage type T: float64 kinds shift to their float32
 // counterparts (same order)
@@ -231,6 +231,12 @@ struct sr_fmg_s {
   std::vector<Leg> legs;
   bool legs_on = false;            // sr_debug_segment_legs (measured slower: off)
   int zchunk = kDefaultZChunk, cpt = kDefaultCellsPerThread;  // launch shape
+  // the global V-cycle as one persistent launch (persistent.cu) from the
+  // first global level of at most kPersistentCells cells down
+  bool persistent = false;         // usable: float64, 7-point, degree-2 smoothers
+  bool persistent_on = true;       // sr_debug_persistent_vcycle
+  int vc_blocks = 0;               // blocks of the cooperative launch
+  unsigned* vbar = nullptr;        // its grid barrier
   long long generation = 0;        // bumped when the launch sequence changes
   int force_timeout = 0;           // sr_debug_force_wait_timeout
   Profile prof;
@@ -780,6 +786,29 @@ int build_sr_levels(sr_fmg_s* h, Hier<T>& H) {
   return SR_OK;
 }
 
+// The persistent global V-cycle (persistent.cu): float64, 7-point,
+// degree-2 smoothers; one block per SM.  One block of 256 threads per SM
+// measured faster than two (each grid barrier waits on half as many
+// arrivals; the per-pass work is HBM- or FP64-bound either way) and than a
+// half or a quarter of the SMs (too few warps to cover the finest level).
+int plan_persistent(sr_fmg_s* h) {
+  h->persistent = false;
+  if (h->mixed || h->op27 || h->pre.nu != 2 || h->post.nu != 2 || h->G < 2) return SR_OK;
+  if ((int)h->h64.glev.size() > kVcycleMaxLevels) return SR_OK;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return SR_OK;
+  }
+  const int per_sm = std::min(vcycle_max_blocks_per_sm(), 1);
+  if (per_sm < 1 || sms < 1) return SR_OK;
+  int rc = dalloc(h, &h->vbar, 2);
+  if (rc) return rc;
+  h->vc_blocks = sms * per_sm;
+  h->persistent = true;
+  return SR_OK;
+}
+
 // Segment-resident legs for the float32 SR levels j = 1 .. K-1 (the
 // levels below a stage's top): a level qualifies when its boxes' stored
 // planes can be split over a cluster of at most 16 CTAs whose shared memory
@@ -971,6 +1000,69 @@ int coarse_solve(sr_fmg_s* h, const Level<T>& L, FieldT<T> f, T* u, cudaStream_t
   return SR_OK;
 }
 
+// The persistent cycle takes over from the first global level of at most
+// this many cells (its cooperative launch keeps two blocks per SM: enough for
+// these small levels, fewer warps than the separate kernels give a large one).
+constexpr long long kPersistentCells = 64LL * 64 * 64;
+
+// FASMGV from global level g down (g >= 1) in one persistent launch
+int persistent_vcycle(sr_fmg_s* h, Hier<double>& H, int g, double* u, const double* f,
+                      const double* r_first, cudaStream_t s) {
+  VcycleArgs a{};
+  a.top = g;
+  for (int j = 0; j <= g; ++j) {
+    Level<double>& L = H.glev[j];
+    VcycleLevel& v = a.lev[j];
+    const double n2 = (double)L.n * L.n;
+    v.view = L.view;
+    v.u = (j == g) ? u : L.u;
+    v.r = L.r;
+    v.t = L.t;
+    v.rhs = L.rhs;
+    v.rho = L.rho;
+    v.f = (j == g) ? f : L.rhs;
+    // the constants the separate kernels' launchers pass
+    v.cf = 1.0 / (6.0 * n2);
+    v.cS = -3.0 * n2 / 8.0;
+    v.cO = n2 / 8.0;
+    v.c6 = 6.0 * n2;
+    v.cn = -n2;
+    v.cr = 1.0 / (6.0 * n2);
+  }
+  a.r_first = r_first;
+  a.minv = h->minv;
+  a.sep = h->sep;
+  a.sep_g = h->sep_g;
+  a.sep_q = h->sep_q;
+  {
+    const Geom& c = H.glev[0];
+    int W = 1;
+    while (W < std::max(c.nd[0], std::max(c.nd[1], c.nd[2]))) W *= 2;
+    a.sep_w = W;
+  }
+  a.pre_a = h->pre.a;
+  a.pre_b = h->pre.b;
+  a.post_a = h->post.a;
+  a.post_b = h->post.b;
+  a.sixth = 1.0 / 6.0;
+  a.eighth = 0.125;
+  a.three = 3.0;
+  a.w64 = 1.0 / 64.0;
+  a.mone = -1.0;
+  a.one = 1.0;
+  a.zero = 0.0;
+  a.bar = h->vbar;
+  a.status = h->status;
+  a.force_timeout = h->force_timeout;
+  CK(cudaMemsetAsync(h->vbar, 0, sizeof(unsigned), s));
+  // algorithmic counts per cell of the top level: about 45 operations and
+  // 200 bytes per cell of each level with the coarser ones adding 1/8 each
+  const double cells = H.glev[g].tot_cells;
+  LAUNCH(h, kVcyclePersistent, cells, 45.0 * 8 / 7, 200.0 * 8 / 7, s,
+         launch_vcycle(a, h->vc_blocks, s));
+  return SR_OK;
+}
+
 // FASMGV on global level g (Fig. "FAS multigrid V-cycle"); u is the level's
 // u (or the caller's u on the finest plain FP64 level).
 template <typename T>
@@ -979,6 +1071,10 @@ int vcycle_global(sr_fmg_s* h, Hier<T>& H, int g, T* u, FieldT<T> rhs, cudaStrea
   Level<T>& L = H.glev[g];
   const double w = sizeof(T);
   if (g == 0) return coarse_solve<T>(h, L, rhs, u, s);
+  if constexpr (sizeof(T) == 8) {
+    if (h->persistent && h->persistent_on && cells_of(L) <= kPersistentCells)
+      return persistent_vcycle(h, H, g, u, rhs.p, r_first, s);
+  }
   Level<T>& C = H.glev[g - 1];
   int rc = smooth(h, L, h->pre, u, rhs, s, r_first);
   if (rc) return rc;
@@ -1457,6 +1553,7 @@ int sr_fmg_create(sr_fmg_t* out, const sr_fmg_config* cfg) {
   if (!h->mixed) {
     if (!rc) rc = build_global_levels<double>(h, h->h64, cfg->n >> h->K, h->K == 0);
     if (!rc && h->K) rc = build_sr_levels<double>(h, h->h64);
+    if (!rc) rc = plan_persistent(h);
   } else {
     const size_t cells = (size_t)srfmg::handle_cells(h);
     if (!rc) rc = dalloc(h, &h->defect, cells);
@@ -1769,6 +1866,15 @@ int sr_debug_segment_legs(sr_fmg_t h, int enable, int* levels) {
     for (size_t j = 1; j < h->legs.size(); ++j)
       if (h->legs[j].C > 0) *levels |= 1 << j;
   }
+  return SR_OK;
+}
+
+int sr_debug_persistent_vcycle(sr_fmg_t h, int enable, int* available) {
+  if (!h) return SR_ERR_INVALID;
+  DeviceGuard g(h->device);
+  sequence_changed(h);
+  h->persistent_on = enable != 0;
+  if (available) *available = h->persistent ? 1 : 0;
   return SR_OK;
 }
 

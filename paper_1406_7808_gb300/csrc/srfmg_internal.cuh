@@ -308,6 +308,36 @@ int leg_max_clusters(int C, size_t smem);
 // allow smem bytes of dynamic shared memory for the leg kernels
 cudaError_t leg_prepare(size_t smem);
 
+// ---- the global V-cycle in one persistent cooperative launch (persistent.cu;
+// float64, 7-point, degree-2 smoothers).  Levels 0 (coarsest) .. top.
+constexpr int kVcycleThreads = 256;
+constexpr int kVcycleMaxLevels = 12;
+struct VcycleLevel {
+  LevelView view;        // one whole global level
+  double* u;             // the level's solution (the caller's at the top)
+  double *r, *t, *rhs, *rho;
+  const double* f;       // right-hand side: the caller's at the top, rhs below
+  double cf;             // 1 / (6 n^2)                 (smoother residual)
+  double cS, cO;         // -3 n^2 / 8, n^2 / 8          (residual + restriction)
+  double c6, cn, cr;     // 6 n^2, -n^2, 1 / (6 n^2)     (coarse right-hand side)
+};
+struct VcycleArgs {
+  VcycleLevel lev[kVcycleMaxLevels];
+  int top;
+  const double* r_first;  // the top level's first residual, or null
+  const double* minv;     // dense coarsest inverse, or null for the separable solve
+  const double* sep;
+  double *sep_g, *sep_q;
+  int sep_w;
+  double pre_a, pre_b, post_a, post_b;
+  double sixth, eighth, three, w64, mone, one, zero;
+  unsigned* bar;          // grid barrier: arrivals (zero at launch), generation
+  unsigned* status;
+  int force_timeout;
+};
+cudaError_t launch_vcycle(const VcycleArgs& a, int blocks, cudaStream_t s);
+int vcycle_max_blocks_per_sm();
+
 // Queue one solve of handle h on stream without validating the pointers
 // (the batch path validates them before stream capture); srfmg_api.cu.
 int enqueue_solve_unchecked(::sr_fmg_s* h, const double* f, double* u, cudaStream_t s);

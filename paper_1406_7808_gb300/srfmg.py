@@ -140,6 +140,7 @@ def load():
     lib.sr_debug_narrow.argtypes = [_VP, _VP, ctypes.c_longlong, _VP]
     lib.sr_debug_segment_legs.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.sr_debug_force_wait_timeout.argtypes = [_VP, ctypes.c_int]
+    lib.sr_debug_persistent_vcycle.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.sr_fmg_set_launch_shape.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
     lib.sr_fmg_launch_shape.argtypes = [_VP, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]
@@ -365,6 +366,14 @@ class Solver:
         _check(load().sr_debug_segment_legs(self._h, int(bool(enable)), ctypes.byref(levels)),
                "sr_debug_segment_legs")
         return [j for j in range(1, 31) if levels.value >> j & 1]
+
+    def debug_persistent_vcycle(self, enable):
+        """The global V-cycle as one persistent launch (default) or as separate
+        kernels; returns whether the handle can use the persistent one."""
+        avail = ctypes.c_int(0)
+        _check(load().sr_debug_persistent_vcycle(self._h, int(bool(enable)), ctypes.byref(avail)),
+               "sr_debug_persistent_vcycle")
+        return bool(avail.value)
 
     def debug_force_wait_timeout(self, enable):
         """Make the legs' bounded waits run out (the solve reports
