@@ -34,7 +34,7 @@ CASES = [
 
 @pytest.mark.parametrize("n,kw", CASES)
 def test_persistent_equals_separate_kernels(gpu, n, kw):
-    f, _ = inputs.manufactured(n, 8)
+    f, _ = inputs.paper_problem(n) if "lengths" in kw else inputs.manufactured(n, 8)
     with gpu.Solver(n, **kw) as s:
         assert s.debug_persistent_vcycle(True)
         a = s.solve(T(f)).cpu().numpy()
