@@ -150,6 +150,50 @@ def ncu_traffic(kernel):
         return None
 
 
+def csrc_sha():
+    """sha256[:16] over the library's .cu and .cuh sources, concatenated in
+    file-name order."""
+    d = os.path.join(ROOT, "paper_1406_7808_gb300", "csrc")
+    names = sorted(x for x in os.listdir(d) if x.endswith((".cu", ".cuh")))
+    return hashlib.sha256(b"".join(open(os.path.join(d, x), "rb").read()
+                                   for x in names)).hexdigest()[:16]
+
+
+def ncu_dram_per_solve():
+    """{workload: DRAM bytes per solve} from the committed ncu launch lists of
+    whole solves, if the library sources are unchanged since (else {})."""
+    path = os.path.join(ROOT, "profiles", "ncu_dram_per_solve.md")
+    if not os.path.exists(path):
+        return {}
+    vals = {}
+    for line in open(path):
+        if ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(": ", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("csrc sha256[:16]") != csrc_sha():
+        return {}
+    out = {}
+    for k, v in vals.items():
+        if k.endswith(" dram bytes per solve"):
+            try:
+                out[k[: -len(" dram bytes per solve")]] = float(v)
+            except ValueError:
+                pass
+    return out
+
+
+def dram_rate(nbytes, ms, hbm_peak):
+    """Measured DRAM traffic of a solve against the measured copy bandwidth
+    and the 8 TB/s nominal figure."""
+    if not nbytes:
+        return None
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"dram_bytes_per_solve": nbytes, "gbs": gbs,
+            "frac_of_measured": gbs / hbm_peak if hbm_peak else None,
+            "frac_of_nominal_8tbs": gbs / 8000.0,
+            "source": "profiles/ncu_dram_per_solve.md (ncu, whole solve)"}
+
+
 def cpu_baseline(f, min_seconds=10.0, max_solves=6):
     """The oracle, as it stands, timed on this host's cores (full solves of
     the same workload until about min_seconds of work)."""
@@ -488,6 +532,12 @@ def run_ours(args):
     }
     if mixed is not None and hbm:
         mixed["hbm_frac_of_measured"] = mixed["hbm_gbs"] / hbm
+    dram = ncu_dram_per_solve()
+    comparison["plain_fmg_fp64_256"]["dram"] = dram_rate(dram.get("plain_fmg_fp64_256"),
+                                                         plain_ms, hbm_peak)
+    comparison["sr_fmg_fp64_256"]["dram"] = dram_rate(dram.get("sr_fmg_fp64_256"), ms, hbm_peak)
+    if mixed is not None:
+        mixed["dram"] = dram_rate(dram.get("mixed_sr_512"), mixed["ms"], hbm_peak)
 
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
@@ -495,8 +545,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, "n": N, **SR, "J": J,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2: f is 134 MB and each solve sweeps about 3 GB "
-                         "of workspace",
+                   "l2": "inputs larger than L2: f is 134 MB and each solve moves about "
+                         "21.6 GB through DRAM (ncu)",
                    "n_coarse": SR["n_coarse"],
                    "plain_fmg_dof_s": world * N ** 3 / (plain_ms / 1e3),
                    "plain_fmg_ms_per_step": plain_ms},
@@ -504,6 +554,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": N ** 3 * 8, "d2h_bytes_per_step": N ** 3 * 8},
         "gpu_launches": launches * args.steps,
         "roofline": roofline,
+        "hbm": comparison["sr_fmg_fp64_256"]["dram"],
         "peaks": {"fp64_fma_tops_measured": fp64_peak, "fp32_fma_tops_measured": fp32_peak,
                   "fp64_fma_tops_derived": fp64_derived, "sms": sms,
                   "hbm_gbs_measured": hbm_peak},
