@@ -717,12 +717,15 @@ __device__ __forceinline__ bool zcolumn(const int lo[3], const int hi[3], int np
 // every coarse plane it meets it forms the bilinear (x, y) value once
 // (4 reads, 3 FMA, weights 3/4 and 1/4 as 3 a + b), and a fine cell combines
 // the plane of its own coarse cell with the one on its side (1 FMA) and is
-// scaled by 1/64 into uf (add == 0: uf = P uc;  add == 1: uf += P uc).
-template <typename T>
+// scaled by 1/64 into uf (uf = P uc, or uf += P uc).
+// kMode: 0 sets uf, 1 adds to it, 2 adds if add != 0 (one kernel for both,
+// the float64 form: splitting it costs the set mode 1 %)
+template <typename T, int kMode>
 __global__ void __launch_bounds__(kZThreads, 6) k_prolong_zcol(LevelView C, const T* __restrict__ uc,
                                                             LevelView F, T* __restrict__ uf,
                                                             int add, T three, T w64, int nplane,
                                                             Fk<T> k) {
+  constexpr bool kAdd = kMode == 1;
   grid_dep_wait();
   __shared__ BoxDesc B, CB;
   if (threadIdx.x == 0) {
@@ -756,17 +759,158 @@ __global__ void __launch_bounds__(kZThreads, 6) k_prolong_zcol(LevelView C, cons
   T pc = plane(Zlo);
   const long long sz = B.sz;
   long long o = at(B, x, y, 2 * Zlo);
+  if constexpr (kAdd && sizeof(T) == 4) {
+    // float32 correction: the fine values (the stream from DRAM) are loaded
+    // one coarse step ahead, from the planes of this thread's own chunk
+    // (2.16 -> 1.87 ms per 512^3 mixed solve; the float64 kernel and the
+    // FMG prolongation, which reads no fine values, keep the plain loop)
+    T oe = (2 * Zlo >= z0) ? uf[o] : k.zero;
+    T oo = (2 * Zlo + 1 < z1) ? uf[o + sz] : k.zero;
 #pragma unroll 2
-  for (int Zc = Zlo; Zc <= Zhi; ++Zc, o += 2 * sz) {
-    const int fe = 2 * Zc, fo = fe + 1;
-    const bool we = fe >= z0, wo = fo < z1;
-    const T pp = wo ? plane(Zc + 1) : k.zero;
-    const T oe = (add && we) ? uf[o] : k.zero;
-    const T oo = (add && wo) ? uf[o + sz] : k.zero;
-    if (we) uf[o] = fma(w64, fma(three, pc, pm), oe);
-    if (wo) uf[o + sz] = fma(w64, fma(three, pc, pp), oo);
-    pm = pc;
-    pc = pp;
+    for (int Zc = Zlo; Zc <= Zhi; ++Zc, o += 2 * sz) {
+      const int fe = 2 * Zc, fo = fe + 1;
+      const bool we = fe >= z0, wo = fo < z1;
+      const bool next = Zc + 1 <= Zhi;
+      const T ne = next ? uf[o + 2 * sz] : k.zero;
+      const T no = (next && fo + 2 < z1) ? uf[o + 3 * sz] : k.zero;
+      const T pp = wo ? plane(Zc + 1) : k.zero;
+      if (we) uf[o] = fma(w64, fma(three, pc, pm), oe);
+      if (wo) uf[o + sz] = fma(w64, fma(three, pc, pp), oo);
+      pm = pc;
+      pc = pp;
+      oe = ne;
+      oo = no;
+    }
+  } else {
+#pragma unroll 2
+    for (int Zc = Zlo; Zc <= Zhi; ++Zc, o += 2 * sz) {
+      const int fe = 2 * Zc, fo = fe + 1;
+      const bool we = fe >= z0, wo = fo < z1;
+      const T pp = wo ? plane(Zc + 1) : k.zero;
+      const bool addv = kMode == 2 ? add != 0 : kAdd;
+      const T oe = (addv && we) ? uf[o] : k.zero;
+      const T oo = (addv && wo) ? uf[o + sz] : k.zero;
+      if (we) uf[o] = fma(w64, fma(three, pc, pm), oe);
+      if (wo) uf[o + sz] = fma(w64, fma(three, pc, pp), oo);
+      pm = pc;
+      pc = pp;
+    }
+  }
+}
+
+// Column form of k_resid_restrict (float32, where the pass streams): a thread
+// owns a coarse (X, Y) of the restriction region and walks L.zchunk coarse
+// cells in z.  The 2x2 inner values of the fine plane below a coarse cell
+// are the upper children of the previous one, and those of the plane above
+// are the next cell's lower children, so each is loaded once (32 loads per
+// coarse cell instead of 40).  Every sum takes the per-cell kernel's terms
+// in its order (bit-identical results).
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_resid_restrict_zm(LevelView F, const T* __restrict__ u,
+                                                                FieldT<T> f, LevelView C,
+                                                                T* __restrict__ uhat_dst,
+                                                                T* __restrict__ rho_dst, T cS, T cO,
+                                                                T eighth, Fk<T> k, int nplane) {
+  grid_dep_wait();
+  __shared__ BoxDesc B, FB, CB;
+  if (threadIdx.x == 0) {
+    B = F.boxes[blockIdx.y];
+    FB = f.single ? f.boxes[0] : f.boxes[blockIdx.y];
+    CB = (C.nbox == 1) ? C.boxes[0] : C.boxes[blockIdx.y];
+  }
+  __syncthreads();
+  int lo[3], hi[3];
+  region_of(B, kRestrict, lo, hi);
+  int X, Y, Z0, Z1;
+  if (!zcolumn(lo, hi, nplane, F.zchunk, X, Y, Z0, Z1)) return;
+  const int x0 = 2 * X, y0 = 2 * Y;
+  const long long sy = B.sy, sz = B.sz, fy = FB.sy, fz = FB.sz;
+  const bool xl = x0 > 0, xr = x0 + 2 < F.nx, yl = y0 > 0, yr = y0 + 2 < F.ny;
+  long long c0 = at(B, x0, y0, 2 * Z0);
+  long long f0 = at(FB, x0, y0, 2 * Z0);
+  long long cc = at(CB, X, Y, Z0);
+  T below[2][2], cur[2][2];
+  bool zl = 2 * Z0 > 0;
+  if (zl) {
+    below[0][0] = u[c0 - sz];
+    below[0][1] = u[c0 - sz + 1];
+    below[1][0] = u[c0 - sz + sy];
+    below[1][1] = u[c0 - sz + sy + 1];
+  }
+  cur[0][0] = u[c0];
+  cur[0][1] = u[c0 + 1];
+  cur[1][0] = u[c0 + sy];
+  cur[1][1] = u[c0 + sy + 1];
+  for (int Z = Z0; Z < Z1; ++Z) {
+    const int z0 = 2 * Z;
+    T v[2][2][2];
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        v[0][cy][cx] = cur[cy][cx];
+        v[1][cy][cx] = u[c0 + sz + cy * sy + cx];
+      }
+    const bool zr = z0 + 2 < F.nz;
+    T above[2][2];
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) above[cy][cx] = zr ? u[c0 + 2 * sz + cy * sy + cx] : k.zero;
+    T fs = fma(f.p[f0], k.one, f.p[f0 + 1]);
+    fs = fma(f.p[f0 + fy], k.one, fs);
+    fs = fma(f.p[f0 + fy + 1], k.one, fs);
+    fs = fma(f.p[f0 + fz], k.one, fs);
+    fs = fma(f.p[f0 + fz + 1], k.one, fs);
+    fs = fma(f.p[f0 + fz + fy], k.one, fs);
+    fs = fma(f.p[f0 + fz + fy + 1], k.one, fs);
+    T S = fma(v[0][0][0], k.one, v[0][0][1]);
+    S = fma(v[0][1][0], k.one, S);
+    S = fma(v[0][1][1], k.one, S);
+    S = fma(v[1][0][0], k.one, S);
+    S = fma(v[1][0][1], k.one, S);
+    S = fma(v[1][1][0], k.one, S);
+    S = fma(v[1][1][1], k.one, S);
+    T O = k.zero;
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+      for (int cy = 0; cy < 2; ++cy) {
+        const long long row = c0 + cz * sz + cy * sy;
+        O = fma(xl ? u[row - 1] : negx(v[cz][cy][0]), k.one, O);
+        O = fma(xr ? u[row + 2] : negx(v[cz][cy][1]), k.one, O);
+      }
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        const long long col = c0 + cz * sz + cx;
+        O = fma(yl ? u[col - sy] : negx(v[cz][0][cx]), k.one, O);
+        O = fma(yr ? u[col + 2 * sy] : negx(v[cz][1][cx]), k.one, O);
+      }
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        O = fma(zl ? below[cy][cx] : negx(v[0][cy][cx]), k.one, O);
+        O = fma(zr ? above[cy][cx] : negx(v[1][cy][cx]), k.one, O);
+      }
+    rho_dst[cc] = fma(cS, S, fma(cO, O, fma(fs, eighth, k.zero)));
+    uhat_dst[cc] = fma(S, eighth, k.zero);
+    // the next coarse cell: its plane below is this cell's upper children,
+    // its lower children the plane above (loaded when it lies in the domain,
+    // which it does whenever there is a next cell)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        below[cy][cx] = v[1][cy][cx];
+        cur[cy][cx] = above[cy][cx];
+      }
+    zl = true;
+    c0 += 2 * sz;
+    f0 += 2 * fz;
+    cc += CB.sz;
   }
 }
 
@@ -999,9 +1143,19 @@ template <typename T>
 cudaError_t launch_resid_restrict(const LevelView& F, const T* u, FieldT<T> f,
                                   const LevelView& C, T* uhat_dst, T* rho_dst, cudaStream_t s) {
   const double n2 = sq(F.n);
-  SRFMG_LAUNCH(pdl_launch(k_resid_restrict<T>, grid_for(F, F.max_restrict), kThreads, 0, s, F, u,
-                          f, C, uhat_dst, rho_dst, T(-3.0 * n2 / 8.0), T(n2 / 8.0), T(0.125),
-                          fk<T>()));
+  if (sizeof(T) == 4) {
+    // coarse z-columns over the restriction region, which lies within half
+    // the compute region in each dimension
+    const int rx = (F.max_ex + 1) / 2, ry = (F.max_ey + 1) / 2, rz = (F.max_ez + 1) / 2;
+    const int nplane = (rx * ry + kZThreads - 1) / kZThreads;
+    const dim3 grid((unsigned)(nplane * ((rz + F.zchunk - 1) / F.zchunk)), (unsigned)F.nbox, 1);
+    SRFMG_LAUNCH(pdl_launch(k_resid_restrict_zm<T>, grid, kZThreads, 0, s, F, u, f, C, uhat_dst,
+                            rho_dst, T(-3.0 * n2 / 8.0), T(n2 / 8.0), T(0.125), fk<T>(), nplane));
+  } else {
+    SRFMG_LAUNCH(pdl_launch(k_resid_restrict<T>, grid_for(F, F.max_restrict), kThreads, 0, s, F,
+                            u, f, C, uhat_dst, rho_dst, T(-3.0 * n2 / 8.0), T(n2 / 8.0),
+                            T(0.125), fk<T>()));
+  }
   return cudaGetLastError();
 }
 
@@ -1038,8 +1192,16 @@ cudaError_t launch_prolong(const LevelView& C, const T* uc, const LevelView& F, 
   LevelView Fz = F;
   if (sizeof(T) == 4) Fz.zchunk = 2 * F.zchunk;
   const ZTiles z = ztiles_stored(Fz);  // the prolongation range lies in the stored region
-  SRFMG_LAUNCH(pdl_launch(k_prolong_zcol<T>, zgrid(Fz, z), kZThreads, 0, s, C, uc, Fz, uf, add,
-                          T(3.0), T(1.0 / 64.0), z.nplane, fk<T>()));
+  if constexpr (sizeof(T) == 8) {
+    SRFMG_LAUNCH(pdl_launch(k_prolong_zcol<T, 2>, zgrid(Fz, z), kZThreads, 0, s, C, uc, Fz, uf,
+                            add, T(3.0), T(1.0 / 64.0), z.nplane, fk<T>()));
+  } else if (add) {
+    SRFMG_LAUNCH(pdl_launch(k_prolong_zcol<T, 1>, zgrid(Fz, z), kZThreads, 0, s, C, uc, Fz, uf,
+                            add, T(3.0), T(1.0 / 64.0), z.nplane, fk<T>()));
+  } else {
+    SRFMG_LAUNCH(pdl_launch(k_prolong_zcol<T, 0>, zgrid(Fz, z), kZThreads, 0, s, C, uc, Fz, uf,
+                            add, T(3.0), T(1.0 / 64.0), z.nplane, fk<T>()));
+  }
   return cudaGetLastError();
 }
 
