@@ -799,18 +799,20 @@ __global__ void __launch_bounds__(kZThreads, 6) k_prolong_zcol(LevelView C, cons
 }
 
 // Column form of k_resid_restrict (float32, where the pass streams): a thread
-// owns a coarse (X, Y) of the restriction region and walks L.zchunk coarse
-// cells in z.  The 2x2 inner values of the fine plane below a coarse cell
+// owns a coarse (X, Y) of the restriction region and walks zc coarse cells
+// in z (a quarter of the handle's z-chunk: more blocks, as the kernel holds
+// few warps per SM; 6 blocks per SM).  The 2x2 inner values of the fine plane below a coarse cell
 // are the upper children of the previous one, and those of the plane above
 // are the next cell's lower children, so each is loaded once (32 loads per
 // coarse cell instead of 40).  Every sum takes the per-cell kernel's terms
 // in its order (bit-identical results).
 template <typename T>
-__global__ void __launch_bounds__(kZThreads) k_resid_restrict_zm(LevelView F, const T* __restrict__ u,
+__global__ void __launch_bounds__(kZThreads, 6) k_resid_restrict_zm(LevelView F, const T* __restrict__ u,
                                                                 FieldT<T> f, LevelView C,
                                                                 T* __restrict__ uhat_dst,
                                                                 T* __restrict__ rho_dst, T cS, T cO,
-                                                                T eighth, Fk<T> k, int nplane) {
+                                                                T eighth, Fk<T> k, int nplane,
+                                                                int zc) {
   grid_dep_wait();
   __shared__ BoxDesc B, FB, CB;
   if (threadIdx.x == 0) {
@@ -822,7 +824,7 @@ __global__ void __launch_bounds__(kZThreads) k_resid_restrict_zm(LevelView F, co
   int lo[3], hi[3];
   region_of(B, kRestrict, lo, hi);
   int X, Y, Z0, Z1;
-  if (!zcolumn(lo, hi, nplane, F.zchunk, X, Y, Z0, Z1)) return;
+  if (!zcolumn(lo, hi, nplane, zc, X, Y, Z0, Z1)) return;
   const int x0 = 2 * X, y0 = 2 * Y;
   const long long sy = B.sy, sz = B.sz, fy = FB.sy, fz = FB.sz;
   const bool xl = x0 > 0, xr = x0 + 2 < F.nx, yl = y0 > 0, yr = y0 + 2 < F.ny;
@@ -1143,14 +1145,16 @@ template <typename T>
 cudaError_t launch_resid_restrict(const LevelView& F, const T* u, FieldT<T> f,
                                   const LevelView& C, T* uhat_dst, T* rho_dst, cudaStream_t s) {
   const double n2 = sq(F.n);
-  if (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4) {
     // coarse z-columns over the restriction region, which lies within half
     // the compute region in each dimension
     const int rx = (F.max_ex + 1) / 2, ry = (F.max_ey + 1) / 2, rz = (F.max_ez + 1) / 2;
     const int nplane = (rx * ry + kZThreads - 1) / kZThreads;
-    const dim3 grid((unsigned)(nplane * ((rz + F.zchunk - 1) / F.zchunk)), (unsigned)F.nbox, 1);
+    const int zc = F.zchunk / 4 > 1 ? F.zchunk / 4 : 1;
+    const dim3 grid((unsigned)(nplane * ((rz + zc - 1) / zc)), (unsigned)F.nbox, 1);
     SRFMG_LAUNCH(pdl_launch(k_resid_restrict_zm<T>, grid, kZThreads, 0, s, F, u, f, C, uhat_dst,
-                            rho_dst, T(-3.0 * n2 / 8.0), T(n2 / 8.0), T(0.125), fk<T>(), nplane));
+                            rho_dst, T(-3.0 * n2 / 8.0), T(n2 / 8.0), T(0.125), fk<T>(), nplane,
+                            zc));
   } else {
     SRFMG_LAUNCH(pdl_launch(k_resid_restrict<T>, grid_for(F, F.max_restrict), kThreads, 0, s, F,
                             u, f, C, uhat_dst, rho_dst, T(-3.0 * n2 / 8.0), T(n2 / 8.0),
