@@ -719,9 +719,11 @@ __device__ __forceinline__ bool zcolumn(const int lo[3], const int hi[3], int np
 // the plane of its own coarse cell with the one on its side (1 FMA) and is
 // scaled by 1/64 into uf (uf = P uc, or uf += P uc).
 // kMode: 0 sets uf, 1 adds to it, 2 adds if add != 0 (one kernel for both,
-// the float64 form: splitting it costs the set mode 1 %)
+// the float64 form: splitting it costs the set mode 1 %).  Register bound:
+// 6 blocks per SM in float64, 8 in float32 (32 registers, no spills; the
+// float32 passes ran 14-16 % faster than at 6)
 template <typename T, int kMode>
-__global__ void __launch_bounds__(kZThreads, 6) k_prolong_zcol(LevelView C, const T* __restrict__ uc,
+__global__ void __launch_bounds__(kZThreads, sizeof(T) == 4 ? 8 : 6) k_prolong_zcol(LevelView C, const T* __restrict__ uc,
                                                             LevelView F, T* __restrict__ uf,
                                                             int add, T three, T w64, int nplane,
                                                             Fk<T> k) {
