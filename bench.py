@@ -52,6 +52,15 @@ def workload_name(n=N, sr=SR):
             f"global levels {n >> sr['K']}^3..{nc}^3, {nc}^3 solved exactly"), J
 
 
+def bench_config(world):
+    """The workload's config, the same on both arms of the benchmark."""
+    name, J = workload_name()
+    return {"workload": name, "n": N, **SR, "J": J,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2: f is 134 MB and each solve moves about 21.6 GB "
+                  "through DRAM (ncu)"}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -230,7 +239,6 @@ def run_reference(args):
     oracle_build.build()
     threads = os.cpu_count() or 1
     f, _ = inputs.manufactured(N, SEED)
-    name, J = workload_name()
     # a step is one full solve unless the whole run would take too long, then
     # the same segment geometry on a 128^3 grid (1/8 of the work)
     t0 = time.perf_counter()
@@ -253,7 +261,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "n": N, **SR, "J": J},
+            "config": bench_config(args.gpus),
             "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
@@ -314,7 +322,6 @@ def run_ours(args):
     f, u_exact = inputs.manufactured(N, rank_seed(rank))
     ft = torch.from_numpy(f).cuda()
     ut = torch.empty_like(ft)
-    name, J = workload_name()
     stream = torch.cuda.current_stream()
 
     def timed(solver, steps, sampler=None):
@@ -438,13 +445,13 @@ def run_ours(args):
     # the same segments at the paper's depth (2^3 coarsest grid, J = 8) and
     # plain FMG there: far from discretisation error (comparison only)
     depth2 = {}
-    for name, kw in (("sr", SR_DEPTH2), ("plain", {})):
+    for kind, kw in (("sr", SR_DEPTH2), ("plain", {})):
         with srfmg.Solver(N, graph=True, **kw) as s2:
             for _ in range(args.warmup):
                 s2.solve_async(ft, ut)
             s2.check()
-            depth2[name + "_u"] = ut.cpu().numpy()
-            depth2[name + "_ms"] = timed(s2, args.steps) / args.steps
+            depth2[kind + "_u"] = ut.cpu().numpy()
+            depth2[kind + "_ms"] = timed(s2, args.steps) / args.steps
 
     mixed = batch = None
     paper = adjoint = None
@@ -474,9 +481,9 @@ def run_ours(args):
         acc["e_alg_sr_over_e_disc"] = acc["e_alg_sr"] / acc["e_disc"]
         acc["e_alg_plain_over_e_disc"] = acc["e_alg_plain"] / acc["e_disc"]
         acc["sr_minus_plain_over_e_disc"] = float(np.abs(u_sr - u_plain).max()) / acc["e_disc"]
-        for name in ("sr", "plain"):
-            depth2["e_alg_" + name + "_over_e_disc"] = \
-                float(np.abs(depth2[name + "_u"] - u_h).max()) / acc["e_disc"]
+        for kind in ("sr", "plain"):
+            depth2["e_alg_" + kind + "_over_e_disc"] = \
+                float(np.abs(depth2[kind + "_u"] - u_h).max()) / acc["e_disc"]
     except ImportError:
         pass
     acc["e_sr"] = float(np.abs(u_sr - u_exact).max())
@@ -543,13 +550,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "n": N, **SR, "J": J,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2: f is 134 MB and each solve moves about "
-                         "21.6 GB through DRAM (ncu)",
-                   "n_coarse": SR["n_coarse"],
-                   "plain_fmg_dof_s": world * N ** 3 / (plain_ms / 1e3),
-                   "plain_fmg_ms_per_step": plain_ms},
+        "config": bench_config(world),
         "e2e": {"value": world * N ** 3 / e2e_s, "unit": "DOF/s",
                 "h2d_bytes_per_step": N ** 3 * 8, "d2h_bytes_per_step": N ** 3 * 8},
         "gpu_launches": launches * args.steps,
