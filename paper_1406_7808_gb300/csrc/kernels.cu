@@ -725,10 +725,9 @@ __device__ __forceinline__ bool zcolumn(const int lo[3], const int hi[3], int np
 // 6 blocks per SM in float64, 8 in float32 (32 registers, no spills; the
 // float32 passes ran 14-16 % faster than at 6)
 template <typename T, int kMode>
-__global__ void __launch_bounds__(kZThreads, sizeof(T) == 4 ? 8 : 6) k_prolong_zcol(LevelView C, const T* __restrict__ uc,
-                                                            LevelView F, T* __restrict__ uf,
-                                                            int add, T three, T w64, int nplane,
-                                                            Fk<T> k) {
+__global__ void __launch_bounds__(kZThreads, sizeof(T) == 4 ? 8 : 6)
+    k_prolong_zcol(LevelView C, const T* __restrict__ uc, LevelView F, T* __restrict__ uf,
+                   int add, T three, T w64, int nplane, Fk<T> k) {
   constexpr bool kAdd = kMode == 1;
   grid_dep_wait();
   __shared__ BoxDesc B, CB;
@@ -811,12 +810,10 @@ __global__ void __launch_bounds__(kZThreads, sizeof(T) == 4 ? 8 : 6) k_prolong_z
 // coarse cell instead of 40).  Every sum takes the per-cell kernel's terms
 // in its order (bit-identical results).
 template <typename T>
-__global__ void __launch_bounds__(kZThreads, 6) k_resid_restrict_zm(LevelView F, const T* __restrict__ u,
-                                                                FieldT<T> f, LevelView C,
-                                                                T* __restrict__ uhat_dst,
-                                                                T* __restrict__ rho_dst, T cS, T cO,
-                                                                T eighth, Fk<T> k, int nplane,
-                                                                int zc) {
+__global__ void __launch_bounds__(kZThreads, 6)
+    k_resid_restrict_zm(LevelView F, const T* __restrict__ u, FieldT<T> f, LevelView C,
+                        T* __restrict__ uhat_dst, T* __restrict__ rho_dst, T cS, T cO, T eighth,
+                        Fk<T> k, int nplane, int zc) {
   grid_dep_wait();
   __shared__ BoxDesc B, FB, CB;
   if (threadIdx.x == 0) {
