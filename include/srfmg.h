@@ -258,8 +258,10 @@ int sr_fmg_stage_up(sr_fmg_t h, const double* f_dev, int k, double* u_dev, void*
 /*
  * Launch shape of the handle's kernels (results do not depend on it, bit
  * for bit): zchunk = cells in z that a thread of the z-column kernels walks
- * (1..256, default 16), cells_per_thread = cells a thread of the per-cell
- * kernels takes (1..16, default 2).  Drops the handle's captured graphs;
+ * (1..256, default 16; the float32 prolongation walks twice that, the
+ * float32 residual + restriction a quarter of it in coarse cells, at least
+ * one), cells_per_thread = cells a thread of the per-cell kernels takes
+ * (1..16, default 2).  Drops the handle's captured graphs;
  * batches holding the handle re-capture theirs at their next solve.  The
  * batch autotuner (paper_1406_7808_gb300/autotune.py) picks both per grid
  * size by timing.  The paper has no counterpart.
