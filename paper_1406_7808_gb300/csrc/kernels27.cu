@@ -9,8 +9,9 @@
 // dimension, so edge and corner ghosts of the reflection are exact); a
 // neighbour inside the domain but outside the box's compute region is read
 // from the box's one-cell shell (frozen SR ghosts, or zero in the smoother's
-// residual array).  The smoother passes and the residual walk columns in z
-// (below); the coarse-level kernels read every neighbour through the L1
+// residual array).  The smoother passes, the residual and the coarse
+// right-hand side walk columns in z (below); the transition-level
+// right-hand side and the residual norm read every neighbour through the L1
 // cache.
 #include "srfmg_internal.cuh"
 
@@ -96,50 +97,6 @@ __global__ void __launch_bounds__(kThreads27) k27_apply(LevelView L, const doubl
     const Cell27 q = cell27(i, B.lo, ex, ey);
     const double au = op27(u, B, L, w, n2, q.x, q.y, q.z);
     out[at27(B, q.x, q.y, q.z)] = residual ? f.p[at27(FB, q.x, q.y, q.z)] - au : au;
-  }
-}
-
-// rhs = rho + A u inside the matching fine box's restriction region, A u on
-// the rest of the compute region; t = u on the whole stored box; with r, the
-// smoother's first residual D^-1 (rhs - A u): D^-1 rho and 0 (cr = D^-1)
-__global__ void __launch_bounds__(kThreads27) k27_coarse_rhs(LevelView C, LevelView F,
-                                                             const double* __restrict__ u,
-                                                             const double* __restrict__ rho,
-                                                             double* __restrict__ rhs,
-                                                             double* __restrict__ t,
-                                                             double* __restrict__ r, W27 w,
-                                                             double n2, double cr) {
-  grid_dep_wait();
-  __shared__ BoxDesc B, FBx;
-  if (threadIdx.x == 0) {
-    B = C.boxes[blockIdx.y];
-    FBx = (F.nbox == 1) ? F.boxes[0] : F.boxes[blockIdx.y];
-  }
-  __syncthreads();
-  const bool shell = B.ox < B.lo[0];
-  int lo[3], hi[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    lo[d] = shell ? B.lo[d] - 1 : B.lo[d];
-    hi[d] = shell ? B.hi[d] + 1 : B.hi[d];
-  }
-  const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
-  const int ncell = ex * ey * ez;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
-    const Cell27 q = cell27(i, lo, ex, ey);
-    const bool inside_domain =
-        q.x >= 0 && q.x < C.nx && q.y >= 0 && q.y < C.ny && q.z >= 0 && q.z < C.nz;
-    if (!inside_domain) continue;
-    const long long c = at27(B, q.x, q.y, q.z);
-    t[c] = u[c];
-    const bool compute = q.x >= B.lo[0] && q.x < B.hi[0] && q.y >= B.lo[1] && q.y < B.hi[1] &&
-                         q.z >= B.lo[2] && q.z < B.hi[2];
-    if (!compute) continue;
-    const bool inF = q.x >= FBx.rlo[0] && q.x < FBx.rhi[0] && q.y >= FBx.rlo[1] &&
-                     q.y < FBx.rhi[1] && q.z >= FBx.rlo[2] && q.z < FBx.rhi[2];
-    const double au = op27(u, B, C, w, n2, q.x, q.y, q.z);
-    rhs[c] = inF ? rho[c] + au : au;
-    if (r) r[c] = inF ? cr * rho[c] : 0.0;
   }
 }
 
@@ -336,6 +293,48 @@ __global__ void __launch_bounds__(kZ27Threads) k27_column(LevelView L,
   }
 }
 
+// The coarse-level right-hand side in column form (15 operations per cell
+// instead of 31): rhs = rho + A u inside the restriction region of the
+// matching fine box, A u on the rest of the compute region, with A u =
+// c0 u + cf F + ce E + cc C over the neighbour classes (c0 = w0 n^2,
+// cf = -w1 n^2, ...); t = u and, with r, the smoother's first residual
+// D^-1 (rhs - A u), which is D^-1 rho and 0 (cr = D^-1).  t on the box's
+// shell is copied by the shell-copy pass that follows on SR levels.
+__global__ void __launch_bounds__(kZ27Threads) k27_coarse_rhs_col(
+    LevelView C, LevelView F, const double* __restrict__ u, const double* __restrict__ rho,
+    double* __restrict__ rhs, double* __restrict__ t, double* __restrict__ r, double c0, double cf,
+    double ce, double cc, double cr, double one, double zero, int nplane) {
+  grid_dep_wait();
+  __shared__ BoxDesc B, FBx;
+  if (threadIdx.x == 0) {
+    B = C.boxes[blockIdx.y];
+    FBx = (F.nbox == 1) ? F.boxes[0] : F.boxes[blockIdx.y];
+  }
+  __syncthreads();
+  int x, y, z0, z1;
+  if (!ztile27(B, nplane, x, y, z0, z1)) return;
+  const Col27 q = column27(B, C, x, y);
+  const long long sz = B.sz;
+  long long p = at27(B, x, y, z0);
+  const bool in_xy = x >= FBx.rlo[0] && x < FBx.rhi[0] && y >= FBx.rlo[1] && y < FBx.rhi[1];
+  Plane27 pc = plane27(u, p, q, one);
+  Plane27 pm = (z0 > 0) ? plane27(u, p - sz, q, one) : neg27(pc);
+  for (int z = z0; z < z1; ++z) {
+    const Plane27 pp = (z < C.nz - 1) ? plane27(u, p + sz, q, one) : neg27(pc);
+    const double Fs = fma(pp.c, one, fma(pm.c, one, pc.e));
+    const double Es = fma(pp.e, one, fma(pm.e, one, pc.k));
+    const double Cs = fma(pm.k, one, pp.k);
+    const bool inF = in_xy && z >= FBx.rlo[2] && z < FBx.rhi[2];
+    const double rh = inF ? rho[p] : zero;
+    t[p] = pc.c;
+    rhs[p] = fma(cc, Cs, fma(ce, Es, fma(cf, Fs, fma(c0, pc.c, rh))));
+    if (r) r[p] = inF ? cr * rh : zero;
+    pm = pc;
+    pc = pp;
+    p += sz;
+  }
+}
+
 // uhat = average of the 8 children of u, rho = average of the 8 children of r
 // (r = f - A u already formed on the fine compute region)
 __global__ void __launch_bounds__(kThreads27) k27_restrict_pair(LevelView F,
@@ -446,8 +445,10 @@ cudaError_t launch27_residual(const LevelView& L, const double* u, FieldT<double
 cudaError_t launch27_coarse_rhs(const LevelView& C, const LevelView& F, const double* u,
                                 const double* rho, double* rhs, double* t, double* r, W27 w,
                                 cudaStream_t s) {
-  SRFMG_LAUNCH(pdl_launch(k27_coarse_rhs, grid27(C, C.max_stored), kThreads27, 0, s, C, F, u, rho,
-                          rhs, t, r, w, sq27(C.n), 1.0 / (w.w0 * sq27(C.n))));
+  const double n2 = sq27(C.n);
+  SRFMG_LAUNCH(pdl_launch(k27_coarse_rhs_col, zgrid27(C), kZ27Threads, 0, s, C, F, u, rho, rhs, t,
+                          r, w.w0 * n2, -w.w1 * n2, -w.w2 * n2, -w.w3 * n2,
+                          1.0 / (w.w0 * n2), 1.0, 0.0, nplane27(C)));
   return cudaGetLastError();
 }
 

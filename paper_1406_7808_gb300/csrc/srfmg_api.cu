@@ -902,7 +902,7 @@ cudaError_t op_transition_rhs(const sr_fmg_s* h, const LevelView& C, const T* t,
 // (7-point / 27-point): smoother passes per cell, residual + restriction per
 // coarse cell, coarse right-hand side per cell
 double ops_smooth(const sr_fmg_s* h) { return h->op27 ? 15 : 7; }
-double ops_rhs(const sr_fmg_s* h) { return h->op27 ? 31 : 7; }
+double ops_rhs(const sr_fmg_s* h) { return h->op27 ? 15 : 7; }
 
 // uhat, rho on the coarse cells of F's restriction region from the fine u
 // and right-hand side f: one fused 7-point pass (the residual of the 8
@@ -1215,9 +1215,8 @@ int sr_stage_down(sr_fmg_s* h, Hier<T>& H, const T* f, int k, cudaStream_t s) {
       LAUNCH(h, kind_of<T>(kCoarseRhs), C.tot_cells, ops_rhs(h) + (cr ? 1 : 0), (cr ? 5 : 4) * w,
              s,
              op_coarse_rhs<T>(h, C.view, Lj.view, C.u, C.rho, C.rhs, C.t, cr ? C.r : nullptr, s));
-      if (!h->op27)
-        LAUNCH(h, kind_of<T>(kShellCopy), C.tot_cells / 4, 0, 2 * w, s,
-               launch_shell_copy<T>(C.view, C.u, C.t, s));
+      LAUNCH(h, kind_of<T>(kShellCopy), C.tot_cells / 4, 0, 2 * w, s,
+             launch_shell_copy<T>(C.view, C.u, C.t, s));
     }
   }
   return SR_OK;
